@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark of the red/black Moebius domain-wall hot path on GB300.
+
+Workload (one "step"): a full solve D_DW(m) x = b on a 16^3 x 32 lattice,
+Ls = 16, M5 = 1.8, mf = 0.01, b5 = 1.5, c5 = 0.5 (alpha = b5 + c5 = 2,
+b5 - c5 = 1), SU(3) links exp(i 0.2 H), one Gaussian source: red/black source
+preparation, CGNE on M^dag M to a true FP64 residual of 1e-10 with the
+operator in FP32 (mixed precision, FP64 reliable updates), reconstruction.
+
+metric: Moebius Dslash GFLOP/s over the solve = (M and M^dag applications
+x 3120 flops per odd 5d site) / step time, inputs resident in HBM. Extra keys
+report the per-precision Dslash rate, the time to solution of the mixed and
+plain FP64 solves, the roofline of the dominant kernel (CUDA events around
+each launch in one profiled solve of the same workload), the FP64 oracle on
+the host cores, and the end-to-end rate through mdwf_cgne with host buffers.
+
+Multi-GPU: every rank solves its own source (independent problems, no
+collective on the data path); value = all ranks' flops / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (16, 16, 16, 32)
+LS, M5, B5, C5, MF, EPS = 16, 1.8, 1.5, 0.5, 0.01, 0.2
+GAUGE_SEED, SOURCE_SEED = 1002, 2002
+FLOPS_PER_SITE = 3120.0      # per odd 5d site and M (or M^dag) application
+METRIC = "Moebius Dslash GFLOP/s in CGNE to 1e-10 (mixed FP32/FP64)"
+N5 = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2 * LS
+
+
+def workload_config(inner: str) -> dict:
+    return {"workload": "mdwf-cgne 16^3x32 Ls=16 M5=1.8 mf=0.01 b5=1.5 c5=0.5 eps=0.2",
+            "lattice": list(DIMS), "Ls": LS, "M5": M5, "b5": B5, "c5": C5, "mf": MF, "eps": EPS,
+            "nrhs": 1, "tol": 1e-10, "inner": inner,
+            "l2": "256 MB buffer written between timed steps (L2 129 MB); each step streams > 1 GB"}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["mdwf", "reference"], default="mdwf")
+    ap.add_argument("--inner", choices=["f32", "f16n"], default="f32")
+    ap.add_argument("--no-f64", action="store_true", help="skip the plain FP64 solve comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--quick", action="store_true", help="small lattice, for debugging only")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id is not None:
+                cmd += ["-i", self.gpu_id]
+            self.proc = subprocess.Popen(cmd, stdout=self.file, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        if self.proc is None or self.file is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), float(parts[3]) if parts[3] not in ("[N/A]", "N/A") else 0.0,
+                                 parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+def gpu_identifier(torch) -> str | None:
+    try:
+        u = torch.cuda.get_device_properties(torch.cuda.current_device()).uuid
+        s = str(u)
+        return s if s.startswith("GPU-") else "GPU-" + s
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        return vis.split(",")[0] if vis else None
+
+
+# ------------------------------------------------------------ oracle (CPU)
+
+def cpu_baseline(dims, Ls) -> dict:
+    """The FP64 oracle on this host's cores: a bounded sample of the same
+    workload, two CG iterations' worth of operator work (M, M^dag, M, M^dag)."""
+    import numpy as np
+    import oracle
+    import synthetic as sy
+    oracle.build()
+    p = oracle.Params(dims, Ls, M5, B5, C5, MF)
+    U = sy.gauge_field(dims, EPS, GAUGE_SEED)
+    _, xo = oracle.split(sy.gaussian_field(dims, Ls, SOURCE_SEED), dims)
+    t0 = time.perf_counter()
+    v = xo
+    for _ in range(2):
+        v = oracle.m(v, U, p)
+        v = oracle.m(v, U, p, dagger=True)
+    dt = time.perf_counter() - t0
+    n5 = int(np.prod(dims)) // 2 * Ls
+    gf = 4 * FLOPS_PER_SITE * n5 / dt / 1e9
+    return {"value": gf, "unit": "GFLOP/s", "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"4 applications (M, M^dag, M, M^dag) of the FP64 oracle on the full workload lattice, {dt:.1f} s"}
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    dims, Ls = DIMS, LS
+    import numpy as np
+    import oracle
+    import synthetic as sy
+    oracle.build()
+    p = oracle.Params(dims, Ls, M5, B5, C5, MF)
+    U = sy.gauge_field(dims, EPS, GAUGE_SEED)
+    _, xo = oracle.split(sy.gaussian_field(dims, Ls, SOURCE_SEED), dims)
+    # one step = one CG iteration's operator work (M then M^dag) on the workload
+    def step(v):
+        return oracle.m(oracle.m(v, U, p), U, p, dagger=True)
+    v = xo
+    for _ in range(args.warmup):
+        v = step(v)
+        v = v / np.linalg.norm(v)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v = step(v)
+        v = v / np.linalg.norm(v)
+    dt = time.perf_counter() - t0
+    n5 = int(np.prod(dims)) // 2 * Ls
+    val = 2 * FLOPS_PER_SITE * n5 * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config("f64"),
+            "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": oracle.get_threads(), "kind": "oracle",
+                             "sample": "each step: M then M^dag of the FP64 oracle on the full workload lattice"},
+            "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- GPU arm
+
+def main() -> None:
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    import paper_1206_5214_gb300 as mdwf
+    import synthetic as sy
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    dims, Ls = ((8, 8, 8, 8), 8) if args.quick else (DIMS, LS)
+    n5 = dims[0] * dims[1] * dims[2] * dims[3] // 2 * Ls
+    inner = mdwf.MDWF_F32 if args.inner == "f32" else mdwf.MDWF_F16N
+    U = sy.gauge_field(dims, EPS, GAUGE_SEED)
+    b = sy.gaussian_field(dims, Ls, SOURCE_SEED + 100 * rank)
+    h = mdwf.mdwf_create(dims, Ls, M5, B5, C5, MF)
+    Ud = torch.from_numpy(U).cuda()
+    mdwf.mdwf_load_gauge(h, Ud)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+
+    def solve(prec, use_graph=True):
+        st, info = mdwf.mdwf_cgne(h, xd, bd, tol=1e-10, inner_prec=prec, use_graph=use_graph)
+        return info[0]
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        solve(inner)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+
+    # ---------------- timed region: K solves, device-resident inputs
+    launches0, applies0 = mdwf.mdwf_counters(h)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    infos = []
+    with ClockSampler(gpu_identifier(torch)) as clocks:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record()
+            infos.append(solve(inner))
+            ev[k][1].record()
+        torch.cuda.synchronize()
+    launches1, applies1 = mdwf.mdwf_counters(h)
+    ms = sum(a.elapsed_time(bb) for a, bb in ev)
+    applies = sum(applies1) - sum(applies0)
+    flops = applies * FLOPS_PER_SITE * n5
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    f = torch.tensor([flops], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(f, op=dist.ReduceOp.SUM)
+    ms_max, flops_all = float(t.item()), float(f.item())
+    value = flops_all / (ms_max * 1e-3) / 1e9
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        mdwf.mdwf_destroy(h)
+        return
+
+    # ---------------- dominant kernel: per-launch CUDA events in one profiled solve
+    mdwf.mdwf_profile_read(h, reset=True)
+    mdwf.mdwf_profile_enable(h, True)
+    flush.zero_()
+    prof_info = solve(inner, use_graph=False)
+    stats = mdwf.mdwf_profile_read(h, reset=True)
+    mdwf.mdwf_profile_enable(h, False)
+    total_ms = sum(s["ms"] for s in stats)
+    top = max(stats, key=lambda s: s["ms"])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    achieved = top["bytes"] / top["launches"] / (top["ms"] / top["launches"] * 1e-3) / 1e9
+    roofline = {"kernel": top["name"], "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_source": peak_src, "traffic": None,
+                "launches": top["launches"], "avg_us": 1e3 * top["ms"] / top["launches"],
+                "share_of_solve_kernel_time": top["ms"] / total_ms,
+                "algorithmic_bytes_per_launch": top["bytes"] / top["launches"]}
+    kernels = [{"name": s["name"], "launches": s["launches"], "ms": round(s["ms"], 3),
+                "share": round(s["ms"] / total_ms, 4),
+                "GBps": round(s["bytes"] / (s["ms"] * 1e-3) / 1e9, 1) if s["ms"] > 0 else None}
+               for s in sorted(stats, key=lambda s: -s["ms"])]
+
+    # ---------------- Dslash alone per precision (M applications on resident fields)
+    dslash = {}
+    x_, y_, z_, t_ = dims
+    Vh = x_ * y_ * z_ * t_ // 2
+    src_odd = torch.from_numpy(np.ascontiguousarray(
+        b.reshape(Ls, -1, 4, 3)[:, :Vh])).cuda()   # any field of the right size
+    for name, prec in (("f64", mdwf.MDWF_F64), ("f32", mdwf.MDWF_F32), ("f16n", mdwf.MDWF_F16N)):
+        nbytes = mdwf.mdwf_field_bytes(h, prec, 1)
+        fi = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        fo = torch.empty_like(fi)
+        mdwf.mdwf_field_import(h, fi, src_odd, prec)
+        reps = 4 if name == "f64" else 20
+        for _ in range(3):
+            mdwf.mdwf_apply(h, fo, fi, prec)
+        torch.cuda.synchronize()
+        mdwf.mdwf_profile_enable(h, True)
+        mdwf.mdwf_profile_read(h, reset=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record()
+        for _ in range(reps):
+            mdwf.mdwf_apply(h, fo, fi, prec)
+        e1.record()
+        torch.cuda.synchronize()
+        st = mdwf.mdwf_profile_read(h, reset=True)
+        mdwf.mdwf_profile_enable(h, False)
+        ms_apply = e0.elapsed_time(e1) / reps
+        hop = [s for s in st if s["name"].startswith("hop")]
+        hop_bytes = sum(s["bytes"] for s in hop) / reps
+        dslash[name] = {"ms_per_M": ms_apply, "GFLOPs": FLOPS_PER_SITE * n5 / (ms_apply * 1e-3) / 1e9,
+                        "GBps": hop_bytes / (ms_apply * 1e-3) / 1e9,
+                        "hbm_frac": hop_bytes / (ms_apply * 1e-3) / 1e9 / hbm_peak,
+                        "kernels": {s["name"]: round(1e3 * s["ms"] / s["launches"], 2) for s in st}}
+        del fi, fo
+
+    # ---------------- time to solution: mixed (both inner precisions) and plain FP64
+    cg = {"mixed_" + args.inner: {"ms": ms / args.steps, "iters": infos[-1].iters,
+                                  "reliable_updates": infos[-1].reliable_updates,
+                                  "true_res": infos[-1].true_res, "res_m": infos[-1].res_m}}
+    other = "f16n" if args.inner == "f32" else "f32"
+    for name, prec in ((f"mixed_{other}", mdwf.MDWF_F16N if other == "f16n" else mdwf.MDWF_F32),) + \
+            ((() if args.no_f64 else (("f64", mdwf.MDWF_F64),))):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        inf = solve(prec)
+        e1.record()
+        torch.cuda.synchronize()
+        cg[name] = {"ms": e0.elapsed_time(e1), "iters": inf.iters, "reliable_updates": inf.reliable_updates,
+                    "true_res": inf.true_res, "res_m": inf.res_m}
+
+    # ---------------- end to end through the C ABI with host buffers
+    bh = torch.from_numpy(b).pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    mdwf.mdwf_cgne(h, xh, bh, tol=1e-10, inner_prec=inner)
+    e2e_times = []
+    a0 = sum(mdwf.mdwf_counters(h)[1])
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mdwf.mdwf_cgne(h, xh, bh, tol=1e-10, inner_prec=inner)
+        e2e_times.append(time.perf_counter() - t0)
+    a1 = sum(mdwf.mdwf_counters(h)[1])
+    e2e_flops = (a1 - a0) / len(e2e_times) * FLOPS_PER_SITE * n5
+    e2e_s = sum(e2e_times) / len(e2e_times)
+    bytes_field = b.nbytes
+    e2e = {"value": e2e_flops / e2e_s / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": bytes_field,
+           "d2h_bytes_per_step": bytes_field, "ms_per_step": 1e3 * e2e_s}
+
+    cpu = None if args.no_cpu else cpu_baseline(dims, Ls)
+
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.inner == "f32" else "f16n",
+            "data": "synthetic", "config": workload_config(args.inner),
+            "gpu_launches": launches1 - launches0,
+            "applies_per_step": applies / args.steps,
+            "roofline": roofline, "clocks": clocks.summary(), "e2e": e2e, "cpu_baseline": cpu,
+            "cgne": cg, "dslash": dslash, "kernels": kernels,
+            "profiled_solve": {"iters": prof_info.iters, "true_res": prof_info.true_res}}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    mdwf.mdwf_destroy(h)
+
+
+if __name__ == "__main__":
+    main()

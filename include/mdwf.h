@@ -1,0 +1,203 @@
+/*
+ * mdwf.h -- C ABI of libmdwf: the 4d red/black-preconditioned Moebius
+ * domain-wall operator and its CG solve on one GB300 GPU (sm_103a).
+ *
+ * Method: R. C. Brower, H. Neff, K. Orginos, "The Moebius Domain Wall Fermion
+ * Algorithm", arXiv:1206.5214.
+ *
+ * Operator conventions (shared with every caller):
+ *   D_W   = (4 - M5) - H/2,  H = sum_mu [(1 - g_mu) U_mu(x) d_{x+mu,y}
+ *                                       + (1 + g_mu) U_mu(y)^dag d_{x,y+mu}]
+ *           (Eq. D^Wilson with the Wilson mass -M5; M5 > 0 is the wall height).
+ *   D_DW  = the tridiagonal of Eq. MoebiusOp with D+ = b5 D_W + 1,
+ *           D- = c5 D_W - 1 and the mass-mf corners.
+ *   red/black = checkerboard on x+y+z+t, the same for every s (Sec. 4).
+ *   M     = 1 - I_bb^-1 D_br I_rr^-1 D_rb on the odd (black) sites (Sec. 4),
+ *           the operator every mdwf_apply computes and mdwf_cgne inverts.
+ *   Chiral gamma basis g_mu = [[0, A_mu], [A_mu^dag, 0]], A_k = -i sigma_k,
+ *   A_4 = 1, g5 = diag(1, 1, -1, -1); P+ is spins 0, 1 and P- spins 2, 3.
+ *   Periodic boundary conditions in all four directions.
+ *
+ * User data formats (complex128 = two doubles, C order):
+ *   gauge      U[t][z][y][x][mu][3][3], mu = 0..3 for x, y, z, t; U_mu(x) links
+ *              x to x+mu.
+ *   full field [rhs][s][t][z][y][x][spin 4][colour 3]
+ *   odd field  [rhs][s][t][z][y][x/2][spin 4][colour 3]: the odd sites
+ *              (x+y+z+t odd) of every (y, z, t) row in increasing x.
+ *   dims = {X, Y, Z, T}, every extent even and >= 2, Ls even and >= 2.
+ *
+ * Internal fields are opaque device buffers of mdwf_field_bytes() bytes
+ * (256-byte aligned pointers), one per precision: the caller allocates them
+ * (cudaMalloc, torch.empty, ...) and owns them; the library never frees
+ * caller memory. The context owns its own workspace (gauge copies, Ls x Ls
+ * tables, temporaries) and frees it in mdwf_destroy.
+ *
+ * Streams and synchronisation: every call enqueues its GPU work on the
+ * context's stream (mdwf_opts.stream, or mdwf_set_stream) and returns after
+ * the enqueue, except where a function says it synchronises. Calls on one
+ * context must not run concurrently from several host threads.
+ *
+ * Errors: every function returns an mdwf_status; nothing is thrown across the
+ * ABI. MDWF_ECUDA reports a failed CUDA call (the CUDA error string is kept
+ * for mdwf_last_error()).
+ */
+#ifndef MDWF_H
+#define MDWF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MDWF_OK = 0,
+    MDWF_EINVAL = 1,      /* bad argument: odd/zero extent, Ls < 2 or odd, NULL pointer, bad enum */
+    MDWF_ENOMEM = 2,      /* device or host allocation failed */
+    MDWF_ECUDA = 3,       /* a CUDA runtime call failed */
+    MDWF_ENOCONV = 4,     /* the solve reached maxiter; x holds the last iterate */
+    MDWF_EBREAKDOWN = 5,  /* CG breakdown: <p, M^dag M p> <= 0 or a non-finite scalar */
+    MDWF_ETIMEOUT = 6,    /* a bounded device-side wait gave up */
+    MDWF_ENOGAUGE = 7     /* no gauge field loaded yet */
+} mdwf_status;
+
+typedef enum {
+    MDWF_F64 = 0,         /* FP64 values, FP64 arithmetic */
+    MDWF_F32 = 1,         /* FP32 values, FP32 arithmetic */
+    MDWF_F16N = 2         /* FP16 values with one FP32 norm per (site, s); FP32 arithmetic */
+} mdwf_precision;
+
+typedef enum {
+    MDWF_HOST = 0,        /* pointer is host memory (pageable or pinned) */
+    MDWF_DEVICE = 1       /* pointer is device memory of the context's device */
+} mdwf_where;
+
+typedef struct mdwf_ctx mdwf_ctx;
+
+typedef struct {
+    void *stream;         /* cudaStream_t to enqueue on; NULL = the legacy default stream */
+    int device;           /* CUDA device ordinal; -1 = the device current at mdwf_create */
+} mdwf_opts;
+
+/*
+ * Creates a context for one lattice and one set of Moebius parameters
+ * (Eq. MoebiusOp with constant b5(s) = b5, c5(s) = c5, Sec. 3).
+ * dims: {X, Y, Z, T}, each even and >= 2. Ls: even, 2 <= Ls <= 32.
+ * M5: wall height (D_W diagonal 4 - M5). mf: wall mass m (Eq. DWaction).
+ * opts may be NULL. On success *out owns device workspace until mdwf_destroy.
+ */
+int mdwf_create(mdwf_ctx **out, const int dims[4], int Ls, double M5, double b5, double c5,
+                double mf, const mdwf_opts *opts);
+
+/* Frees the context and its workspace (synchronises the context's stream). NULL is accepted. */
+int mdwf_destroy(mdwf_ctx *ctx);
+
+/* Changes the stream later calls enqueue on. */
+int mdwf_set_stream(mdwf_ctx *ctx, void *stream);
+
+/*
+ * Loads the SU(3) links U_mu(x) (Eq. D^Wilson) from complex128
+ * U[t][z][y][x][mu][3][3] in host (where = MDWF_HOST) or device memory.
+ * The data is copied into per-parity, per-direction link arrays in FP64,
+ * FP32 and FP16; the caller's buffer may be reused once the call returns
+ * (host) or once the stream has passed this point (device).
+ */
+int mdwf_load_gauge(mdwf_ctx *ctx, const double *U, int where);
+
+/* Bytes of one internal odd- (or even-) parity field of nrhs right-hand sides. */
+size_t mdwf_field_bytes(const mdwf_ctx *ctx, int prec, int nrhs);
+
+/*
+ * Converts nrhs odd-site fields from the user odd format (complex128) in
+ * host or device memory into the internal layout of precision prec (dst:
+ * device, mdwf_field_bytes(ctx, prec, nrhs) bytes). F16N stores each (site, s)
+ * spinor as FP16 values scaled by their max-abs component, kept as an FP32 norm.
+ */
+int mdwf_field_import(mdwf_ctx *ctx, void *dst, const double *src, int prec, int nrhs, int where);
+
+/* Inverse of mdwf_field_import: internal field (device) -> user odd format (host or device). */
+int mdwf_field_export(mdwf_ctx *ctx, double *dst, const void *src, int prec, int nrhs, int where);
+
+/*
+ * out = M in on the odd sites, M = 1 - I_bb^-1 D_br I_rr^-1 D_rb (Sec. 4),
+ * for nrhs internal fields of precision prec (device buffers, in != out).
+ * mf_per_rhs: NULL (every right-hand side uses the context's mf) or nrhs
+ * masses (host memory), one per right-hand side.
+ */
+int mdwf_apply(mdwf_ctx *ctx, void *out, const void *in, int prec, int nrhs, const double *mf_per_rhs);
+
+/* out = M^dag in, the adjoint of mdwf_apply's operator (same arguments). */
+int mdwf_apply_dag(mdwf_ctx *ctx, void *out, const void *in, int prec, int nrhs, const double *mf_per_rhs);
+
+typedef struct {
+    double tol;           /* target |M^dag b' - M^dag M x| / |M^dag b'| (FP64, recomputed); 0 = 1e-10 */
+    int maxiter;          /* CG iteration cap; 0 = 20000 */
+    int inner_prec;       /* MDWF_F64: plain FP64 CG; MDWF_F32 / MDWF_F16N: mixed precision
+                             with FP64 reliable updates of x and the true residual */
+    double delta;         /* reliable-update threshold on |r| / max |r|; 0 = 0.1 */
+    int check_every;      /* iterations between host convergence polls; 0 = 8 */
+    int use_graph;        /* 1: replay the CG iteration as a captured CUDA graph */
+} mdwf_solve_params;
+
+typedef struct {
+    int status;           /* MDWF_OK, MDWF_ENOCONV or MDWF_EBREAKDOWN for this right-hand side */
+    int iters;            /* CG iterations */
+    int reliable_updates; /* FP64 true-residual recomputations (mixed solves) */
+    double true_res;      /* final FP64 |M^dag b' - M^dag M x| / |M^dag b'| */
+    double res_m;         /* final FP64 |b' - M x| / |b'| */
+    double seconds;       /* wall time of the whole call (same for every right-hand side) */
+} mdwf_solve_info;
+
+/*
+ * Solves D_DW(m) x = b for nrhs full 5d right-hand sides (user full format,
+ * complex128, host or device as where says): b'_o = I_bb^-1 (b_o - D_br
+ * I_rr^-1 b_e), CG on M^dag M x_o = M^dag b'_o (Sec. 3.2, Sec. 4), then
+ * x_e = I_rr^-1 (b_e - D_rb x_o). x has b's format and location.
+ * mf_per_rhs: NULL or nrhs masses (host). params may be NULL (defaults).
+ * info: NULL or an array of nrhs entries. Synchronises the stream.
+ * Returns the worst per-rhs status.
+ */
+int mdwf_cgne(mdwf_ctx *ctx, double *x, const double *b, int nrhs, const double *mf_per_rhs,
+              int where, const mdwf_solve_params *params, mdwf_solve_info *info);
+
+/*
+ * Per-kernel timing. While enabled, every kernel the context launches outside
+ * a CUDA-graph capture is bracketed by two CUDA events on the launch stream
+ * (solves then run without graphs). mdwf_profile_read synchronises the
+ * stream, adds up the event pairs and fills up to max entries (kernels with
+ * at least one launch): launches, total milliseconds and the algorithmic
+ * bytes and flops of those launches (the model the roofline uses: every
+ * input and output field read or written once, every link read once per
+ * hop; 1320 flops per 5d site for the hopping term). reset != 0 clears the
+ * accumulators afterwards.
+ */
+typedef struct {
+    char name[40];        /* e.g. "hop_gather_f32", "hop_dag_xpay_f16n", "m5_f64", "blas_f32" */
+    long long launches;
+    double ms;
+    double bytes;
+    double flops;
+} mdwf_kernel_stat;
+
+int mdwf_profile_enable(mdwf_ctx *ctx, int enable);
+int mdwf_profile_read(mdwf_ctx *ctx, mdwf_kernel_stat *out, int max, int *n_out, int reset);
+
+/*
+ * Cumulative counters since mdwf_create: kernel launches of this library
+ * (a replayed CUDA graph counts every kernel it holds) and operator
+ * applications M or M^dag per precision (applies[MDWF_F64 .. MDWF_F16N], one
+ * count per right-hand side batch). Either pointer may be NULL.
+ */
+int mdwf_counters(const mdwf_ctx *ctx, long long *launches, long long applies[3]);
+
+/* Human-readable name of a status code (static string). */
+const char *mdwf_strerror(int status);
+
+/* Text of the last CUDA error seen by this thread, or "" (static/thread-local string). */
+const char *mdwf_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MDWF_H */

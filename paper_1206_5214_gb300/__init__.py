@@ -1,0 +1,232 @@
+"""Python binding of libmdwf, the GB300 (sm_103a) Moebius domain-wall operator.
+
+The functions here carry the names of the C entry points in ``include/mdwf.h``
+and only marshal arguments: every step of the operator and the solve runs in
+the library's CUDA kernels. Buffers are passed as ``torch.Tensor`` (device or
+host) or ``numpy.ndarray`` (host); their pointers go straight to the C call.
+There is no CPU fallback: if ``libmdwf.so`` cannot be loaded every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "MDWF_F64", "MDWF_F32", "MDWF_F16N", "MdwfError", "lib_path", "load",
+    "mdwf_create", "mdwf_destroy", "mdwf_set_stream", "mdwf_load_gauge", "mdwf_field_bytes",
+    "mdwf_field_import", "mdwf_field_export", "mdwf_apply", "mdwf_apply_dag", "mdwf_cgne",
+    "mdwf_strerror", "mdwf_profile_enable", "mdwf_profile_read", "mdwf_counters", "SolveParams",
+    "SolveInfo", "KernelStat",
+]
+
+MDWF_F64, MDWF_F32, MDWF_F16N = 0, 1, 2
+MDWF_HOST, MDWF_DEVICE = 0, 1
+_lib = None
+
+
+class MdwfError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = f"{where}: {mdwf_strerror(status)}"
+        if _lib is not None:
+            extra = _lib.mdwf_last_error().decode()
+            if extra:
+                msg += f" ({extra})"
+        super().__init__(msg)
+        self.status = status
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("device", ctypes.c_int)]
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("inner_prec", ctypes.c_int),
+                ("delta", ctypes.c_double), ("check_every", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int),
+                ("true_res", ctypes.c_double), ("res_m", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libmdwf.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise OSError(f"libmdwf.so not found at {path}; run paper_1206_5214_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, ip, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    dp = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "mdwf_create": (ip, [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), ip, ctypes.c_double,
+                             ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_Opts)]),
+        "mdwf_destroy": (ip, [vp]),
+        "mdwf_set_stream": (ip, [vp, vp]),
+        "mdwf_load_gauge": (ip, [vp, vp, ip]),
+        "mdwf_field_bytes": (sz, [vp, ip, ip]),
+        "mdwf_field_import": (ip, [vp, vp, vp, ip, ip, ip]),
+        "mdwf_field_export": (ip, [vp, vp, vp, ip, ip, ip]),
+        "mdwf_apply": (ip, [vp, vp, vp, ip, ip, dp]),
+        "mdwf_apply_dag": (ip, [vp, vp, vp, ip, ip, dp]),
+        "mdwf_cgne": (ip, [vp, vp, vp, ip, dp, ip, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]),
+        "mdwf_profile_enable": (ip, [vp, ip]),
+        "mdwf_profile_read": (ip, [vp, ctypes.POINTER(KernelStat), ip, ctypes.POINTER(ctypes.c_int), ip]),
+        "mdwf_counters": (ip, [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+        "mdwf_strerror": (ctypes.c_char_p, [ip]),
+        "mdwf_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str) -> None:
+    if status != 0:
+        raise MdwfError(status, where)
+
+
+def _ptr_where(a) -> tuple[int, int]:
+    """(pointer, MDWF_HOST / MDWF_DEVICE) of a torch tensor or numpy array."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy buffers must be C-contiguous")
+        return a.ctypes.data, MDWF_HOST
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr(), (MDWF_DEVICE if a.is_cuda else MDWF_HOST)
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _masses(mf_per_rhs):
+    if mf_per_rhs is None:
+        return None
+    arr = (ctypes.c_double * len(mf_per_rhs))(*[float(m) for m in mf_per_rhs])
+    return arr
+
+
+def mdwf_strerror(status: int) -> str:
+    return load().mdwf_strerror(int(status)).decode()
+
+
+def mdwf_create(dims, Ls: int, M5: float, b5: float, c5: float, mf: float, stream=None, device: int = -1):
+    """Create a context; returns an opaque handle (int). ``stream``: torch.cuda.Stream, raw handle or None."""
+    lib = load()
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    opts = _Opts(_stream_handle(stream), int(device))
+    _check(lib.mdwf_create(ctypes.byref(h), d, int(Ls), float(M5), float(b5), float(c5), float(mf),
+                           ctypes.byref(opts)), "mdwf_create")
+    return h.value
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def mdwf_destroy(ctx) -> None:
+    _check(load().mdwf_destroy(ctx), "mdwf_destroy")
+
+
+def mdwf_set_stream(ctx, stream) -> None:
+    _check(load().mdwf_set_stream(ctx, _stream_handle(stream)), "mdwf_set_stream")
+
+
+def mdwf_load_gauge(ctx, U) -> None:
+    p, where = _ptr_where(U)
+    _check(load().mdwf_load_gauge(ctx, p, where), "mdwf_load_gauge")
+
+
+def mdwf_field_bytes(ctx, prec: int, nrhs: int = 1) -> int:
+    return int(load().mdwf_field_bytes(ctx, int(prec), int(nrhs)))
+
+
+def mdwf_field_import(ctx, dst, src, prec: int, nrhs: int = 1) -> None:
+    pd, wd = _ptr_where(dst)
+    if wd != MDWF_DEVICE:
+        raise ValueError("internal fields live in device memory")
+    ps, ws = _ptr_where(src)
+    _check(load().mdwf_field_import(ctx, pd, ps, int(prec), int(nrhs), ws), "mdwf_field_import")
+
+
+def mdwf_field_export(ctx, dst, src, prec: int, nrhs: int = 1) -> None:
+    pd, wd = _ptr_where(dst)
+    ps, ws = _ptr_where(src)
+    if ws != MDWF_DEVICE:
+        raise ValueError("internal fields live in device memory")
+    _check(load().mdwf_field_export(ctx, pd, ps, int(prec), int(nrhs), wd), "mdwf_field_export")
+
+
+def mdwf_apply(ctx, out, inp, prec: int, nrhs: int = 1, mf_per_rhs=None) -> None:
+    po, _ = _ptr_where(out)
+    pi, _ = _ptr_where(inp)
+    _check(load().mdwf_apply(ctx, po, pi, int(prec), int(nrhs), _masses(mf_per_rhs)), "mdwf_apply")
+
+
+def mdwf_apply_dag(ctx, out, inp, prec: int, nrhs: int = 1, mf_per_rhs=None) -> None:
+    po, _ = _ptr_where(out)
+    pi, _ = _ptr_where(inp)
+    _check(load().mdwf_apply_dag(ctx, po, pi, int(prec), int(nrhs), _masses(mf_per_rhs)), "mdwf_apply_dag")
+
+
+def mdwf_cgne(ctx, x, b, nrhs: int = 1, mf_per_rhs=None, tol: float = 1e-10, maxiter: int = 20000,
+              inner_prec: int = MDWF_F64, delta: float = 0.1, check_every: int = 8, use_graph: bool = True,
+              raise_on_error: bool = True):
+    """Solve D_DW(m) x = b (full 5d fields, complex128, user order). Returns (status, [SolveInfo per rhs])."""
+    px, wx = _ptr_where(x)
+    pb, wb = _ptr_where(b)
+    if wx != wb:
+        raise ValueError("x and b must both be host or both be device buffers")
+    prm = SolveParams(float(tol), int(maxiter), int(inner_prec), float(delta), int(check_every), int(bool(use_graph)))
+    infos = (SolveInfo * int(nrhs))()
+    st = load().mdwf_cgne(ctx, px, pb, int(nrhs), _masses(mf_per_rhs), wb, ctypes.byref(prm), infos)
+    if raise_on_error and st not in (0,):
+        raise MdwfError(st, "mdwf_cgne")
+    return st, list(infos)
+
+
+def mdwf_profile_enable(ctx, enable: bool = True) -> None:
+    _check(load().mdwf_profile_enable(ctx, int(bool(enable))), "mdwf_profile_enable")
+
+
+def mdwf_profile_read(ctx, reset: bool = False) -> list[dict]:
+    """Per-kernel launches, total ms (CUDA events) and algorithmic bytes / flops."""
+    out = (KernelStat * 64)()
+    n = ctypes.c_int(0)
+    _check(load().mdwf_profile_read(ctx, out, 64, ctypes.byref(n), int(bool(reset))), "mdwf_profile_read")
+    return [{"name": out[i].name.decode(), "launches": out[i].launches, "ms": out[i].ms,
+             "bytes": out[i].bytes, "flops": out[i].flops} for i in range(n.value)]
+
+
+def mdwf_counters(ctx) -> tuple[int, list[int]]:
+    """(kernel launches, [M/M^dag applications in F64, F32, F16N]) since mdwf_create."""
+    launches = ctypes.c_longlong(0)
+    applies = (ctypes.c_longlong * 3)()
+    _check(load().mdwf_counters(ctx, ctypes.byref(launches), applies), "mdwf_counters")
+    return int(launches.value), [int(a) for a in applies]

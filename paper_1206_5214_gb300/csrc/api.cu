@@ -1,0 +1,496 @@
+// C entry points of libmdwf: context, gauge upload, field conversion and the
+// red/black preconditioned Moebius operator M and M^dag.
+//
+// M = 1 - I_bb^-1 D_br I_rr^-1 D_rb (Sec. 4) is applied in the factored form
+//   D_rb = -1/2 H_eo M_phi,   I_rr = I_bb = M+ + M- C,   M_phi = b5 + c5 C,
+//   M = 1 - 1/4 A H_oe K H_eo M_phi,   A = I^-1,  K = M_phi A,
+// with C the fifth-dimension shift (P- psi_{s+1} + P+ psi_{s-1}, mass -m on
+// the wrap-around), M+ = b5 (4 - M5) + 1, M- = c5 (4 - M5) - 1. Every s-mixing
+// factor is a real Ls x Ls matrix per chirality; A, K and their adjoints are
+// built here in FP64 by dense inversion of I. Two launches make one M:
+//   z_e  = K H_eo (M_phi psi_o)                  (gather fused into the hop)
+//   out  = psi_o - 1/4 A H_oe z_e                (xpay fused)
+// and three make M^dag = 1 - 1/4 M_phi^dag H'_oe K^dag H'_eo A^dag (H' the
+// hopping part of D_W^dag):
+//   v_o  = A^dag psi_o;  z_e = K^dag H'_eo v_o;  out = psi_o - 1/4 M_phi^dag H'_oe z_e.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "mdwf_internal.cuh"
+
+namespace {
+thread_local char g_last_error[512] = "";
+}
+
+namespace mdwf {
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return MDWF_OK;
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) return MDWF_ENOMEM;
+    return MDWF_ECUDA;
+}
+
+int check_launch() { return cuda_status(cudaGetLastError()); }
+
+// ----------------------------------------------------------- instrumentation
+
+static cudaEvent_t take_event(mdwf_ctx* c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+LaunchScope::LaunchScope(mdwf_ctx* c, int kind, double bytes, double flops)
+    : c_(c), kind_(kind), bytes_(bytes), flops_(flops) {
+    if (c_->prof_on && !c_->capturing) {
+        a_ = take_event(c_);
+        if (a_) cudaEventRecord(a_, c_->stream);
+    }
+}
+
+LaunchScope::~LaunchScope() {
+    if (c_->capturing) {
+        c_->cap_launches += 1;
+        c_->cap_kstat[kind_].launches += 1;
+        c_->cap_kstat[kind_].bytes += bytes_;
+        c_->cap_kstat[kind_].flops += flops_;
+        return;
+    }
+    c_->launches += 1;
+    c_->kstat[kind_].launches += 1;
+    c_->kstat[kind_].bytes += bytes_;
+    c_->kstat[kind_].flops += flops_;
+    if (a_) {
+        cudaEvent_t b = take_event(c_);
+        if (b) {
+            cudaEventRecord(b, c_->stream);
+            c_->prof_pending.push_back(ProfRec{kind_, a_, b});
+        } else {
+            c_->ev_pool.push_back(a_);
+        }
+    }
+}
+
+void note_apply(mdwf_ctx* c, int prec) {
+    if (c->capturing) c->cap_applies[prec] += 1;
+    else c->applies[prec] += 1;
+}
+
+void replay_graph_counts(mdwf_ctx* c, long long replays) {
+    c->launches += replays * c->cap_launches;
+    for (int p = 0; p < 3; ++p) c->applies[p] += replays * c->cap_applies[p];
+    for (int k = 0; k < KK_NUM; ++k) {
+        c->kstat[k].launches += replays * c->cap_kstat[k].launches;
+        c->kstat[k].bytes += replays * c->cap_kstat[k].bytes;
+        c->kstat[k].flops += replays * c->cap_kstat[k].flops;
+    }
+}
+
+static void kernel_name(int kind, char* out, size_t n) {
+    static const char* base[KB_NUM] = {"hop", "hop_gather", "hop_xpay", "hop_gather_xpay", "hop_dag",
+                                       "hop_dag_xpay", "m5", "m5_xpay", "blas", "layout"};
+    static const char* prec[3] = {"f64", "f32", "f16n"};
+    snprintf(out, n, "%s_%s", base[kind / 3], prec[kind % 3]);
+}
+
+int ensure_workspace(Workspace& w, size_t bytes) {
+    if (w.bytes >= bytes) return MDWF_OK;
+    if (w.p) {
+        cudaError_t e = cudaFree(w.p);
+        w.p = nullptr;
+        w.bytes = 0;
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    cudaError_t e = cudaMalloc(&w.p, bytes);
+    if (e != cudaSuccess) {
+        w.p = nullptr;
+        return cuda_status(e);
+    }
+    w.bytes = bytes;
+    return MDWF_OK;
+}
+
+// ----------------------------------------------------- Ls x Ls tables (host)
+
+// Gauss-Jordan inverse with partial pivoting, n <= kMaxLs.
+static bool invert(int n, const double* a, double* inv) {
+    double m[kMaxLs][2 * kMaxLs];
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < 2 * n; ++j) m[i][j] = j < n ? a[i * n + j] : (j - n == i ? 1.0 : 0.0);
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < n; ++r)
+            if (fabs(m[r][col]) > fabs(m[piv][col])) piv = r;
+        if (m[piv][col] == 0.0) return false;
+        if (piv != col)
+            for (int j = 0; j < 2 * n; ++j) { double t = m[col][j]; m[col][j] = m[piv][j]; m[piv][j] = t; }
+        double d = 1.0 / m[col][col];
+        for (int j = 0; j < 2 * n; ++j) m[col][j] *= d;
+        for (int r = 0; r < n; ++r) {
+            if (r == col || m[r][col] == 0.0) continue;
+            double f = m[r][col];
+            for (int j = 0; j < 2 * n; ++j) m[r][j] -= f * m[col][j];
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) inv[i * n + j] = m[i][n + j];
+    return true;
+}
+
+static void matmul(int n, const double* a, const double* b, double* c) {
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double s = 0;
+            for (int k = 0; k < n; ++k) s += a[i * n + k] * b[k * n + j];
+            c[i * n + j] = s;
+        }
+}
+
+// out[op][chir][s'][s] = Mat_op,chir(s, s') for one mass; chir 0 = P+, 1 = P-.
+static bool build_tables(int Ls, double M5, double b5, double c5, double mf, double* out) {
+    const int n = Ls, nn = Ls * Ls;
+    const double Mp = b5 * (4.0 - M5) + 1.0, Mm = c5 * (4.0 - M5) - 1.0;
+    for (int chir = 0; chir < 2; ++chir) {
+        std::vector<double> C(nn, 0.0), Mphi(nn), Mee(nn), A(nn), K(nn);
+        // P- (chir 1): (C psi)_s = psi_{s+1}, row Ls-1 takes -m psi_0.
+        // P+ (chir 0): the transpose, (C psi)_s = psi_{s-1}, row 0 takes -m psi_{Ls-1}.
+        for (int s = 0; s < n; ++s) {
+            if (chir == 1) {
+                if (s + 1 < n) C[s * n + s + 1] = 1.0;
+                else C[s * n + 0] = -mf;
+            } else {
+                if (s > 0) C[s * n + s - 1] = 1.0;
+                else C[0 * n + n - 1] = -mf;
+            }
+        }
+        for (int i = 0; i < nn; ++i) {
+            const double id = (i / n == i % n) ? 1.0 : 0.0;
+            Mphi[i] = b5 * id + c5 * C[i];
+            Mee[i] = Mp * id + Mm * C[i];
+        }
+        if (!invert(n, Mee.data(), A.data())) return false;
+        matmul(n, Mphi.data(), A.data(), K.data());
+        const double* mats[T_NUM] = {K.data(), A.data(), A.data(), K.data(), Mphi.data(), nullptr};
+        const bool transp[T_NUM] = {false, false, true, true, true, false};
+        for (int op = 0; op < T_NUM; ++op) {
+            double* dst = out + ((size_t)op * 2 + chir) * nn;
+            for (int s = 0; s < n; ++s)
+                for (int sp = 0; sp < n; ++sp) {
+                    double v;
+                    if (op == T_ID) v = (s == sp) ? 1.0 : 0.0;
+                    else v = transp[op] ? mats[op][sp * n + s] : mats[op][s * n + sp];
+                    dst[sp * n + s] = v;  // element (s, s') stored at [s'][s]
+                }
+        }
+    }
+    return true;
+}
+
+int ensure_tables(mdwf_ctx* c, int nrhs, const double* mf_per_rhs) {
+    if (nrhs < 1 || nrhs > 64) return MDWF_EINVAL;
+    double masses[64];
+    for (int r = 0; r < nrhs; ++r) masses[r] = mf_per_rhs ? mf_per_rhs[r] : c->mf;
+    if (c->tab_valid && c->tab_nrhs == nrhs && memcmp(masses, c->tab_masses, sizeof(double) * nrhs) == 0)
+        return MDWF_OK;
+    const int Ls = c->g.Ls, nn = Ls * Ls;
+    const size_t per_rhs = (size_t)T_NUM * 2 * nn;
+    const size_t total = per_rhs * nrhs;
+    // previous kernels may still read the old tables: let them finish first
+    int st = cuda_status(cudaStreamSynchronize(c->stream));
+    if (st) return st;
+    if (c->tab_cap < nrhs || !c->tab64) {
+        cudaFree(c->tab64); cudaFree(c->tab32); cudaFree(c->mass64); cudaFree(c->mass32);
+        cudaFreeHost(c->tab_host);
+        c->tab64 = nullptr; c->tab32 = nullptr; c->mass64 = nullptr; c->mass32 = nullptr; c->tab_host = nullptr;
+        if ((st = cuda_status(cudaMalloc(&c->tab64, total * sizeof(double))))) return st;
+        if ((st = cuda_status(cudaMalloc(&c->tab32, total * sizeof(float))))) return st;
+        if ((st = cuda_status(cudaMalloc(&c->mass64, 64 * sizeof(double))))) return st;
+        if ((st = cuda_status(cudaMalloc(&c->mass32, 64 * sizeof(float))))) return st;
+        if ((st = cuda_status(cudaMallocHost(&c->tab_host, total * (sizeof(double) + sizeof(float)) + 64 * 12 + 16))))
+            return st;
+        c->tab_cap = nrhs;
+    }
+    // host layout: [op][rhs][chir][s'][s]
+    double* h64 = c->tab_host;
+    float* h32 = reinterpret_cast<float*>(h64 + total);
+    double* hm64 = reinterpret_cast<double*>(h32 + total + (total & 1));
+    float* hm32 = reinterpret_cast<float*>(hm64 + 64);
+    std::vector<double> one(per_rhs);
+    for (int r = 0; r < nrhs; ++r) {
+        if (!build_tables(Ls, c->M5, c->b5, c->c5, masses[r], one.data())) return MDWF_EINVAL;
+        for (int op = 0; op < T_NUM; ++op)
+            memcpy(h64 + ((size_t)op * nrhs + r) * 2 * nn, one.data() + (size_t)op * 2 * nn, sizeof(double) * 2 * nn);
+        hm64[r] = masses[r];
+        hm32[r] = (float)masses[r];
+    }
+    for (size_t i = 0; i < total; ++i) h32[i] = (float)h64[i];
+    if ((st = cuda_status(cudaMemcpyAsync(c->tab64, h64, total * sizeof(double), cudaMemcpyHostToDevice, c->stream))))
+        return st;
+    if ((st = cuda_status(cudaMemcpyAsync(c->tab32, h32, total * sizeof(float), cudaMemcpyHostToDevice, c->stream))))
+        return st;
+    if ((st = cuda_status(cudaMemcpyAsync(c->mass64, hm64, 64 * sizeof(double), cudaMemcpyHostToDevice, c->stream))))
+        return st;
+    if ((st = cuda_status(cudaMemcpyAsync(c->mass32, hm32, 64 * sizeof(float), cudaMemcpyHostToDevice, c->stream))))
+        return st;
+    if ((st = cuda_status(cudaStreamSynchronize(c->stream)))) return st;
+    memcpy(c->tab_masses, masses, sizeof(double) * nrhs);
+    c->tab_nrhs = nrhs;
+    c->tab_valid = true;
+    return MDWF_OK;
+}
+
+// ------------------------------------------------------------ operator chain
+
+int apply_op(mdwf_ctx* c, void* out, const void* in, int prec, int nrhs, int dagger) {
+    const size_t fb = field_bytes(prec, c->g, nrhs);
+    int st;
+    note_apply(c, prec);
+    if ((st = ensure_workspace(c->tmp[0], fb))) return st;
+    if ((st = ensure_workspace(c->tmp[1], fb))) return st;
+    const void* mass = prec == MDWF_F64 ? (const void*)c->mass64 : (const void*)c->mass32;
+    HopLaunch h{};
+    h.nrhs = nrhs;
+    h.b5 = c->b5;
+    h.c5 = c->c5;
+    h.mass = mass;
+    if (!dagger) {
+        h.out = c->tmp[0].p; h.in = in; h.x = nullptr; h.coef = 1.0; h.out_parity = 0;
+        h.gather = 1; h.dagger = 0; h.mat = table_ptr(c, prec, T_K);
+        if ((st = launch_hop(c, prec, h))) return st;
+        h.out = out; h.in = c->tmp[0].p; h.x = in; h.coef = -0.25; h.out_parity = 1;
+        h.gather = 0; h.dagger = 0; h.mat = table_ptr(c, prec, T_A);
+        return launch_hop(c, prec, h);
+    }
+    M5Launch m{};
+    m.out = c->tmp[1].p; m.in = in; m.x = nullptr; m.coef = 1.0; m.nrhs = nrhs;
+    m.mat = table_ptr(c, prec, T_ADAG);
+    if ((st = launch_m5(c, prec, m))) return st;
+    h.out = c->tmp[0].p; h.in = c->tmp[1].p; h.x = nullptr; h.coef = 1.0; h.out_parity = 0;
+    h.gather = 0; h.dagger = 1; h.mat = table_ptr(c, prec, T_KDAG);
+    if ((st = launch_hop(c, prec, h))) return st;
+    h.out = out; h.in = c->tmp[0].p; h.x = in; h.coef = -0.25; h.out_parity = 1;
+    h.gather = 0; h.dagger = 1; h.mat = table_ptr(c, prec, T_MPHIDAG);
+    return launch_hop(c, prec, h);
+}
+
+}  // namespace mdwf
+
+using namespace mdwf;
+
+// ------------------------------------------------------------------- C ABI
+
+extern "C" {
+
+const char* mdwf_strerror(int status) {
+    switch (status) {
+        case MDWF_OK: return "MDWF_OK";
+        case MDWF_EINVAL: return "MDWF_EINVAL: invalid argument";
+        case MDWF_ENOMEM: return "MDWF_ENOMEM: out of memory";
+        case MDWF_ECUDA: return "MDWF_ECUDA: CUDA runtime error";
+        case MDWF_ENOCONV: return "MDWF_ENOCONV: solver did not converge";
+        case MDWF_EBREAKDOWN: return "MDWF_EBREAKDOWN: CG breakdown";
+        case MDWF_ETIMEOUT: return "MDWF_ETIMEOUT: device wait limit reached";
+        case MDWF_ENOGAUGE: return "MDWF_ENOGAUGE: no gauge field loaded";
+    }
+    return "unknown mdwf status";
+}
+
+const char* mdwf_last_error(void) { return g_last_error; }
+
+int mdwf_create(mdwf_ctx** out, const int dims[4], int Ls, double M5, double b5, double c5, double mf,
+                const mdwf_opts* opts) {
+    if (!out || !dims) return MDWF_EINVAL;
+    *out = nullptr;
+    for (int mu = 0; mu < 4; ++mu)
+        if (dims[mu] < 2 || (dims[mu] & 1)) return MDWF_EINVAL;
+    if (Ls < 2 || Ls > kMaxLs || (Ls & 1)) return MDWF_EINVAL;
+    if (!isfinite(M5) || !isfinite(b5) || !isfinite(c5) || !isfinite(mf)) return MDWF_EINVAL;
+    int dev = opts ? opts->device : -1;
+    int st;
+    if (dev < 0) {
+        if ((st = cuda_status(cudaGetDevice(&dev)))) return st;
+    } else if ((st = cuda_status(cudaSetDevice(dev)))) {
+        return st;
+    }
+    mdwf_ctx* c = new (std::nothrow) mdwf_ctx();
+    if (!c) return MDWF_ENOMEM;
+    c->device = dev;
+    c->stream = opts ? (cudaStream_t)opts->stream : nullptr;
+    c->g.X = dims[0]; c->g.Y = dims[1]; c->g.Z = dims[2]; c->g.T = dims[3];
+    c->g.Ls = Ls;
+    c->g.Vh = (long long)dims[0] * dims[1] * dims[2] * dims[3] / 2;
+    c->M5 = M5; c->b5 = b5; c->c5 = c5; c->mf = mf;
+    // the default mass tables, so that an apply needs no host round trip
+    if ((st = ensure_tables(c, 1, nullptr))) {
+        mdwf_destroy(c);
+        return st;
+    }
+    *out = c;
+    return MDWF_OK;
+}
+
+int mdwf_destroy(mdwf_ctx* c) {
+    if (!c) return MDWF_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (int k = 0; k < 3; ++k) cudaFree(c->gauge[k]);
+    cudaFree(c->tab64); cudaFree(c->tab32); cudaFree(c->mass64); cudaFree(c->mass32);
+    cudaFreeHost(c->tab_host);
+    cudaFree(c->tmp[0].p); cudaFree(c->tmp[1].p);
+    cudaFree(c->solver.p);
+    cudaFree(c->red_partials);
+    for (auto& r : c->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    delete c;
+    return check_launch();
+}
+
+int mdwf_set_stream(mdwf_ctx* c, void* stream) {
+    if (!c) return MDWF_EINVAL;
+    c->stream = (cudaStream_t)stream;
+    return MDWF_OK;
+}
+
+int mdwf_load_gauge(mdwf_ctx* c, const double* U, int where) {
+    if (!c || !U || (where != MDWF_HOST && where != MDWF_DEVICE)) return MDWF_EINVAL;
+    int st;
+    if ((st = cuda_status(cudaSetDevice(c->device)))) return st;
+    const size_t nlink = (size_t)c->g.Vh * 2 * 4 * 9;  // complex entries
+    const size_t bytes[3] = {nlink * 16, nlink * 8, nlink * 4};
+    for (int k = 0; k < 3; ++k)
+        if (!c->gauge[k] && (st = cuda_status(cudaMalloc(&c->gauge[k], bytes[k])))) return st;
+    const double* src = U;
+    void* stage = nullptr;
+    if (where == MDWF_HOST) {
+        if ((st = cuda_status(cudaMalloc(&stage, bytes[0])))) return st;
+        st = cuda_status(cudaMemcpyAsync(stage, U, bytes[0], cudaMemcpyHostToDevice, c->stream));
+        if (st) { cudaFree(stage); return st; }
+        src = (const double*)stage;
+    }
+    st = launch_gauge_pack(c, src);
+    if (stage) {
+        int s2 = cuda_status(cudaStreamSynchronize(c->stream));
+        cudaFree(stage);
+        if (!st) st = s2;
+    }
+    if (!st) c->have_gauge = true;
+    return st;
+}
+
+size_t mdwf_field_bytes(const mdwf_ctx* c, int prec, int nrhs) {
+    if (!c || nrhs < 1) return 0;
+    return field_bytes(prec, c->g, nrhs);
+}
+
+static bool valid_prec(int p) { return p == MDWF_F64 || p == MDWF_F32 || p == MDWF_F16N; }
+
+int mdwf_field_import(mdwf_ctx* c, void* dst, const double* src, int prec, int nrhs, int where) {
+    if (!c || !dst || !src || !valid_prec(prec) || nrhs < 1 || (where != MDWF_HOST && where != MDWF_DEVICE))
+        return MDWF_EINVAL;
+    int st;
+    if ((st = cuda_status(cudaSetDevice(c->device)))) return st;
+    const size_t ub = (size_t)nrhs * c->g.Ls * c->g.Vh * 24 * sizeof(double);
+    const double* s = src;
+    void* stage = nullptr;
+    if (where == MDWF_HOST) {
+        if ((st = cuda_status(cudaMalloc(&stage, ub)))) return st;
+        st = cuda_status(cudaMemcpyAsync(stage, src, ub, cudaMemcpyHostToDevice, c->stream));
+        if (st) { cudaFree(stage); return st; }
+        s = (const double*)stage;
+    }
+    st = launch_import_odd(c, dst, s, prec, nrhs);
+    if (stage) {
+        int s2 = cuda_status(cudaStreamSynchronize(c->stream));
+        cudaFree(stage);
+        if (!st) st = s2;
+    }
+    return st;
+}
+
+int mdwf_field_export(mdwf_ctx* c, double* dst, const void* src, int prec, int nrhs, int where) {
+    if (!c || !dst || !src || !valid_prec(prec) || nrhs < 1 || (where != MDWF_HOST && where != MDWF_DEVICE))
+        return MDWF_EINVAL;
+    int st;
+    if ((st = cuda_status(cudaSetDevice(c->device)))) return st;
+    const size_t ub = (size_t)nrhs * c->g.Ls * c->g.Vh * 24 * sizeof(double);
+    if (where == MDWF_DEVICE) return launch_export_odd(c, dst, src, prec, nrhs);
+    void* stage = nullptr;
+    if ((st = cuda_status(cudaMalloc(&stage, ub)))) return st;
+    st = launch_export_odd(c, (double*)stage, src, prec, nrhs);
+    if (!st) st = cuda_status(cudaMemcpyAsync(dst, stage, ub, cudaMemcpyDeviceToHost, c->stream));
+    int s2 = cuda_status(cudaStreamSynchronize(c->stream));
+    cudaFree(stage);
+    return st ? st : s2;
+}
+
+static int apply_entry(mdwf_ctx* c, void* out, const void* in, int prec, int nrhs, const double* mf, int dagger) {
+    if (!c || !out || !in || !valid_prec(prec) || nrhs < 1 || nrhs > 64 || out == in) return MDWF_EINVAL;
+    if (!c->have_gauge) return MDWF_ENOGAUGE;
+    int st;
+    if ((st = cuda_status(cudaSetDevice(c->device)))) return st;
+    if ((st = ensure_tables(c, nrhs, mf))) return st;
+    return apply_op(c, out, in, prec, nrhs, dagger);
+}
+
+int mdwf_apply(mdwf_ctx* c, void* out, const void* in, int prec, int nrhs, const double* mf_per_rhs) {
+    return apply_entry(c, out, in, prec, nrhs, mf_per_rhs, 0);
+}
+
+int mdwf_apply_dag(mdwf_ctx* c, void* out, const void* in, int prec, int nrhs, const double* mf_per_rhs) {
+    return apply_entry(c, out, in, prec, nrhs, mf_per_rhs, 1);
+}
+
+int mdwf_profile_enable(mdwf_ctx* c, int enable) {
+    if (!c) return MDWF_EINVAL;
+    c->prof_on = enable != 0;
+    return MDWF_OK;
+}
+
+int mdwf_profile_read(mdwf_ctx* c, mdwf_kernel_stat* out, int max, int* n_out, int reset) {
+    if (!c || (max > 0 && !out)) return MDWF_EINVAL;
+    int st = cuda_status(cudaStreamSynchronize(c->stream));
+    if (st) return st;
+    for (auto& r : c->prof_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) c->kstat[r.kind].ms += ms;
+        c->ev_pool.push_back(r.a);
+        c->ev_pool.push_back(r.b);
+    }
+    c->prof_pending.clear();
+    int n = 0;
+    for (int k = 0; k < KK_NUM; ++k) {
+        if (c->kstat[k].launches == 0) continue;
+        if (n < max) {
+            kernel_name(k, out[n].name, sizeof(out[n].name));
+            out[n].launches = c->kstat[k].launches;
+            out[n].ms = c->kstat[k].ms;
+            out[n].bytes = c->kstat[k].bytes;
+            out[n].flops = c->kstat[k].flops;
+        }
+        ++n;
+    }
+    if (n_out) *n_out = n < max ? n : max;
+    if (reset)
+        for (int k = 0; k < KK_NUM; ++k) c->kstat[k] = KStat{};
+    return MDWF_OK;
+}
+
+int mdwf_counters(const mdwf_ctx* c, long long* launches, long long applies[3]) {
+    if (!c) return MDWF_EINVAL;
+    if (launches) *launches = c->launches;
+    if (applies)
+        for (int p = 0; p < 3; ++p) applies[p] = c->applies[p];
+    return MDWF_OK;
+}
+
+}  // extern "C"

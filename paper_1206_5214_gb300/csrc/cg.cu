@@ -1,0 +1,665 @@
+// CGNE on M^dag M for the red/black Moebius operator, plain FP64 or mixed
+// precision with FP64 reliable updates, for a batch of right-hand sides.
+//
+// The paper solves with conjugate gradient (Sec. 3.2, Sec. 5) and measures
+// cost in Dirac applications; the variant here is CG on the normal
+// equations M^dag M x = M^dag b', with b' the red/black-preconditioned source
+// of the Schur decomposition (Sec. 4). All CG scalars live on the device
+// (alpha, beta, |r|^2 per right-hand side); the host only polls them every
+// few iterations. Dot products and norms accumulate in FP64 through a
+// two-pass reduction: per-block partials, then one block per right-hand side
+// summing the partials in a fixed order, so results do not depend on timing.
+//
+// Mixed precision: the iteration runs with the operator in FP32 or FP16+norm
+// (FP32 arithmetic) on p, M p, M^dag M p, with the iterated residual r_s and
+// the correction x_s in FP32. When |r_s| drops below delta * max |r_s| since
+// the last update (or below the target), x += x_s and the true residual
+// r = M^dag b' - M^dag M x is recomputed with the FP64 operator; r_s = r.
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+#include <vector>
+
+#include "mdwf_internal.cuh"
+
+namespace mdwf {
+
+enum { S_RR = 0, S_PAP, S_ALPHA, S_BETA, S_SRC2, S_ACTIVE, S_STATUS, S_AUX, S_ITERS, S_NUM };
+constexpr int kMaxRhs = 64;
+constexpr int kRedThreads = 256;
+#define SC(k, r) sc[(k) * kMaxRhs + (r)]
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double ws[32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) ws[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    v = (threadIdx.x < nw) ? ws[lane] : 0.0;
+    if (wid == 0) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    }
+    return v;
+}
+
+#define SITE_LOOP(g)                                                                                 \
+    const long long n5 = (g).Vh * (g).Ls;                                                            \
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n5;                     \
+         i += (long long)gridDim.x * blockDim.x)
+
+// |a|^2 per right-hand side -> partials
+template <int PA>
+__global__ void __launch_bounds__(kRedThreads) k_norm(Field<PA> a, double* part, Geom g, const double* sc) {
+    typedef typename PrecTraits<PA>::real RA;
+    const int rhs = blockIdx.y;
+    double acc = 0;
+    if (!sc || SC(S_ACTIVE, rhs) != 0.0) {
+        SITE_LOOP(g) {
+            const int s = (int)(i % g.Ls);
+            const long long sr = rhs * g.Vh + i / g.Ls;
+            RA v[24];
+            a.load(sr, s, v);
+#pragma unroll
+            for (int k = 0; k < 24; ++k) acc += (double)v[k] * (double)v[k];
+        }
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[rhs * gridDim.x + blockIdx.x] = acc;
+}
+
+enum { FIN_STORE = 0, FIN_ALPHA = 1, FIN_BETA = 2 };
+
+__global__ void k_finalize(const double* part, int nb, double* sc, int mode, int slot) {
+    const int rhs = blockIdx.x;
+    double v = 0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) v += part[rhs * nb + i];
+    v = block_sum(v);
+    if (threadIdx.x != 0) return;
+    const bool active = SC(S_ACTIVE, rhs) != 0.0;
+    if (mode == FIN_STORE) {
+        SC(slot, rhs) = v;
+    } else if (mode == FIN_ALPHA) {
+        SC(S_PAP, rhs) = v;
+        double a = 0.0;
+        if (active) {
+            if (!(v > 0.0) || !isfinite(v)) {
+                SC(S_STATUS, rhs) = (double)MDWF_EBREAKDOWN;
+                SC(S_ACTIVE, rhs) = 0.0;
+            } else {
+                a = SC(S_RR, rhs) / v;
+            }
+        }
+        SC(S_ALPHA, rhs) = a;
+    } else {  // FIN_BETA: v = |r_new|^2
+        double b = 0.0;
+        if (active) {
+            if (!isfinite(v)) {
+                SC(S_STATUS, rhs) = (double)MDWF_EBREAKDOWN;
+                SC(S_ACTIVE, rhs) = 0.0;
+            } else {
+                b = v / SC(S_RR, rhs);
+                SC(S_RR, rhs) = v;
+                SC(S_ITERS, rhs) += 1.0;
+            }
+        }
+        SC(S_BETA, rhs) = b;
+    }
+}
+
+// x += alpha p; r -= alpha ap; partial |r|^2
+template <int PX, int PR, int PP>
+__global__ void __launch_bounds__(kRedThreads) k_update(Field<PX> x, Field<PR> r, Field<PP> p, Field<PP> ap,
+                                                       double* part, const double* sc, Geom g) {
+    typedef typename PrecTraits<PX>::real RX;
+    typedef typename PrecTraits<PR>::real RR;
+    typedef typename PrecTraits<PP>::real RP;
+    const int rhs = blockIdx.y;
+    double acc = 0;
+    if (SC(S_ACTIVE, rhs) != 0.0) {
+        const double alpha = SC(S_ALPHA, rhs);
+        SITE_LOOP(g) {
+            const int s = (int)(i % g.Ls);
+            const long long sr = rhs * g.Vh + i / g.Ls;
+            RX xv[24];
+            RR rv[24];
+            RP pv[24], av[24];
+            x.load(sr, s, xv);
+            r.load(sr, s, rv);
+            p.load(sr, s, pv);
+            ap.load(sr, s, av);
+#pragma unroll
+            for (int k = 0; k < 24; ++k) {
+                xv[k] += (RX)alpha * (RX)pv[k];
+                rv[k] -= (RR)alpha * (RR)av[k];
+                acc += (double)rv[k] * (double)rv[k];
+            }
+            x.store(sr, s, xv);
+            r.store(sr, s, rv);
+        }
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[rhs * gridDim.x + blockIdx.x] = acc;
+}
+
+// p = r + beta p
+template <int PR, int PP>
+__global__ void __launch_bounds__(kRedThreads) k_pupdate(Field<PP> p, Field<PR> r, const double* sc, Geom g) {
+    typedef typename PrecTraits<PR>::real RR;
+    typedef typename PrecTraits<PP>::real RP;
+    const int rhs = blockIdx.y;
+    if (SC(S_ACTIVE, rhs) == 0.0) return;
+    const RP beta = (RP)SC(S_BETA, rhs);
+    SITE_LOOP(g) {
+        const int s = (int)(i % g.Ls);
+        const long long sr = rhs * g.Vh + i / g.Ls;
+        RR rv[24];
+        RP pv[24];
+        r.load(sr, s, rv);
+        p.load(sr, s, pv);
+#pragma unroll
+        for (int k = 0; k < 24; ++k) pv[k] = (RP)rv[k] + beta * pv[k];
+        p.store(sr, s, pv);
+    }
+}
+
+// dst = src (precision conversion); only active right-hand sides when sc != null
+template <int PD, int PS>
+__global__ void __launch_bounds__(kRedThreads) k_copy(Field<PD> d, Field<PS> src, const double* sc, Geom g) {
+    typedef typename PrecTraits<PD>::real RD;
+    typedef typename PrecTraits<PS>::real RS;
+    const int rhs = blockIdx.y;
+    if (sc && SC(S_ACTIVE, rhs) == 0.0) return;
+    SITE_LOOP(g) {
+        const int s = (int)(i % g.Ls);
+        const long long sr = rhs * g.Vh + i / g.Ls;
+        RS v[24];
+        RD w[24];
+        src.load(sr, s, v);
+#pragma unroll
+        for (int k = 0; k < 24; ++k) w[k] = (RD)v[k];
+        d.store(sr, s, w);
+    }
+}
+
+// y += x; x = 0 (active right-hand sides)
+template <int PY, int PX>
+__global__ void __launch_bounds__(kRedThreads) k_accum_zero(Field<PY> y, Field<PX> x, const double* sc, Geom g) {
+    typedef typename PrecTraits<PY>::real RY;
+    typedef typename PrecTraits<PX>::real RX;
+    const int rhs = blockIdx.y;
+    if (SC(S_ACTIVE, rhs) == 0.0) return;
+    SITE_LOOP(g) {
+        const int s = (int)(i % g.Ls);
+        const long long sr = rhs * g.Vh + i / g.Ls;
+        RY yv[24];
+        RX xv[24];
+        y.load(sr, s, yv);
+        x.load(sr, s, xv);
+#pragma unroll
+        for (int k = 0; k < 24; ++k) {
+            yv[k] += (RY)xv[k];
+            xv[k] = 0;
+        }
+        y.store(sr, s, yv);
+        x.store(sr, s, xv);
+    }
+}
+
+// r = a - b (FP64), optional low-precision copy rs = r; partial |r|^2
+template <int PS, bool COPY>
+__global__ void __launch_bounds__(kRedThreads) k_residual(Field<MDWF_F64> r, Field<PS> rs, Field<MDWF_F64> a,
+                                                         Field<MDWF_F64> b, double* part, const double* sc,
+                                                         Geom g) {
+    typedef typename PrecTraits<PS>::real RS;
+    const int rhs = blockIdx.y;
+    double acc = 0;
+    if (!sc || SC(S_ACTIVE, rhs) != 0.0) {
+        SITE_LOOP(g) {
+            const int s = (int)(i % g.Ls);
+            const long long sr = rhs * g.Vh + i / g.Ls;
+            double av[24], bv[24];
+            a.load(sr, s, av);
+            b.load(sr, s, bv);
+#pragma unroll
+            for (int k = 0; k < 24; ++k) {
+                av[k] -= bv[k];
+                acc += av[k] * av[k];
+            }
+            r.store(sr, s, av);
+            if (COPY) {
+                RS w[24];
+#pragma unroll
+                for (int k = 0; k < 24; ++k) w[k] = (RS)av[k];
+                rs.store(sr, s, w);
+            }
+        }
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[rhs * gridDim.x + blockIdx.x] = acc;
+}
+
+// ------------------------------------------------------------------ solver
+
+namespace {
+
+struct Solver {
+    mdwf_ctx* c;
+    Geom g;
+    int nrhs;
+    int nb;             // reduction blocks per right-hand side
+    double* sc;         // device scalars [S_NUM][kMaxRhs]
+    double* part;       // device partials [nrhs][nb]
+    double* hsc;        // pinned host copy of sc
+
+    dim3 grid() const { return dim3(nb, nrhs); }
+
+    double n5() const { return (double)g.Vh * g.Ls * nrhs; }
+    int fin(int mode, int slot = 0) {
+        LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, 8.0 * nrhs * nb, 0.0);
+        k_finalize<<<nrhs, kRedThreads, 0, c->stream>>>(part, nb, sc, mode, slot);
+        return check_launch();
+    }
+    template <int P>
+    int norm(const void* a, bool masked, int slot) {
+        {
+        LaunchScope scope(c, KB_BLAS * 3 + P, n5() * site_bytes(P), n5() * 48.0);
+        k_norm<P><<<grid(), kRedThreads, 0, c->stream>>>(make_field<P>(const_cast<void*>(a), g, nrhs), part, g,
+                                                         masked ? sc : nullptr);
+        }
+        int st = check_launch();
+        return st ? st : fin(FIN_STORE, slot);
+    }
+    template <int PD, int PS>
+    int copy(void* d, const void* s, bool masked) {
+        LaunchScope scope(c, KB_BLAS * 3 + PD, n5() * (site_bytes(PS) + site_bytes(PD)), 0.0);
+        k_copy<PD, PS><<<grid(), kRedThreads, 0, c->stream>>>(make_field<PD>(d, g, nrhs),
+                                                               make_field<PS>(const_cast<void*>(s), g, nrhs),
+                                                               masked ? sc : nullptr, g);
+        return check_launch();
+    }
+    int pull() {
+        int st = cuda_status(cudaMemcpyAsync(hsc, sc, sizeof(double) * S_NUM * kMaxRhs, cudaMemcpyDeviceToHost,
+                                             c->stream));
+        return st ? st : cuda_status(cudaStreamSynchronize(c->stream));
+    }
+    int push() {
+        return cuda_status(cudaMemcpyAsync(sc, hsc, sizeof(double) * S_NUM * kMaxRhs, cudaMemcpyHostToDevice,
+                                           c->stream));
+    }
+};
+
+void begin_capture(mdwf_ctx* c) {
+    c->capturing = true;
+    c->cap_launches = 0;
+    for (int p = 0; p < 3; ++p) c->cap_applies[p] = 0;
+    for (int k = 0; k < KK_NUM; ++k) c->cap_kstat[k] = KStat{};
+}
+
+}  // namespace
+
+// one CG iteration on fields of operator precision PP, residual/solution precision PR
+template <int PR, int PP>
+static int cg_iteration(Solver& S, void* x, void* r, void* p, void* t, void* ap) {
+    mdwf_ctx* c = S.c;
+    int st;
+    if ((st = apply_op(c, t, p, PP, S.nrhs, 0))) return st;
+    if ((st = apply_op(c, ap, t, PP, S.nrhs, 1))) return st;
+    {
+        LaunchScope scope(c, KB_BLAS * 3 + PP, S.n5() * site_bytes(PP), S.n5() * 48.0);
+        k_norm<PP><<<S.grid(), kRedThreads, 0, c->stream>>>(make_field<PP>(t, S.g, S.nrhs), S.part, S.g, S.sc);
+    }
+    if ((st = check_launch())) return st;
+    if ((st = S.fin(FIN_ALPHA))) return st;
+    {
+    LaunchScope scope(c, KB_BLAS * 3 + PP, S.n5() * (4.0 * site_bytes(PR) + 2.0 * site_bytes(PP)), S.n5() * 144.0);
+    k_update<PR, PR, PP><<<S.grid(), kRedThreads, 0, c->stream>>>(
+        make_field<PR>(x, S.g, S.nrhs), make_field<PR>(r, S.g, S.nrhs), make_field<PP>(p, S.g, S.nrhs),
+        make_field<PP>(ap, S.g, S.nrhs), S.part, S.sc, S.g);
+    }
+    if ((st = check_launch())) return st;
+    if ((st = S.fin(FIN_BETA))) return st;
+    LaunchScope scope(c, KB_BLAS * 3 + PP, S.n5() * (site_bytes(PR) + 2.0 * site_bytes(PP)), S.n5() * 48.0);
+    k_pupdate<PR, PP><<<S.grid(), kRedThreads, 0, c->stream>>>(make_field<PP>(p, S.g, S.nrhs),
+                                                                make_field<PR>(r, S.g, S.nrhs), S.sc, S.g);
+    return check_launch();
+}
+
+// r = src - M^dag M x in FP64 (active rhs), r_s = r in precision PS; |r|^2 -> S_AUX
+template <int PS, bool COPY>
+static int true_residual(Solver& S, void* r, void* rs, const void* src, const void* x, void* t64, void* ap64,
+                         bool masked) {
+    int st;
+    if ((st = apply_op(S.c, t64, x, MDWF_F64, S.nrhs, 0))) return st;
+    if ((st = apply_op(S.c, ap64, t64, MDWF_F64, S.nrhs, 1))) return st;
+    {
+    LaunchScope scope(S.c, KB_BLAS * 3 + MDWF_F64, S.n5() * (3.0 * 192.0 + (COPY ? site_bytes(PS) : 0.0)), S.n5() * 48.0);
+    k_residual<PS, COPY><<<S.grid(), kRedThreads, 0, S.c->stream>>>(
+        make_field<MDWF_F64>(r, S.g, S.nrhs), make_field<PS>(rs ? rs : r, S.g, S.nrhs),
+        make_field<MDWF_F64>(const_cast<void*>(src), S.g, S.nrhs), make_field<MDWF_F64>(ap64, S.g, S.nrhs), S.part,
+        masked ? S.sc : nullptr, S.g);
+    }
+    if ((st = check_launch())) return st;
+    return S.fin(FIN_STORE, S_AUX);
+}
+
+struct Fields {
+    // FP64
+    void *be, *bp, *xo, *xe, *r, *src, *t64, *ap64, *stage_b, *stage_x;
+    // inner
+    void *xs, *rs, *p, *t, *ap;
+};
+
+template <int PP>
+static int run_mixed(Solver& S, Fields& F, const mdwf_solve_params& prm, double tol, int maxiter,
+                     std::vector<double>& maxr, std::vector<int>& rupd, cudaGraphExec_t* gexec, bool use_graph) {
+    mdwf_ctx* c = S.c;
+    const int nrhs = S.nrhs;
+    int st;
+    // r = src (x = 0), r_s = r, x_s = 0, p = r_s
+    if ((st = S.copy<MDWF_F64, MDWF_F64>(F.r, F.src, false))) return st;
+    if ((st = S.copy<MDWF_F32, MDWF_F64>(F.rs, F.src, false))) return st;
+    if ((st = cuda_status(cudaMemsetAsync(F.xs, 0, field_bytes(MDWF_F32, S.g, nrhs), c->stream)))) return st;
+    if ((st = S.copy<PP, MDWF_F64>(F.p, F.src, false))) return st;
+    if ((st = S.norm<MDWF_F64>(F.src, false, S_RR))) return st;
+    if ((st = S.pull())) return st;
+    for (int r = 0; r < nrhs; ++r) maxr[r] = sqrt(S.hsc[S_RR * kMaxRhs + r]);
+    const double delta = prm.delta > 0 ? prm.delta : 0.1;
+    const int every = prm.check_every > 0 ? prm.check_every : 8;
+    int it = 0;
+    bool graph_ready = false;
+    while (it < maxiter) {
+        const int steps = (maxiter - it) < every ? (maxiter - it) : every;
+        if (use_graph) {
+            if (!graph_ready) {
+                cudaGraph_t graph;
+                if ((st = cuda_status(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal)))) return st;
+                begin_capture(c);
+                int st2 = cg_iteration<MDWF_F32, PP>(S, F.xs, F.rs, F.p, F.t, F.ap);
+                c->capturing = false;
+                st = cuda_status(cudaStreamEndCapture(c->stream, &graph));
+                if (st2) return st2;
+                if (st) return st;
+                st = cuda_status(cudaGraphInstantiate(gexec, graph, 0));
+                cudaGraphDestroy(graph);
+                if (st) return st;
+                graph_ready = true;
+            }
+            for (int k = 0; k < steps; ++k) {
+                if ((st = cuda_status(cudaGraphLaunch(*gexec, c->stream)))) return st;
+                replay_graph_counts(c, 1);
+            }
+        } else {
+            for (int k = 0; k < steps; ++k)
+                if ((st = cg_iteration<MDWF_F32, PP>(S, F.xs, F.rs, F.p, F.t, F.ap))) return st;
+        }
+        it += steps;
+        if ((st = S.pull())) return st;
+        bool any_active = false, need_update = false;
+        for (int r = 0; r < nrhs; ++r) {
+            if (S.hsc[S_ACTIVE * kMaxRhs + r] == 0.0) continue;
+            any_active = true;
+            const double rr = S.hsc[S_RR * kMaxRhs + r];
+            const double src2 = S.hsc[S_SRC2 * kMaxRhs + r];
+            const double rn = sqrt(rr);
+            if (rn < delta * maxr[r] || rr <= tol * tol * src2 || it >= maxiter) need_update = true;
+            if (rn > maxr[r]) maxr[r] = rn;
+        }
+        if (!any_active) break;
+        if (!need_update) continue;
+        // reliable update: x += x_s, x_s = 0, r = src - M^dag M x (FP64), r_s = r
+        {
+            LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, S.n5() * (2.0 * 192.0 + 2.0 * 96.0), S.n5() * 24.0);
+            k_accum_zero<MDWF_F64, MDWF_F32><<<S.grid(), kRedThreads, 0, c->stream>>>(
+                make_field<MDWF_F64>(F.xo, S.g, nrhs), make_field<MDWF_F32>(F.xs, S.g, nrhs), S.sc, S.g);
+        }
+        if ((st = check_launch())) return st;
+        if ((st = true_residual<MDWF_F32, true>(S, F.r, F.rs, F.src, F.xo, F.t64, F.ap64, true))) return st;
+        if ((st = S.pull())) return st;
+        for (int r = 0; r < nrhs; ++r) {
+            if (S.hsc[S_ACTIVE * kMaxRhs + r] == 0.0) continue;
+            rupd[r] += 1;
+            const double rr = S.hsc[S_AUX * kMaxRhs + r];
+            const double src2 = S.hsc[S_SRC2 * kMaxRhs + r];
+            S.hsc[S_RR * kMaxRhs + r] = rr;
+            maxr[r] = sqrt(rr);
+            if (rr <= tol * tol * src2) S.hsc[S_ACTIVE * kMaxRhs + r] = 0.0;
+        }
+        if ((st = S.push())) return st;
+    }
+    return MDWF_OK;
+}
+
+static int run_plain(Solver& S, Fields& F, const mdwf_solve_params& prm, double tol, int maxiter,
+                     cudaGraphExec_t* gexec, bool use_graph) {
+    mdwf_ctx* c = S.c;
+    const int nrhs = S.nrhs;
+    int st;
+    const int every = prm.check_every > 0 ? prm.check_every : 8;
+    int it = 0;
+    bool graph_ready = false;
+    for (;;) {
+        // (re)start from the true residual of the current x
+        if ((st = true_residual<MDWF_F64, false>(S, F.r, nullptr, F.src, F.xo, F.t64, F.ap64, true))) return st;
+        if ((st = S.pull())) return st;
+        bool any = false;
+        for (int r = 0; r < nrhs; ++r) {
+            if (S.hsc[S_ACTIVE * kMaxRhs + r] == 0.0) continue;
+            const double rr = S.hsc[S_AUX * kMaxRhs + r];
+            S.hsc[S_RR * kMaxRhs + r] = rr;
+            if (rr <= tol * tol * S.hsc[S_SRC2 * kMaxRhs + r]) S.hsc[S_ACTIVE * kMaxRhs + r] = 0.0;
+            else any = true;
+        }
+        if ((st = S.push())) return st;
+        if (!any || it >= maxiter) break;
+        if ((st = S.copy<MDWF_F64, MDWF_F64>(F.p, F.r, true))) return st;
+        while (it < maxiter) {
+            const int steps = (maxiter - it) < every ? (maxiter - it) : every;
+            if (use_graph) {
+                if (!graph_ready) {
+                    cudaGraph_t graph;
+                    if ((st = cuda_status(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal))))
+                        return st;
+                    begin_capture(c);
+                    int st2 = cg_iteration<MDWF_F64, MDWF_F64>(S, F.xo, F.r, F.p, F.t, F.ap);
+                    c->capturing = false;
+                    st = cuda_status(cudaStreamEndCapture(c->stream, &graph));
+                    if (st2) return st2;
+                    if (st) return st;
+                    st = cuda_status(cudaGraphInstantiate(gexec, graph, 0));
+                    cudaGraphDestroy(graph);
+                    if (st) return st;
+                    graph_ready = true;
+                }
+                for (int k = 0; k < steps; ++k) {
+                    if ((st = cuda_status(cudaGraphLaunch(*gexec, c->stream)))) return st;
+                    replay_graph_counts(c, 1);
+                }
+            } else {
+                for (int k = 0; k < steps; ++k)
+                    if ((st = cg_iteration<MDWF_F64, MDWF_F64>(S, F.xo, F.r, F.p, F.t, F.ap))) return st;
+            }
+            it += steps;
+            if ((st = S.pull())) return st;
+            bool active_left = false, reached = false;
+            for (int r = 0; r < nrhs; ++r) {
+                if (S.hsc[S_ACTIVE * kMaxRhs + r] == 0.0) continue;
+                active_left = true;
+                if (S.hsc[S_RR * kMaxRhs + r] <= tol * tol * S.hsc[S_SRC2 * kMaxRhs + r]) reached = true;
+            }
+            if (!active_left || reached) break;
+        }
+    }
+    return MDWF_OK;
+}
+
+}  // namespace mdwf
+
+using namespace mdwf;
+
+extern "C" int mdwf_cgne(mdwf_ctx* c, double* x, const double* b, int nrhs, const double* mf_per_rhs, int where,
+                         const mdwf_solve_params* params, mdwf_solve_info* info) {
+    auto t0 = std::chrono::steady_clock::now();
+    if (!c || !x || !b || nrhs < 1 || nrhs > kMaxRhs || (where != MDWF_HOST && where != MDWF_DEVICE))
+        return MDWF_EINVAL;
+    if (!c->have_gauge) return MDWF_ENOGAUGE;
+    mdwf_solve_params prm{};
+    if (params) prm = *params;
+    const double tol = prm.tol > 0 ? prm.tol : 1e-10;
+    const int maxiter = prm.maxiter > 0 ? prm.maxiter : 20000;
+    const int inner = prm.inner_prec;
+    if (inner != MDWF_F64 && inner != MDWF_F32 && inner != MDWF_F16N) return MDWF_EINVAL;
+    int st;
+    if ((st = cuda_status(cudaSetDevice(c->device)))) return st;
+    if ((st = ensure_tables(c, nrhs, mf_per_rhs))) return st;
+
+    // a captured graph needs a stream other than the legacy default one
+    cudaStream_t user_stream = c->stream, own = nullptr;
+    const bool use_graph = prm.use_graph != 0 && !c->prof_on;
+    if (use_graph && user_stream == nullptr) {
+        if ((st = cuda_status(cudaStreamCreate(&own)))) return st;
+        c->stream = own;
+    }
+
+    const Geom g = c->g;
+    const size_t f64 = field_bytes(MDWF_F64, g, nrhs), f32 = field_bytes(MDWF_F32, g, nrhs);
+    const size_t fpp = field_bytes(inner, g, nrhs);
+    const size_t full = (size_t)nrhs * g.Ls * 2 * g.Vh * 24 * sizeof(double);
+    const size_t align = 256;
+    auto up = [&](size_t v) { return (v + align - 1) / align * align; };
+    const int nb = 2 * 152;
+    size_t need = up(f64) * 8 + (inner == MDWF_F64 ? up(f64) * 3 : up(f32) * 2 + up(fpp) * 3) +
+                  (where == MDWF_HOST ? 2 * up(full) : 0) + up(sizeof(double) * S_NUM * kMaxRhs) +
+                  up(sizeof(double) * nrhs * nb);
+    Fields F{};
+    Solver S{};
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<double> maxr(nrhs, 0.0);
+    std::vector<int> rupd(nrhs, 0);
+    double* hsc = nullptr;
+    int ret = MDWF_OK;
+    do {
+        if ((st = ensure_workspace(c->solver, need))) { ret = st; break; }
+        // the apply temporaries for both precisions used below
+        if ((st = ensure_workspace(c->tmp[0], f64)) || (st = ensure_workspace(c->tmp[1], f64))) { ret = st; break; }
+        char* w = (char*)c->solver.p;
+        auto take = [&](size_t bytes) { void* p = w; w += up(bytes); return p; };
+        F.be = take(f64); F.bp = take(f64); F.xo = take(f64); F.xe = take(f64);
+        F.r = take(f64); F.src = take(f64); F.t64 = take(f64); F.ap64 = take(f64);
+        if (inner == MDWF_F64) {
+            F.p = take(f64); F.t = take(f64); F.ap = take(f64);
+        } else {
+            F.xs = take(f32); F.rs = take(f32); F.p = take(fpp); F.t = take(fpp); F.ap = take(fpp);
+        }
+        if (where == MDWF_HOST) { F.stage_b = take(full); F.stage_x = take(full); }
+        S.c = c; S.g = g; S.nrhs = nrhs; S.nb = nb;
+        S.sc = (double*)take(sizeof(double) * S_NUM * kMaxRhs);
+        S.part = (double*)take(sizeof(double) * nrhs * nb);
+        if ((st = cuda_status(cudaMallocHost(&hsc, sizeof(double) * S_NUM * kMaxRhs)))) { ret = st; break; }
+        S.hsc = hsc;
+        memset(hsc, 0, sizeof(double) * S_NUM * kMaxRhs);
+        for (int r = 0; r < nrhs; ++r) hsc[S_ACTIVE * kMaxRhs + r] = 1.0;
+        if ((st = S.push())) { ret = st; break; }
+
+        // source: b -> (b_e, b_o)
+        const double* bdev = b;
+        if (where == MDWF_HOST) {
+            if ((st = cuda_status(cudaMemcpyAsync(F.stage_b, b, full, cudaMemcpyHostToDevice, c->stream)))) { ret = st; break; }
+            bdev = (const double*)F.stage_b;
+        }
+        if ((st = launch_split_full(c, F.be, F.bp, bdev, MDWF_F64, nrhs))) { ret = st; break; }
+        // b'_o = A b_o + 1/2 A H_oe M_phi (A b_e), A = I^-1 (D_br = -1/2 H_oe M_phi)
+        M5Launch m{};
+        m.nrhs = nrhs; m.coef = 1.0; m.x = nullptr; m.mat = table_ptr(c, MDWF_F64, T_A);
+        m.out = F.xe; m.in = F.be;
+        if ((st = launch_m5(c, MDWF_F64, m))) { ret = st; break; }
+        m.out = F.r; m.in = F.bp;
+        if ((st = launch_m5(c, MDWF_F64, m))) { ret = st; break; }
+        HopLaunch h{};
+        h.nrhs = nrhs; h.b5 = c->b5; h.c5 = c->c5; h.mass = c->mass64;
+        h.out = F.bp; h.in = F.xe; h.x = F.r; h.coef = 0.5; h.out_parity = 1; h.gather = 1; h.dagger = 0;
+        h.mat = table_ptr(c, MDWF_F64, T_A);
+        if ((st = launch_hop(c, MDWF_F64, h))) { ret = st; break; }
+        // src = M^dag b', |src|^2
+        if ((st = apply_op(c, F.src, F.bp, MDWF_F64, nrhs, 1))) { ret = st; break; }
+        if ((st = S.norm<MDWF_F64>(F.src, false, S_SRC2))) { ret = st; break; }
+        if ((st = cuda_status(cudaMemsetAsync(F.xo, 0, f64, c->stream)))) { ret = st; break; }
+        // zero-source right-hand sides are solved by x = 0
+        if ((st = S.pull())) { ret = st; break; }
+        for (int r = 0; r < nrhs; ++r)
+            if (S.hsc[S_SRC2 * kMaxRhs + r] == 0.0) S.hsc[S_ACTIVE * kMaxRhs + r] = 0.0;
+        if ((st = S.push())) { ret = st; break; }
+
+        if (inner == MDWF_F64) st = run_plain(S, F, prm, tol, maxiter, &gexec, use_graph);
+        else if (inner == MDWF_F32) st = run_mixed<MDWF_F32>(S, F, prm, tol, maxiter, maxr, rupd, &gexec, use_graph);
+        else st = run_mixed<MDWF_F16N>(S, F, prm, tol, maxiter, maxr, rupd, &gexec, use_graph);
+        if (st) { ret = st; break; }
+
+        // final FP64 residuals for every right-hand side
+        std::vector<double> keep_active(nrhs), status(nrhs), iters(nrhs), src2(nrhs);
+        if ((st = S.pull())) { ret = st; break; }
+        for (int r = 0; r < nrhs; ++r) {
+            keep_active[r] = S.hsc[S_ACTIVE * kMaxRhs + r];
+            status[r] = S.hsc[S_STATUS * kMaxRhs + r];
+            iters[r] = S.hsc[S_ITERS * kMaxRhs + r];
+            src2[r] = S.hsc[S_SRC2 * kMaxRhs + r];
+        }
+        if ((st = true_residual<MDWF_F64, false>(S, F.r, nullptr, F.src, F.xo, F.t64, F.ap64, false))) { ret = st; break; }
+        if ((st = S.pull())) { ret = st; break; }
+        std::vector<double> rel(nrhs);
+        for (int r = 0; r < nrhs; ++r) rel[r] = src2[r] > 0 ? sqrt(S.hsc[S_AUX * kMaxRhs + r] / src2[r]) : 0.0;
+        // |b' - M x| / |b'|
+        if ((st = apply_op(c, F.t64, F.xo, MDWF_F64, nrhs, 0))) { ret = st; break; }
+        {
+        LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, S.n5() * 3.0 * 192.0, S.n5() * 48.0);
+        k_residual<MDWF_F64, false><<<S.grid(), kRedThreads, 0, c->stream>>>(
+            make_field<MDWF_F64>(F.ap64, g, nrhs), make_field<MDWF_F64>(F.ap64, g, nrhs),
+            make_field<MDWF_F64>(F.bp, g, nrhs), make_field<MDWF_F64>(F.t64, g, nrhs), S.part, nullptr, g);
+        }
+        if ((st = check_launch()) || (st = S.fin(FIN_STORE, S_AUX))) { ret = st; break; }
+        if ((st = S.norm<MDWF_F64>(F.bp, false, S_PAP))) { ret = st; break; }
+        if ((st = S.pull())) { ret = st; break; }
+
+        // x_e = A b_e + 1/2 A H_eo M_phi x_o
+        h.out = F.t64; h.in = F.xo; h.x = nullptr; h.coef = 0.5; h.out_parity = 0; h.gather = 1; h.dagger = 0;
+        h.mat = table_ptr(c, MDWF_F64, T_A);
+        if ((st = launch_hop(c, MDWF_F64, h))) { ret = st; break; }
+        m.out = F.xe; m.in = F.be; m.x = F.t64; m.coef = 1.0; m.mat = table_ptr(c, MDWF_F64, T_A);
+        if ((st = launch_m5(c, MDWF_F64, m))) { ret = st; break; }
+        double* xdev = where == MDWF_HOST ? (double*)F.stage_x : x;
+        if ((st = launch_join_full(c, xdev, F.xe, F.xo, MDWF_F64, nrhs))) { ret = st; break; }
+        if (where == MDWF_HOST &&
+            (st = cuda_status(cudaMemcpyAsync(x, F.stage_x, full, cudaMemcpyDeviceToHost, c->stream)))) {
+            ret = st;
+            break;
+        }
+        if ((st = cuda_status(cudaStreamSynchronize(c->stream)))) { ret = st; break; }
+        const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        for (int r = 0; r < nrhs; ++r) {
+            int rs = (int)status[r];
+            if (rs == MDWF_OK && rel[r] > tol) rs = MDWF_ENOCONV;
+            if (rs > ret) ret = rs;
+            if (info) {
+                info[r].status = rs;
+                info[r].iters = (int)iters[r];
+                info[r].reliable_updates = rupd[r];
+                info[r].true_res = rel[r];
+                const double bb = S.hsc[S_PAP * kMaxRhs + r];
+                info[r].res_m = bb > 0 ? sqrt(S.hsc[S_AUX * kMaxRhs + r] / bb) : 0.0;
+                info[r].seconds = secs;
+            }
+        }
+        (void)keep_active;
+    } while (0);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (hsc) cudaFreeHost(hsc);
+    if (own) {
+        cudaStreamSynchronize(own);
+        cudaStreamDestroy(own);
+        c->stream = user_stream;
+    }
+    return ret;
+}

@@ -1,0 +1,287 @@
+// Fused hopping kernel of the red/black Moebius operator.
+//
+// One launch computes, for every site x of parity `out_parity` and every s,
+//   out(x, s) = coef * sum_s' Mat_chi(s, s') [H w](x, s') (+ x_add(x, s))
+// where H is the Wilson hopping sum of Eq. (D^Wilson),
+//   H w(x) = sum_mu [(1 - g_mu) U_mu(x) w(x+mu) + (1 + g_mu) U_mu(x-mu)^dag w(x-mu)]
+// (projector signs flipped for the hopping part of D_W^dag), and w is either
+// the input field or the input with the fifth-dimension gather of Sec. 5
+// applied first: w_s = b5 psi_s + c5 (P+ psi_{s-1} + P- psi_{s+1}) with the
+// mass -m on the wrap-around terms (Eq. DWaction), i.e. w = M_phi psi.
+// Mat is an Ls x Ls real matrix per chirality (K = M_phi I^-1, I^-1, ...).
+//
+// Thread mapping: a block is Ls x SB threads: threadIdx.x = s, threadIdx.y =
+// one of SB 4d sites, blockIdx.y = right-hand side. The Ls threads of a
+// column load the same link (one L1 line, broadcast), so each link is read
+// from HBM once per hop and reused across all Ls slices. Spinor chunks of
+// consecutive s are contiguous, so every vector load of a warp is coalesced.
+// The s-mixing matrix is applied after the hop through shared memory.
+#include "mdwf_internal.cuh"
+
+namespace mdwf {
+
+template <typename R> struct HopParams {
+    Geom g;
+    int out_parity;
+    R coef, b5, c5;
+    const R* mass;  // [rhs]
+    const R* mat;   // [rhs][chir][s'][s]
+};
+
+// --------------------------------------------------------- spin structure
+//
+// Chiral basis g_mu = [[0, A_mu], [A_mu^dag, 0]], A_k = -i sigma_k, A_4 = 1.
+// (1 + S g_mu) psi, psi = (u, l) by chirality halves, has upper half
+// h = u + S A l and lower half S A^dag h, so only h (2 spins x 3 colours) is
+// transported: project -> multiply by the link -> reconstruct.
+
+template <int MU, int S, typename R>
+__device__ __forceinline__ void project(const R* w, R* h) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const R u0r = w[2 * c], u0i = w[2 * c + 1], u1r = w[6 + 2 * c], u1i = w[7 + 2 * c];
+        const R l0r = w[12 + 2 * c], l0i = w[13 + 2 * c], l1r = w[18 + 2 * c], l1i = w[19 + 2 * c];
+        R a0r, a0i, a1r, a1i;  // (A l)_0, (A l)_1
+        if (MU == 0) {         // A = -i sigma_1: (A l)_0 = -i l1, (A l)_1 = -i l0
+            a0r = l1i; a0i = -l1r; a1r = l0i; a1i = -l0r;
+        } else if (MU == 1) {  // A = -i sigma_2: (A l)_0 = -l1, (A l)_1 = l0
+            a0r = -l1r; a0i = -l1i; a1r = l0r; a1i = l0i;
+        } else if (MU == 2) {  // A = -i sigma_3: (A l)_0 = -i l0, (A l)_1 = i l1
+            a0r = l0i; a0i = -l0r; a1r = -l1i; a1i = l1r;
+        } else {               // A = 1
+            a0r = l0r; a0i = l0i; a1r = l1r; a1i = l1i;
+        }
+        h[2 * c] = u0r + S * a0r;
+        h[2 * c + 1] = u0i + S * a0i;
+        h[6 + 2 * c] = u1r + S * a1r;
+        h[7 + 2 * c] = u1i + S * a1i;
+    }
+}
+
+template <int MU, int S, typename R>
+__device__ __forceinline__ void reconstruct_add(R* acc, const R* g) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const R g0r = g[2 * c], g0i = g[2 * c + 1], g1r = g[6 + 2 * c], g1i = g[7 + 2 * c];
+        acc[2 * c] += g0r;
+        acc[2 * c + 1] += g0i;
+        acc[6 + 2 * c] += g1r;
+        acc[7 + 2 * c] += g1i;
+        R b0r, b0i, b1r, b1i;  // (A^dag g)_0, (A^dag g)_1
+        if (MU == 0) {         // A^dag = i sigma_1: (i g1, i g0)
+            b0r = -g1i; b0i = g1r; b1r = -g0i; b1i = g0r;
+        } else if (MU == 1) {  // A^dag = i sigma_2: (g1, -g0)
+            b0r = g1r; b0i = g1i; b1r = -g0r; b1i = -g0i;
+        } else if (MU == 2) {  // A^dag = i sigma_3: (i g0, -i g1)
+            b0r = -g0i; b0i = g0r; b1r = g1i; b1i = -g1r;
+        } else {
+            b0r = g0r; b0i = g0i; b1r = g1r; b1i = g1i;
+        }
+        acc[12 + 2 * c] += S * b0r;
+        acc[13 + 2 * c] += S * b0i;
+        acc[18 + 2 * c] += S * b1r;
+        acc[19 + 2 * c] += S * b1i;
+    }
+}
+
+// g[a][i] = sum_j V[i][j] h[a][j], V = U or U^dag; U row-major complex 3x3
+template <bool ADJ, typename R>
+__device__ __forceinline__ void su3_mul(const R* U, const R* h, R* g) {
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            R sr = 0, si = 0;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const R ur = ADJ ? U[2 * (3 * j + i)] : U[2 * (3 * i + j)];
+                const R ui = ADJ ? -U[2 * (3 * j + i) + 1] : U[2 * (3 * i + j) + 1];
+                const R hr = h[6 * a + 2 * j], hi = h[6 * a + 2 * j + 1];
+                sr += ur * hr - ui * hi;
+                si += ur * hi + ui * hr;
+            }
+            g[6 * a + 2 * i] = sr;
+            g[6 * a + 2 * i + 1] = si;
+        }
+}
+
+// w = psi(s) or M_phi psi at s for the neighbour column sr
+template <int P, bool GATHER, typename R>
+__device__ __forceinline__ void load_input(const Field<P>& in, long long sr, int s, int Ls, R b5, R c5,
+                                           R mass, R* w) {
+    in.load(sr, s, w);
+    if (GATHER) {
+#pragma unroll
+        for (int k = 0; k < 24; ++k) w[k] *= b5;
+        if (c5 != R(0)) {
+            R t[12];
+            const int sm = s > 0 ? s - 1 : Ls - 1;
+            const R fm = s > 0 ? c5 : -mass * c5;
+            in.load_half(sr, sm, 0, t);  // P+ psi_{s-1}
+#pragma unroll
+            for (int k = 0; k < 12; ++k) w[k] += fm * t[k];
+            const int sp = s < Ls - 1 ? s + 1 : 0;
+            const R fp = s < Ls - 1 ? c5 : -mass * c5;
+            in.load_half(sr, sp, 1, t);  // P- psi_{s+1}
+#pragma unroll
+            for (int k = 0; k < 12; ++k) w[12 + k] += fp * t[k];
+        }
+    }
+}
+
+template <int P, int MU, bool GATHER, bool DAG, typename R>
+__device__ __forceinline__ void hop_dir(R* acc, const Field<P>& in, const Gauge<P>& U, const HopParams<R>& hp,
+                                        const int* c, long long site, int s, long long rbase, R mass) {
+    const Geom& g = hp.g;
+    const int Lmu = MU == 0 ? g.X : MU == 1 ? g.Y : MU == 2 ? g.Z : g.T;
+    int f[4] = {c[0], c[1], c[2], c[3]};
+    int b[4] = {c[0], c[1], c[2], c[3]};
+    f[MU] = c[MU] + 1 == Lmu ? 0 : c[MU] + 1;
+    b[MU] = c[MU] == 0 ? Lmu - 1 : c[MU] - 1;
+    const long long jf = cb_index(g, f[0], f[1], f[2], f[3]);
+    const long long jb = cb_index(g, b[0], b[1], b[2], b[3]);
+    constexpr int SF = DAG ? +1 : -1;  // forward projector 1 + SF g_mu
+    {
+        R w[24], h[12], u[18], gg[12];
+        load_input<P, GATHER>(in, rbase + jf, s, g.Ls, hp.b5, hp.c5, mass, w);
+        project<MU, SF>(w, h);
+        U.load(((long long)hp.out_parity * 4 + MU) * g.Vh + site, u);
+        su3_mul<false>(u, h, gg);
+        reconstruct_add<MU, SF>(acc, gg);
+    }
+    {
+        R w[24], h[12], u[18], gg[12];
+        load_input<P, GATHER>(in, rbase + jb, s, g.Ls, hp.b5, hp.c5, mass, w);
+        project<MU, -SF>(w, h);
+        U.load(((long long)(1 - hp.out_parity) * 4 + MU) * g.Vh + jb, u);
+        su3_mul<true>(u, h, gg);
+        reconstruct_add<MU, -SF>(acc, gg);
+    }
+}
+
+template <int P, bool GATHER, bool DAG, bool XPAY>
+__global__ void __launch_bounds__(256) hop_kernel(Field<P> out, Field<P> in, Field<P> xf, Gauge<P> U,
+                                                  HopParams<typename PrecTraits<P>::real> hp) {
+    typedef typename PrecTraits<P>::real R;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Ls = hp.g.Ls;
+    R* mat = reinterpret_cast<R*>(smem_raw);  // [chir][s'][s]
+    R* hs = mat + 2 * Ls * Ls;                // [SB][Ls][24]
+    const int s = threadIdx.x, ly = threadIdx.y;
+    const int rhs = blockIdx.y;
+    const int tid = ly * blockDim.x + s, nthr = blockDim.x * blockDim.y;
+    const R* gm = hp.mat + (size_t)rhs * 2 * Ls * Ls;
+    for (int i = tid; i < 2 * Ls * Ls; i += nthr) mat[i] = gm[i];
+
+    const long long site = (long long)blockIdx.x * blockDim.y + ly;
+    const bool active = site < hp.g.Vh;
+    const long long rbase = (long long)rhs * hp.g.Vh;
+    R acc[24];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) acc[k] = 0;
+    if (active) {
+        int c[4];
+        cb_coords(hp.g, site, hp.out_parity, c);
+        const R mass = GATHER ? hp.mass[rhs] : R(0);
+        hop_dir<P, 0, GATHER, DAG>(acc, in, U, hp, c, site, s, rbase, mass);
+        hop_dir<P, 1, GATHER, DAG>(acc, in, U, hp, c, site, s, rbase, mass);
+        hop_dir<P, 2, GATHER, DAG>(acc, in, U, hp, c, site, s, rbase, mass);
+        hop_dir<P, 3, GATHER, DAG>(acc, in, U, hp, c, site, s, rbase, mass);
+    }
+    R* mine = hs + ((size_t)ly * Ls + s) * 24;
+#pragma unroll
+    for (int k = 0; k < 24; ++k) mine[k] = acc[k];
+    __syncthreads();
+    if (!active) return;
+    R res[24];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) res[k] = 0;
+    const R* col = hs + (size_t)ly * Ls * 24;
+    for (int sp = 0; sp < Ls; ++sp) {
+        const R mp = mat[sp * Ls + s];            // (s, s') of the P+ matrix
+        const R mm = mat[(Ls + sp) * Ls + s];     // (s, s') of the P- matrix
+        const R* h = col + sp * 24;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) res[k] += mp * h[k];
+#pragma unroll
+        for (int k = 12; k < 24; ++k) res[k] += mm * h[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 24; ++k) res[k] *= hp.coef;
+    if (XPAY) {
+        R xv[24];
+        xf.load(rbase + site, s, xv);
+#pragma unroll
+        for (int k = 0; k < 24; ++k) res[k] += xv[k];
+    }
+    out.store(rbase + site, s, res);
+}
+
+// ---------------------------------------------------------------- launcher
+
+static int sites_per_block(int Ls) {
+    int sb = 128 / Ls;
+    return sb < 1 ? 1 : sb;
+}
+
+template <int P, bool G, bool D, bool X>
+static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<typename PrecTraits<P>::real>& hp) {
+    typedef typename PrecTraits<P>::real R;
+    const Geom& g = c->g;
+    const int SB = sites_per_block(g.Ls);
+    dim3 block(g.Ls, SB), grid((unsigned)((g.Vh + SB - 1) / SB), h.nrhs);
+    size_t smem = (size_t)(2 * g.Ls * g.Ls + SB * g.Ls * 24) * sizeof(R);
+    auto kern = hop_kernel<P, G, D, X>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    Field<P> out = make_field<P>(h.out, g, h.nrhs);
+    Field<P> in = make_field<P>(const_cast<void*>(h.in), g, h.nrhs);
+    Field<P> xf = h.x ? make_field<P>(const_cast<void*>(h.x), g, h.nrhs) : out;
+    Gauge<P> U;
+    U.u = reinterpret_cast<decltype(U.u)>(c->gauge[P]);
+    const int base = D ? (X ? KB_HOP_DAG_XPAY : KB_HOP_DAG)
+                       : G ? (X ? KB_HOP_GATHER_XPAY : KB_HOP_GATHER) : (X ? KB_HOP_XPAY : KB_HOP);
+    const double n5 = (double)g.Vh * g.Ls * h.nrhs;
+    const double bytes = n5 * site_bytes(P) * (X ? 3.0 : 2.0) + 8.0 * g.Vh * link_bytes(P);
+    const double flops = n5 * (1320.0 + (G ? 72.0 : 0.0) + 144.0 + (X ? 48.0 : 0.0));
+    LaunchScope scope(c, base * 3 + P, bytes, flops);
+    kern<<<grid, block, smem, c->stream>>>(out, in, xf, U, hp);
+    return check_launch();
+}
+
+template <int P>
+static int launch_hop_t(mdwf_ctx* c, const HopLaunch& h) {
+    typedef typename PrecTraits<P>::real R;
+    HopParams<R> hp;
+    hp.g = c->g;
+    hp.out_parity = h.out_parity;
+    hp.coef = (R)h.coef;
+    hp.b5 = (R)h.b5;
+    hp.c5 = (R)h.c5;
+    hp.mass = reinterpret_cast<const R*>(h.mass);
+    hp.mat = reinterpret_cast<const R*>(h.mat);
+    const bool X = h.x != nullptr;
+    if (h.gather) {
+        if (h.dagger) return MDWF_EINVAL;
+        return X ? launch_hop_variant<P, true, false, true>(c, h, hp)
+                 : launch_hop_variant<P, true, false, false>(c, h, hp);
+    }
+    if (h.dagger)
+        return X ? launch_hop_variant<P, false, true, true>(c, h, hp)
+                 : launch_hop_variant<P, false, true, false>(c, h, hp);
+    return X ? launch_hop_variant<P, false, false, true>(c, h, hp)
+             : launch_hop_variant<P, false, false, false>(c, h, hp);
+}
+
+int launch_hop(mdwf_ctx* c, int prec, const HopLaunch& h) {
+    switch (prec) {
+        case MDWF_F64: return launch_hop_t<MDWF_F64>(c, h);
+        case MDWF_F32: return launch_hop_t<MDWF_F32>(c, h);
+        case MDWF_F16N: return launch_hop_t<MDWF_F16N>(c, h);
+    }
+    return MDWF_EINVAL;
+}
+
+}  // namespace mdwf

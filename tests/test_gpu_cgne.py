@@ -1,0 +1,135 @@
+"""GPU CGNE solves (prepare -> CG on M^dag M -> reconstruct) against the FP64
+oracle: plain FP64 and mixed FP32 / FP16+norm with FP64 reliable updates.
+
+Bar: the reported FP64 true residual |M^dag b' - M^dag M x| / |M^dag b'| is
+<= 1e-10, the oracle recomputes it from the GPU solution and agrees, and on
+lattices where the oracle solves too the solutions agree to cond * 1e-10.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle
+import paper_1206_5214_gb300 as mdwf
+import synthetic as sy
+
+pytestmark = pytest.mark.gpu
+
+F64, F32, F16N = mdwf.MDWF_F64, mdwf.MDWF_F32, mdwf.MDWF_F16N
+
+
+def oracle_residual(x_full, b_full, U, p):
+    """|M^dag b' - M^dag M x_o| / |M^dag b'| computed by the oracle."""
+    bp = oracle.prepare(b_full, U, p)
+    src = oracle.m(bp, U, p, dagger=True)
+    _, xo = oracle.split(x_full, p.dims)
+    r = src - oracle.mdagm(xo, U, p)
+    return np.linalg.norm(r) / np.linalg.norm(src)
+
+
+def gpu_solve(dims, Ls, b5, c5, mf, U, b, inner, nrhs=1, masses=None, host=False, graph=True, tol=1e-10):
+    h = mdwf.mdwf_create(dims, Ls, 1.8, b5, c5, mf)
+    try:
+        if host:
+            mdwf.mdwf_load_gauge(h, np.ascontiguousarray(U))
+            bb = np.ascontiguousarray(b)
+            x = np.zeros_like(bb)
+        else:
+            mdwf.mdwf_load_gauge(h, torch.from_numpy(U).cuda())
+            bb = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+            x = torch.zeros_like(bb)
+        st, info = mdwf.mdwf_cgne(h, x, bb, nrhs=nrhs, mf_per_rhs=masses, tol=tol, inner_prec=inner,
+                                  use_graph=graph)
+        xs = x if host else x.cpu().numpy()
+        return st, info, xs
+    finally:
+        mdwf.mdwf_destroy(h)
+
+
+@pytest.mark.parametrize("b5,c5", [(1.0, 0.0), (1.5, 0.5)], ids=["shamir", "moebius"])
+@pytest.mark.parametrize("inner", [F64, F32, F16N], ids=["f64", "mixed-f32", "mixed-f16n"])
+def test_cgne_4x4x4x4_matches_oracle_solve(b5, c5, inner):
+    """4^4, Ls = 8, M5 = 1.8, mf = 0.01, eps = 0.3, one Gaussian source, CGNE to 1e-10."""
+    dims, Ls = (4, 4, 4, 4), 8
+    U = sy.gauge_field(dims, 0.3, 1001)
+    b = sy.gaussian_field(dims, Ls, 2001)
+    p = oracle.Params(dims, Ls, 1.8, b5, c5, 0.01)
+    x_ref, st_ref, it_ref, rel_ref = oracle.solve(b, U, p, tol=1e-12)
+    assert st_ref == 0
+    st, info, x = gpu_solve(dims, Ls, b5, c5, 0.01, U, b, inner)
+    assert st == 0, info[0].as_dict()
+    assert info[0].true_res <= 1e-10
+    assert oracle_residual(x[0] if x.ndim == 8 else x, b, U, p) <= 1.05e-10
+    err = np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref)
+    assert err <= 1e-7, err
+    if inner != F64:
+        assert info[0].reliable_updates >= 1
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_cgne_multi_mass_batch(graph):
+    """One batched solve of 3 sources at uneven masses, each checked by the oracle."""
+    dims, Ls = (4, 4, 4, 4), 8
+    masses = [0.005, 0.02, 0.05]
+    U = sy.gauge_field(dims, 0.3, 1001)
+    b = sy.gaussian_field(dims, Ls, 2011, nrhs=3)
+    st, info, x = gpu_solve(dims, Ls, 1.5, 0.5, 0.01, U, b, F32, nrhs=3, masses=masses, graph=graph)
+    assert st == 0
+    for r, m in enumerate(masses):
+        p = oracle.Params(dims, Ls, 1.8, 1.5, 0.5, m)
+        assert info[r].true_res <= 1e-10
+        assert oracle_residual(x[r], b[r], U, p) <= 1.05e-10
+    # lighter masses need more iterations
+    assert info[0].iters >= info[2].iters
+
+
+def test_cgne_host_buffers_and_point_sources():
+    """Host-memory b and x; 12 spin-colour point sources on the walls."""
+    dims, Ls = (4, 4, 4, 4), 8
+    U = sy.gauge_field(dims, 0.3, 1003)
+    b = sy.point_sources(dims, Ls)
+    st, info, x = gpu_solve(dims, Ls, 1.5, 0.5, 0.005, U, b, F32, nrhs=12, host=True)
+    assert st == 0
+    p = oracle.Params(dims, Ls, 1.8, 1.5, 0.5, 0.005)
+    for r in (0, 5, 11):
+        assert oracle_residual(x[r], b[r], U, p) <= 1.05e-10
+
+
+def test_cgne_zero_source():
+    dims, Ls = (4, 4, 2, 2), 4
+    U = sy.gauge_field(dims, 0.3, 1004)
+    b = np.zeros((Ls, 2, 2, 4, 4, 4, 3), complex)
+    st, info, x = gpu_solve(dims, Ls, 1.5, 0.5, 0.01, U, b, F32)
+    assert st == 0 and np.count_nonzero(x) == 0
+
+
+def test_cgne_maxiter_reports_noconv():
+    dims, Ls = (4, 4, 4, 4), 8
+    U = sy.gauge_field(dims, 0.3, 1001)
+    b = sy.gaussian_field(dims, Ls, 2001)
+    h = mdwf.mdwf_create(dims, Ls, 1.8, 1.5, 0.5, 0.01)
+    try:
+        mdwf.mdwf_load_gauge(h, torch.from_numpy(U).cuda())
+        bb = torch.from_numpy(b).cuda()
+        x = torch.zeros_like(bb)
+        st, info = mdwf.mdwf_cgne(h, x, bb, maxiter=5, inner_prec=F64, raise_on_error=False)
+        assert st == 4 and info[0].status == 4
+        assert info[0].iters <= 8 and info[0].true_res > 1e-10
+    finally:
+        mdwf.mdwf_destroy(h)
+
+
+@pytest.mark.parametrize("inner", [F32, F16N], ids=["mixed-f32", "mixed-f16n"])
+def test_cgne_full_16x16x16x32(inner):
+    """16^3 x 32, Ls = 16, alpha = 2: the mixed solve reaches 1e-10, checked by the oracle."""
+    dims, Ls = (16, 16, 16, 32), 16
+    U = sy.gauge_field(dims, 0.2, 1002)
+    b = sy.gaussian_field(dims, Ls, 2002)
+    p = oracle.Params(dims, Ls, 1.8, 1.5, 0.5, 0.01)
+    st, info, x = gpu_solve(dims, Ls, 1.5, 0.5, 0.01, U, b, inner)
+    assert st == 0, info[0].as_dict()
+    assert info[0].true_res <= 1e-10
+    assert oracle_residual(x[0] if x.ndim == 8 else x, b, U, p) <= 1.05e-10

@@ -1,0 +1,177 @@
+"""GPU parity of the red/black Moebius operator M, M^dag and the layouts,
+called through the C ABI and compared element by element with the FP64 oracle.
+
+Tolerances (written here, derived from the arithmetic):
+  F64  : max |gpu - oracle| <= 1e-12 * max |oracle|   (rounding of ~3e3 flops per output)
+  F32  : max |gpu - oracle| <= 1e-5  * max |oracle|   (FP32 eps 6e-8 times the same chain)
+  F16N : |gpu - oracle|_2  <= 3e-3 * |oracle|_2       (FP16 storage, 2^-11 of each site's max,
+                                                       on input, intermediate and output)
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle
+import paper_1206_5214_gb300 as mdwf
+import synthetic as sy
+from _gpu import Ctx, rel_err
+
+pytestmark = pytest.mark.gpu
+
+F64, F32, F16N = mdwf.MDWF_F64, mdwf.MDWF_F32, mdwf.MDWF_F16N
+TOL_MAX = {F64: 1e-12, F32: 1e-5}
+TOL_L2_F16N = 3e-3
+
+
+def check(gpu, ref, prec):
+    emax, el2 = rel_err(gpu, ref)
+    if prec == F16N:
+        assert el2 <= TOL_L2_F16N, (emax, el2)
+    else:
+        assert emax <= TOL_MAX[prec], (emax, el2)
+    return emax, el2
+
+
+def setup(dims, Ls, b5, c5, mf, eps, seed, M5=1.8):
+    U = sy.gauge_field(dims, eps, 1000 + seed)
+    psi = sy.gaussian_field(dims, Ls, 2000 + seed)
+    _, odd = oracle.split(psi, dims)
+    p = oracle.Params(dims, Ls, M5, b5, c5, mf)
+    return U, odd, p
+
+
+# ------------------------------------------------------------------ layouts
+
+@pytest.mark.parametrize("prec", [F64, F32, F16N])
+def test_import_export_roundtrip(prec):
+    dims, Ls = (4, 4, 2, 6), 6
+    U, odd, p = setup(dims, Ls, 1.5, 0.5, 0.01, 0.3, 1)
+    with Ctx(dims, Ls, 1.8, 1.5, 0.5, 0.01, U) as c:
+        back = c.download(c.upload(odd, prec), prec)[0]
+    if prec == F64:
+        assert np.array_equal(back, odd)
+    elif prec == F32:
+        f = odd.view(np.float64).astype(np.float32).astype(np.float64).view(np.complex128)
+        assert np.array_equal(back, f)
+    else:
+        # per (site, s) the error is below 2^-11 of that site's max |real component|
+        re = odd.view(np.float64).reshape(Ls, -1, 24)
+        err = np.abs(back.view(np.float64).reshape(Ls, -1, 24) - re).max(axis=-1)
+        assert np.all(err <= 2.0 ** -11 * np.abs(re).max(axis=-1) * 1.0001)
+
+
+# ------------------------------------------------------------- small lattice
+
+@pytest.mark.parametrize("b5,c5", [(1.0, 0.0), (1.5, 0.5), (2.5, 1.5)])
+@pytest.mark.parametrize("prec", [F64, F32, F16N])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_apply_parity_4x4x4x4(b5, c5, prec, dagger):
+    """4^4 lattice, Ls = 8, mf = 0.01, eps = 0.3 (Shamir and Moebius)."""
+    dims, Ls = (4, 4, 4, 4), 8
+    U, odd, p = setup(dims, Ls, b5, c5, 0.01, 0.3, 1)
+    ref = oracle.m(odd, U, p, dagger=dagger)
+    with Ctx(dims, Ls, 1.8, b5, c5, 0.01, U) as c:
+        got = c.apply(odd, prec, dagger)[0]
+    check(got, ref, prec)
+
+
+@pytest.mark.parametrize("dims,Ls", [((6, 2, 2, 4), 4), ((4, 2, 2, 2), 12), ((2, 2, 2, 2), 2), ((8, 2, 4, 2), 16)],
+                         ids=["Vh48-Ls4", "Vh16-Ls12", "Vh8-Ls2", "Vh64-Ls16"])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_apply_ragged_and_edge_shapes(dims, Ls, dagger):
+    """Site counts that leave a ragged last block, the smallest lattice and Ls = 2."""
+    U, odd, p = setup(dims, Ls, 1.5, 0.5, 0.05, 0.3, 2)
+    ref = oracle.m(odd, U, p, dagger=dagger)
+    with Ctx(dims, Ls, 1.8, 1.5, 0.5, 0.05, U) as c:
+        for prec in (F64, F32):
+            check(c.apply(odd, prec, dagger)[0], ref, prec)
+
+
+@pytest.mark.parametrize("prec", [F64, F32])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_apply_multi_rhs_multi_mass(prec, dagger):
+    """One launch over 3 right-hand sides with different masses."""
+    dims, Ls = (4, 4, 2, 4), 8
+    masses = [0.001, 0.02, 0.05]
+    U = sy.gauge_field(dims, 0.2, 1005)
+    srcs = sy.gaussian_field(dims, Ls, 2005, nrhs=3)
+    odd = np.stack([oracle.split(srcs[r], dims)[1] for r in range(3)])
+    with Ctx(dims, Ls, 1.8, 1.5, 0.5, 0.01, U) as c:
+        got = c.apply(odd, prec, dagger, nrhs=3, masses=masses)
+    for r, m in enumerate(masses):
+        ref = oracle.m(odd[r], U, oracle.Params(dims, Ls, 1.8, 1.5, 0.5, m), dagger=dagger)
+        check(got[r], ref, prec)
+
+
+def test_adjoint_identity_f64():
+    dims, Ls = (4, 4, 4, 2), 8
+    U, x, p = setup(dims, Ls, 1.5, 0.5, 0.02, 0.3, 3)
+    y = oracle.split(sy.gaussian_field(dims, Ls, 2103), dims)[1]
+    with Ctx(dims, Ls, 1.8, 1.5, 0.5, 0.02, U) as c:
+        my = c.apply(y, F64)[0]
+        mdx = c.apply(x, F64, dagger=True)[0]
+    lhs, rhs = np.vdot(x, my), np.vdot(mdx, y)
+    assert abs(lhs - rhs) <= 1e-13 * abs(lhs)
+
+
+def test_linearity_and_zero():
+    dims, Ls = (4, 4, 2, 2), 4
+    U, a, p = setup(dims, Ls, 1.5, 0.5, 0.02, 0.3, 4)
+    b = oracle.split(sy.gaussian_field(dims, Ls, 2104), dims)[1]
+    with Ctx(dims, Ls, 1.8, 1.5, 0.5, 0.02, U) as c:
+        z = c.apply(np.zeros_like(a), F64)[0]
+        assert np.count_nonzero(z) == 0
+        lin = c.apply(2.0 * a - 3.0 * b, F64)[0]
+        sep = 2.0 * c.apply(a, F64)[0] - 3.0 * c.apply(b, F64)[0]
+    assert np.abs(lin - sep).max() <= 1e-12 * np.abs(sep).max()
+
+
+def test_errors_reported():
+    dims, Ls = (4, 4, 4, 4), 8
+    h = mdwf.mdwf_create(dims, Ls, 1.8, 1.5, 0.5, 0.01)
+    try:
+        buf = torch.empty(mdwf.mdwf_field_bytes(h, F64, 1), dtype=torch.uint8, device="cuda")
+        out = torch.empty_like(buf)
+        with pytest.raises(mdwf.MdwfError) as e:
+            mdwf.mdwf_apply(h, out, buf, F64)
+        assert e.value.status == 7  # no gauge
+        U = torch.from_numpy(sy.unit_gauge(dims)).cuda()
+        mdwf.mdwf_load_gauge(h, U)
+        with pytest.raises(mdwf.MdwfError) as e:
+            mdwf.mdwf_apply(h, buf, buf, F64)
+        assert e.value.status == 1  # out aliases in
+        with pytest.raises(mdwf.MdwfError):
+            mdwf.mdwf_apply(h, out, buf, 7)
+    finally:
+        mdwf.mdwf_destroy(h)
+
+
+# ------------------------------------------------------------ full sizes
+
+@pytest.fixture(scope="module")
+def c2_case():
+    """16^3 x 32, Ls = 16, M5 = 1.8, mf = 0.01, b5 + c5 = 2, b5 - c5 = 1, eps = 0.2."""
+    dims, Ls = (16, 16, 16, 32), 16
+    U, odd, p = setup(dims, Ls, 1.5, 0.5, 0.01, 0.2, 2)
+    refs = {d: oracle.m(odd, U, p, dagger=d) for d in (False, True)}
+    return dims, Ls, U, odd, refs
+
+
+@pytest.mark.parametrize("prec", [F64, F32, F16N])
+def test_apply_parity_full_16x16x16x32(c2_case, prec):
+    dims, Ls, U, odd, refs = c2_case
+    with Ctx(dims, Ls, 1.8, 1.5, 0.5, 0.01, U) as c:
+        for d in (False, True):
+            check(c.apply(odd, prec, d)[0], refs[d], prec)
+
+
+@pytest.mark.parametrize("b5,c5", [(1.0, 0.0), (2.5, 1.5)], ids=["alpha1", "alpha4"])
+def test_apply_parity_full_16x16x16x32_other_alpha(b5, c5):
+    dims, Ls = (16, 16, 16, 32), 16
+    U, odd, p = setup(dims, Ls, b5, c5, 0.01, 0.2, 2)
+    ref = oracle.m(odd, U, p)
+    with Ctx(dims, Ls, 1.8, b5, c5, 0.01, U) as c:
+        check(c.apply(odd, F32)[0], ref, F32)
