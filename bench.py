@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--no-f64", action="store_true", help="skip the plain FP64 solve comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--quick", action="store_true", help="small lattice, for debugging only")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the per-precision Dslash loops, the second inner precision and the e2e leg")
+    ap.add_argument("--apply-only", choices=["f64", "f32", "f16n"], default=None,
+                    help="only time M applications in this precision (a fixed launch sequence for ncu)")
     return ap.parse_args()
 
 
@@ -188,6 +192,31 @@ def run_reference(args) -> None:
 
 # --------------------------------------------------------------- GPU arm
 
+def apply_only(args, h, b, dims, Ls, n5, flush) -> None:
+    """warmup + steps applications of M on resident fields of one precision."""
+    import numpy as np
+    import torch
+    import paper_1206_5214_gb300 as mdwf
+    prec = {"f64": mdwf.MDWF_F64, "f32": mdwf.MDWF_F32, "f16n": mdwf.MDWF_F16N}[args.apply_only]
+    Vh = int(np.prod(dims)) // 2
+    src = torch.from_numpy(np.ascontiguousarray(b.reshape(Ls, -1, 4, 3)[:, :Vh])).cuda()
+    fi = torch.empty(mdwf.mdwf_field_bytes(h, prec, 1), dtype=torch.uint8, device="cuda")
+    fo = torch.empty_like(fi)
+    mdwf.mdwf_field_import(h, fi, src, prec)
+    for _ in range(args.warmup):
+        mdwf.mdwf_apply(h, fo, fi, prec)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        mdwf.mdwf_apply(h, fo, fi, prec)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"apply_only": args.apply_only, "ms_per_M": ms,
+                      "GFLOPs": FLOPS_PER_SITE * n5 / (ms * 1e-3) / 1e9}), flush=True)
+
+
 def main() -> None:
     args = parse()
     if args.impl == "reference":
@@ -224,6 +253,11 @@ def main() -> None:
     def solve(prec, use_graph=True):
         st, info = mdwf.mdwf_cgne(h, xd, bd, tol=1e-10, inner_prec=prec, use_graph=use_graph)
         return info[0]
+
+    if args.apply_only:
+        apply_only(args, h, b, dims, Ls, n5, flush)
+        mdwf.mdwf_destroy(h)
+        return
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -292,11 +326,12 @@ def main() -> None:
 
     # ---------------- Dslash alone per precision (M applications on resident fields)
     dslash = {}
+    precs = () if args.no_extras else (("f64", mdwf.MDWF_F64), ("f32", mdwf.MDWF_F32), ("f16n", mdwf.MDWF_F16N))
     x_, y_, z_, t_ = dims
     Vh = x_ * y_ * z_ * t_ // 2
     src_odd = torch.from_numpy(np.ascontiguousarray(
         b.reshape(Ls, -1, 4, 3)[:, :Vh])).cuda()   # any field of the right size
-    for name, prec in (("f64", mdwf.MDWF_F64), ("f32", mdwf.MDWF_F32), ("f16n", mdwf.MDWF_F16N)):
+    for name, prec in precs:
         nbytes = mdwf.mdwf_field_bytes(h, prec, 1)
         fi = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
         fo = torch.empty_like(fi)
@@ -330,8 +365,9 @@ def main() -> None:
                                   "reliable_updates": infos[-1].reliable_updates,
                                   "true_res": infos[-1].true_res, "res_m": infos[-1].res_m}}
     other = "f16n" if args.inner == "f32" else "f32"
-    for name, prec in ((f"mixed_{other}", mdwf.MDWF_F16N if other == "f16n" else mdwf.MDWF_F32),) + \
-            ((() if args.no_f64 else (("f64", mdwf.MDWF_F64),))):
+    legs = () if args.no_extras else ((f"mixed_{other}", mdwf.MDWF_F16N if other == "f16n" else mdwf.MDWF_F32),)
+    legs += () if args.no_f64 else (("f64", mdwf.MDWF_F64),)
+    for name, prec in legs:
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -342,23 +378,9 @@ def main() -> None:
                     "true_res": inf.true_res, "res_m": inf.res_m}
 
     # ---------------- end to end through the C ABI with host buffers
-    bh = torch.from_numpy(b).pin_memory()
-    xh = torch.zeros_like(bh).pin_memory()
-    mdwf.mdwf_cgne(h, xh, bh, tol=1e-10, inner_prec=inner)
-    e2e_times = []
-    a0 = sum(mdwf.mdwf_counters(h)[1])
-    for _ in range(max(1, min(args.steps, 3))):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        mdwf.mdwf_cgne(h, xh, bh, tol=1e-10, inner_prec=inner)
-        e2e_times.append(time.perf_counter() - t0)
-    a1 = sum(mdwf.mdwf_counters(h)[1])
-    e2e_flops = (a1 - a0) / len(e2e_times) * FLOPS_PER_SITE * n5
-    e2e_s = sum(e2e_times) / len(e2e_times)
-    bytes_field = b.nbytes
-    e2e = {"value": e2e_flops / e2e_s / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": bytes_field,
-           "d2h_bytes_per_step": bytes_field, "ms_per_step": 1e3 * e2e_s}
+    e2e = None
+    if not args.no_extras:
+        e2e = end_to_end(args, h, b, inner, n5, flush)
 
     cpu = None if args.no_cpu else cpu_baseline(dims, Ls)
 
@@ -376,6 +398,29 @@ def main() -> None:
         dist.barrier()
         dist.destroy_process_group()
     mdwf.mdwf_destroy(h)
+
+
+def end_to_end(args, h, b, inner, n5, flush) -> dict:
+    """The same solve through mdwf_cgne with pinned host buffers: H2D of b and D2H of x timed."""
+    import torch
+    import paper_1206_5214_gb300 as mdwf
+    bh = torch.from_numpy(b).pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    mdwf.mdwf_cgne(h, xh, bh, tol=1e-10, inner_prec=inner)
+    e2e_times = []
+    a0 = sum(mdwf.mdwf_counters(h)[1])
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mdwf.mdwf_cgne(h, xh, bh, tol=1e-10, inner_prec=inner)
+        e2e_times.append(time.perf_counter() - t0)
+    a1 = sum(mdwf.mdwf_counters(h)[1])
+    e2e_flops = (a1 - a0) / len(e2e_times) * FLOPS_PER_SITE * n5
+    e2e_s = sum(e2e_times) / len(e2e_times)
+    bytes_field = b.nbytes
+    return {"value": e2e_flops / e2e_s / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": bytes_field,
+            "d2h_bytes_per_step": bytes_field, "ms_per_step": 1e3 * e2e_s}
 
 
 if __name__ == "__main__":

@@ -77,6 +77,9 @@ typedef struct mdwf_ctx mdwf_ctx;
 typedef struct {
     void *stream;         /* cudaStream_t to enqueue on; NULL = the legacy default stream */
     int device;           /* CUDA device ordinal; -1 = the device current at mdwf_create */
+    int dense_s;          /* 1: apply the Ls x Ls factors (I^-1, K, M_phi) as dense matrices built on
+                             the host; 0: by the closed-form elimination of Sec. 4 wherever
+                             |M-/M+| <= 0.9 (dense otherwise) */
 } mdwf_opts;
 
 /*
@@ -98,9 +101,10 @@ int mdwf_set_stream(mdwf_ctx *ctx, void *stream);
 /*
  * Loads the SU(3) links U_mu(x) (Eq. D^Wilson) from complex128
  * U[t][z][y][x][mu][3][3] in host (where = MDWF_HOST) or device memory.
- * The data is copied into per-parity, per-direction link arrays in FP64,
- * FP32 and FP16; the caller's buffer may be reused once the call returns
- * (host) or once the stream has passed this point (device).
+ * The data is copied into per-parity, per-direction link arrays in FP64 and
+ * FP32 (the FP32 copy also serves the FP16+norm operator); the caller's buffer
+ * may be reused once the call returns (host) or once the stream has passed
+ * this point (device).
  */
 int mdwf_load_gauge(mdwf_ctx *ctx, const double *U, int where);
 
@@ -134,7 +138,7 @@ typedef struct {
     int maxiter;          /* CG iteration cap; 0 = 20000 */
     int inner_prec;       /* MDWF_F64: plain FP64 CG; MDWF_F32 / MDWF_F16N: mixed precision
                              with FP64 reliable updates of x and the true residual */
-    double delta;         /* reliable-update threshold on |r| / max |r|; 0 = 0.1 */
+    double delta;         /* reliable-update threshold on |r| / max |r|; 0 = 0.01 (FP32 inner), 0.1 (FP16N) */
     int check_every;      /* iterations between host convergence polls; 0 = 8 */
     int use_graph;        /* 1: replay the CG iteration as a captured CUDA graph */
 } mdwf_solve_params;
@@ -159,6 +163,26 @@ typedef struct {
  */
 int mdwf_cgne(mdwf_ctx *ctx, double *x, const double *b, int nrhs, const double *mf_per_rhs,
               int where, const mdwf_solve_params *params, mdwf_solve_info *info);
+
+/*
+ * Derivatives of the action S = phi^dag (M^dag M)^-1 phi with M the operator
+ * of mdwf_apply (the Schur complement of Sec. 4) at the context's mass:
+ *   dSdU  : complex128 in the gauge layout U[t][z][y][x][mu][3][3]: for every
+ *           link entry dS/dRe U + i dS/dIm U, so that a variation dU changes S
+ *           by Re sum conj(dSdU) dU (the entries are treated as independent
+ *           complex numbers, not restricted to SU(3));
+ *   dSdb5, dSdc5: dS/db5 and dS/dc5 of the same S (M's dependence on b5, c5
+ *           through M_phi = b5 + c5 C and I = (b5 (4 - M5) + 1) + (c5 (4 - M5) - 1) C);
+ *   S     : the action.
+ * phi: one odd field in the user odd format; phi and dSdU are both host or
+ * both device memory (where). X = (M^dag M)^-1 phi is recomputed by the CG
+ * of mdwf_cgne (params as there; the force arithmetic is FP64 throughout).
+ * info (may be NULL) reports that solve. dSdU, dSdb5, dSdc5, S may each be NULL;
+ * with the three derivatives NULL only the action is computed.
+ * Synchronises the stream. Returns the solve's status.
+ */
+int mdwf_force(mdwf_ctx *ctx, double *dSdU, double *dSdb5, double *dSdc5, double *S, const double *phi,
+               int where, const mdwf_solve_params *params, mdwf_solve_info *info);
 
 /*
  * Per-kernel timing. While enabled, every kernel the context launches outside

@@ -19,7 +19,7 @@ __all__ = [
     "MDWF_F64", "MDWF_F32", "MDWF_F16N", "MdwfError", "lib_path", "load",
     "mdwf_create", "mdwf_destroy", "mdwf_set_stream", "mdwf_load_gauge", "mdwf_field_bytes",
     "mdwf_field_import", "mdwf_field_export", "mdwf_apply", "mdwf_apply_dag", "mdwf_cgne",
-    "mdwf_strerror", "mdwf_profile_enable", "mdwf_profile_read", "mdwf_counters", "SolveParams",
+    "mdwf_strerror", "mdwf_force", "mdwf_profile_enable", "mdwf_profile_read", "mdwf_counters", "SolveParams",
     "SolveInfo", "KernelStat",
 ]
 
@@ -40,7 +40,7 @@ class MdwfError(RuntimeError):
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("stream", ctypes.c_void_p), ("device", ctypes.c_int)]
+    _fields_ = [("stream", ctypes.c_void_p), ("device", ctypes.c_int), ("dense_s", ctypes.c_int)]
 
 
 class SolveParams(ctypes.Structure):
@@ -88,6 +88,7 @@ def load(build_if_missing: bool = True):
         "mdwf_apply": (ip, [vp, vp, vp, ip, ip, dp]),
         "mdwf_apply_dag": (ip, [vp, vp, vp, ip, ip, dp]),
         "mdwf_cgne": (ip, [vp, vp, vp, ip, dp, ip, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]),
+        "mdwf_force": (ip, [vp, vp, dp, dp, dp, vp, ip, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]),
         "mdwf_profile_enable": (ip, [vp, ip]),
         "mdwf_profile_read": (ip, [vp, ctypes.POINTER(KernelStat), ip, ctypes.POINTER(ctypes.c_int), ip]),
         "mdwf_counters": (ip, [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
@@ -131,12 +132,14 @@ def mdwf_strerror(status: int) -> str:
     return load().mdwf_strerror(int(status)).decode()
 
 
-def mdwf_create(dims, Ls: int, M5: float, b5: float, c5: float, mf: float, stream=None, device: int = -1):
-    """Create a context; returns an opaque handle (int). ``stream``: torch.cuda.Stream, raw handle or None."""
+def mdwf_create(dims, Ls: int, M5: float, b5: float, c5: float, mf: float, stream=None, device: int = -1,
+                dense_s: bool = False):
+    """Create a context; returns an opaque handle (int). ``stream``: torch.cuda.Stream, raw handle or None.
+    ``dense_s``: apply the Ls x Ls factors as dense matrices instead of the closed-form elimination."""
     lib = load()
     h = ctypes.c_void_p()
     d = (ctypes.c_int * 4)(*[int(x) for x in dims])
-    opts = _Opts(_stream_handle(stream), int(device))
+    opts = _Opts(_stream_handle(stream), int(device), int(bool(dense_s)))
     _check(lib.mdwf_create(ctypes.byref(h), d, int(Ls), float(M5), float(b5), float(c5), float(mf),
                            ctypes.byref(opts)), "mdwf_create")
     return h.value
@@ -196,7 +199,7 @@ def mdwf_apply_dag(ctx, out, inp, prec: int, nrhs: int = 1, mf_per_rhs=None) -> 
 
 
 def mdwf_cgne(ctx, x, b, nrhs: int = 1, mf_per_rhs=None, tol: float = 1e-10, maxiter: int = 20000,
-              inner_prec: int = MDWF_F64, delta: float = 0.1, check_every: int = 8, use_graph: bool = True,
+              inner_prec: int = MDWF_F64, delta: float = 0.0, check_every: int = 8, use_graph: bool = True,
               raise_on_error: bool = True):
     """Solve D_DW(m) x = b (full 5d fields, complex128, user order). Returns (status, [SolveInfo per rhs])."""
     px, wx = _ptr_where(x)
@@ -209,6 +212,29 @@ def mdwf_cgne(ctx, x, b, nrhs: int = 1, mf_per_rhs=None, tol: float = 1e-10, max
     if raise_on_error and st not in (0,):
         raise MdwfError(st, "mdwf_cgne")
     return st, list(infos)
+
+
+def mdwf_force(ctx, dSdU, phi, tol: float = 1e-12, maxiter: int = 40000, inner_prec: int = MDWF_F64,
+               use_graph: bool = True, raise_on_error: bool = True):
+    """S = phi^dag (M^dag M)^-1 phi, dS/dU (written into dSdU, gauge layout) and dS/db5, dS/dc5.
+
+    Returns (S, dSdb5, dSdc5, status, SolveInfo)."""
+    pp, wp = _ptr_where(phi)
+    if dSdU is None:
+        pg = None
+    else:
+        pg, wg = _ptr_where(dSdU)
+        if wg != wp:
+            raise ValueError("dSdU and phi must both be host or both be device buffers")
+    prm = SolveParams(float(tol), int(maxiter), int(inner_prec), 0.0, 8, int(bool(use_graph)))
+    info = SolveInfo()
+    S, db5, dc5 = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+    derivs = dSdU is not None
+    st = load().mdwf_force(ctx, pg, ctypes.byref(db5) if derivs else None, ctypes.byref(dc5) if derivs else None,
+                           ctypes.byref(S), pp, wp, ctypes.byref(prm), ctypes.byref(info))
+    if raise_on_error and st != 0:
+        raise MdwfError(st, "mdwf_force")
+    return S.value, db5.value, dc5.value, st, info
 
 
 def mdwf_profile_enable(ctx, enable: bool = True) -> None:

@@ -156,43 +156,40 @@ static void matmul(int n, const double* a, const double* b, double* c) {
         }
 }
 
-// out[op][chir][s'][s] = Mat_op,chir(s, s') for one mass; chir 0 = P+, 1 = P-.
+// out[t][chir][s'][s] = Mat_t,chir(s, s') for one mass, t = table_index(sop, swap);
+// chir 0 = P+, 1 = P-. The shift C is N' (psi_{s+1}, row Ls-1 takes -m psi_0)
+// on P- and N'^T on P+; the adjoint (swap) exchanges them.
 static bool build_tables(int Ls, double M5, double b5, double c5, double mf, double* out) {
     const int n = Ls, nn = Ls * Ls;
     const double Mp = b5 * (4.0 - M5) + 1.0, Mm = c5 * (4.0 - M5) - 1.0;
-    for (int chir = 0; chir < 2; ++chir) {
-        std::vector<double> C(nn, 0.0), Mphi(nn), Mee(nn), A(nn), K(nn);
-        // P- (chir 1): (C psi)_s = psi_{s+1}, row Ls-1 takes -m psi_0.
-        // P+ (chir 0): the transpose, (C psi)_s = psi_{s-1}, row 0 takes -m psi_{Ls-1}.
-        for (int s = 0; s < n; ++s) {
-            if (chir == 1) {
-                if (s + 1 < n) C[s * n + s + 1] = 1.0;
-                else C[s * n + 0] = -mf;
-            } else {
-                if (s > 0) C[s * n + s - 1] = 1.0;
-                else C[0 * n + n - 1] = -mf;
+    for (int chir = 0; chir < 2; ++chir)
+        for (int swap = 0; swap < 2; ++swap) {
+            const bool up = (chir == 1) != (swap == 1);
+            std::vector<double> C(nn, 0.0), Id(nn, 0.0), Mphi(nn), Mee(nn), A(nn), K(nn);
+            for (int s = 0; s < n; ++s) {
+                Id[s * n + s] = 1.0;
+                if (up) {
+                    if (s + 1 < n) C[s * n + s + 1] = 1.0;
+                    else C[s * n + 0] = -mf;
+                } else {
+                    if (s > 0) C[s * n + s - 1] = 1.0;
+                    else C[0 * n + n - 1] = -mf;
+                }
+            }
+            for (int i = 0; i < nn; ++i) {
+                Mphi[i] = b5 * Id[i] + c5 * C[i];
+                Mee[i] = Mp * Id[i] + Mm * C[i];
+            }
+            if (!invert(n, Mee.data(), A.data())) return false;
+            matmul(n, Mphi.data(), A.data(), K.data());
+            const double* mats[5] = {Id.data(), A.data(), Mphi.data(), K.data(), C.data()};  // SOP_ID .. SOP_C
+            for (int op = SOP_ID; op <= SOP_C; ++op) {
+                double* dst = out + ((size_t)table_index(op, swap) * 2 + chir) * nn;
+                const double* M = mats[op - SOP_ID];
+                for (int s = 0; s < n; ++s)
+                    for (int sp = 0; sp < n; ++sp) dst[sp * n + s] = M[s * n + sp];  // (s, s') at [s'][s]
             }
         }
-        for (int i = 0; i < nn; ++i) {
-            const double id = (i / n == i % n) ? 1.0 : 0.0;
-            Mphi[i] = b5 * id + c5 * C[i];
-            Mee[i] = Mp * id + Mm * C[i];
-        }
-        if (!invert(n, Mee.data(), A.data())) return false;
-        matmul(n, Mphi.data(), A.data(), K.data());
-        const double* mats[T_NUM] = {K.data(), A.data(), A.data(), K.data(), Mphi.data(), nullptr};
-        const bool transp[T_NUM] = {false, false, true, true, true, false};
-        for (int op = 0; op < T_NUM; ++op) {
-            double* dst = out + ((size_t)op * 2 + chir) * nn;
-            for (int s = 0; s < n; ++s)
-                for (int sp = 0; sp < n; ++sp) {
-                    double v;
-                    if (op == T_ID) v = (s == sp) ? 1.0 : 0.0;
-                    else v = transp[op] ? mats[op][sp * n + s] : mats[op][s * n + sp];
-                    dst[sp * n + s] = v;  // element (s, s') stored at [s'][s]
-                }
-        }
-    }
     return true;
 }
 
@@ -203,7 +200,7 @@ int ensure_tables(mdwf_ctx* c, int nrhs, const double* mf_per_rhs) {
     if (c->tab_valid && c->tab_nrhs == nrhs && memcmp(masses, c->tab_masses, sizeof(double) * nrhs) == 0)
         return MDWF_OK;
     const int Ls = c->g.Ls, nn = Ls * Ls;
-    const size_t per_rhs = (size_t)T_NUM * 2 * nn;
+    const size_t per_rhs = (size_t)kNumTables * 2 * nn;
     const size_t total = per_rhs * nrhs;
     // previous kernels may still read the old tables: let them finish first
     int st = cuda_status(cudaStreamSynchronize(c->stream));
@@ -228,8 +225,8 @@ int ensure_tables(mdwf_ctx* c, int nrhs, const double* mf_per_rhs) {
     std::vector<double> one(per_rhs);
     for (int r = 0; r < nrhs; ++r) {
         if (!build_tables(Ls, c->M5, c->b5, c->c5, masses[r], one.data())) return MDWF_EINVAL;
-        for (int op = 0; op < T_NUM; ++op)
-            memcpy(h64 + ((size_t)op * nrhs + r) * 2 * nn, one.data() + (size_t)op * 2 * nn, sizeof(double) * 2 * nn);
+        for (int t = 0; t < kNumTables; ++t)
+            memcpy(h64 + ((size_t)t * nrhs + r) * 2 * nn, one.data() + (size_t)t * 2 * nn, sizeof(double) * 2 * nn);
         hm64[r] = masses[r];
         hm32[r] = (float)masses[r];
     }
@@ -264,22 +261,31 @@ int apply_op(mdwf_ctx* c, void* out, const void* in, int prec, int nrhs, int dag
     h.c5 = c->c5;
     h.mass = mass;
     if (!dagger) {
+        // z_e = K H_eo (M_phi psi_o)
         h.out = c->tmp[0].p; h.in = in; h.x = nullptr; h.coef = 1.0; h.out_parity = 0;
-        h.gather = 1; h.dagger = 0; h.mat = table_ptr(c, prec, T_K);
+        h.gather = 1; h.dagger = 0;
+        set_sop(c, prec, SOP_K, 0, h);
         if ((st = launch_hop(c, prec, h))) return st;
+        // out = psi_o - 1/4 A H_oe z_e
         h.out = out; h.in = c->tmp[0].p; h.x = in; h.coef = -0.25; h.out_parity = 1;
-        h.gather = 0; h.dagger = 0; h.mat = table_ptr(c, prec, T_A);
+        h.gather = 0; h.dagger = 0;
+        set_sop(c, prec, SOP_A, 0, h);
         return launch_hop(c, prec, h);
     }
+    // v_o = A^dag psi_o
     M5Launch m{};
     m.out = c->tmp[1].p; m.in = in; m.x = nullptr; m.coef = 1.0; m.nrhs = nrhs;
-    m.mat = table_ptr(c, prec, T_ADAG);
+    set_sop(c, prec, SOP_A, 1, m);
     if ((st = launch_m5(c, prec, m))) return st;
+    // z_e = K^dag H'_eo v_o
     h.out = c->tmp[0].p; h.in = c->tmp[1].p; h.x = nullptr; h.coef = 1.0; h.out_parity = 0;
-    h.gather = 0; h.dagger = 1; h.mat = table_ptr(c, prec, T_KDAG);
+    h.gather = 0; h.dagger = 1;
+    set_sop(c, prec, SOP_K, 1, h);
     if ((st = launch_hop(c, prec, h))) return st;
+    // out = psi_o - 1/4 M_phi^dag H'_oe z_e
     h.out = out; h.in = c->tmp[0].p; h.x = in; h.coef = -0.25; h.out_parity = 1;
-    h.gather = 0; h.dagger = 1; h.mat = table_ptr(c, prec, T_MPHIDAG);
+    h.gather = 0; h.dagger = 1;
+    set_sop(c, prec, SOP_MPHI, 1, h);
     return launch_hop(c, prec, h);
 }
 
@@ -330,8 +336,14 @@ int mdwf_create(mdwf_ctx** out, const int dims[4], int Ls, double M5, double b5,
     c->g.Ls = Ls;
     c->g.Vh = (long long)dims[0] * dims[1] * dims[2] * dims[3] / 2;
     c->M5 = M5; c->b5 = b5; c->c5 = c5; c->mf = mf;
+    {
+        const double Mp = b5 * (4.0 - M5) + 1.0, Mm = c5 * (4.0 - M5) - 1.0;
+        c->dense_s = (opts && opts->dense_s) || Mp == 0.0 || fabs(Mm / Mp) > 0.9;
+    }
     // the default mass tables, so that an apply needs no host round trip
-    if ((st = ensure_tables(c, 1, nullptr))) {
+    if ((st = ensure_tables(c, 1, nullptr)) ||
+        (st = cuda_status(cudaMalloc(&c->nbr, sizeof(int) * 16 * (size_t)c->g.Vh))) ||
+        (st = launch_build_neighbours(c)) || (st = cuda_status(cudaStreamSynchronize(c->stream)))) {
         mdwf_destroy(c);
         return st;
     }
@@ -343,12 +355,14 @@ int mdwf_destroy(mdwf_ctx* c) {
     if (!c) return MDWF_OK;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
-    for (int k = 0; k < 3; ++k) cudaFree(c->gauge[k]);
+    for (int k = 0; k < 2; ++k) cudaFree(c->gauge[k]);
     cudaFree(c->tab64); cudaFree(c->tab32); cudaFree(c->mass64); cudaFree(c->mass32);
     cudaFreeHost(c->tab_host);
     cudaFree(c->tmp[0].p); cudaFree(c->tmp[1].p);
     cudaFree(c->solver.p);
+    cudaFree(c->io.p);
     cudaFree(c->red_partials);
+    cudaFree(c->nbr);
     for (auto& r : c->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     delete c;
@@ -365,15 +379,15 @@ int mdwf_load_gauge(mdwf_ctx* c, const double* U, int where) {
     if (!c || !U || (where != MDWF_HOST && where != MDWF_DEVICE)) return MDWF_EINVAL;
     int st;
     if ((st = cuda_status(cudaSetDevice(c->device)))) return st;
-    const size_t nlink = (size_t)c->g.Vh * 2 * 4 * 9;  // complex entries
-    const size_t bytes[3] = {nlink * 16, nlink * 8, nlink * 4};
-    for (int k = 0; k < 3; ++k)
+    const size_t nlink = (size_t)c->g.Vh * 2 * 4;
+    const size_t bytes[2] = {nlink * link_store_bytes(MDWF_F64), nlink * link_store_bytes(MDWF_F32)};
+    for (int k = 0; k < 2; ++k)
         if (!c->gauge[k] && (st = cuda_status(cudaMalloc(&c->gauge[k], bytes[k])))) return st;
     const double* src = U;
     void* stage = nullptr;
     if (where == MDWF_HOST) {
-        if ((st = cuda_status(cudaMalloc(&stage, bytes[0])))) return st;
-        st = cuda_status(cudaMemcpyAsync(stage, U, bytes[0], cudaMemcpyHostToDevice, c->stream));
+        if ((st = cuda_status(cudaMalloc(&stage, nlink * 144)))) return st;
+        st = cuda_status(cudaMemcpyAsync(stage, U, nlink * 144, cudaMemcpyHostToDevice, c->stream));
         if (st) { cudaFree(stage); return st; }
         src = (const double*)stage;
     }

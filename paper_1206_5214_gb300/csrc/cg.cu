@@ -347,15 +347,19 @@ static int true_residual(Solver& S, void* r, void* rs, const void* src, const vo
 }
 
 struct Fields {
-    // FP64
-    void *be, *bp, *xo, *xe, *r, *src, *t64, *ap64, *stage_b, *stage_x;
-    // inner
+    // FP64: solution, right-hand side of the normal equations, residual, operator temporaries
+    void *xo, *src, *r, *t64, *ap64;
+    // inner iteration
     void *xs, *rs, *p, *t, *ap;
 };
 
+// last_true[r] receives |src - M^dag M x|^2 of the FP64 solution x each time
+// it is recomputed; x changes only at those points, so the final value
+// belongs to the returned x.
 template <int PP>
 static int run_mixed(Solver& S, Fields& F, const mdwf_solve_params& prm, double tol, int maxiter,
-                     std::vector<double>& maxr, std::vector<int>& rupd, cudaGraphExec_t* gexec, bool use_graph) {
+                     std::vector<double>& maxr, std::vector<int>& rupd, std::vector<double>& last_true,
+                     cudaGraphExec_t* gexec, bool use_graph) {
     mdwf_ctx* c = S.c;
     const int nrhs = S.nrhs;
     int st;
@@ -366,8 +370,13 @@ static int run_mixed(Solver& S, Fields& F, const mdwf_solve_params& prm, double 
     if ((st = S.copy<PP, MDWF_F64>(F.p, F.src, false))) return st;
     if ((st = S.norm<MDWF_F64>(F.src, false, S_RR))) return st;
     if ((st = S.pull())) return st;
-    for (int r = 0; r < nrhs; ++r) maxr[r] = sqrt(S.hsc[S_RR * kMaxRhs + r]);
-    const double delta = prm.delta > 0 ? prm.delta : 0.1;
+    for (int r = 0; r < nrhs; ++r) {
+        maxr[r] = sqrt(S.hsc[S_RR * kMaxRhs + r]);
+        last_true[r] = S.hsc[S_RR * kMaxRhs + r];  // x = 0: r = src
+    }
+    // FP32 carries ~7 digits, so it can reduce the residual 100x between FP64
+    // updates; FP16 storage only ~3, so it updates after every 10x
+    const double delta = prm.delta > 0 ? prm.delta : (PP == MDWF_F32 ? 0.01 : 0.1);
     const int every = prm.check_every > 0 ? prm.check_every : 8;
     int it = 0;
     bool graph_ready = false;
@@ -424,6 +433,7 @@ static int run_mixed(Solver& S, Fields& F, const mdwf_solve_params& prm, double 
             rupd[r] += 1;
             const double rr = S.hsc[S_AUX * kMaxRhs + r];
             const double src2 = S.hsc[S_SRC2 * kMaxRhs + r];
+            last_true[r] = rr;
             S.hsc[S_RR * kMaxRhs + r] = rr;
             maxr[r] = sqrt(rr);
             if (rr <= tol * tol * src2) S.hsc[S_ACTIVE * kMaxRhs + r] = 0.0;
@@ -434,7 +444,7 @@ static int run_mixed(Solver& S, Fields& F, const mdwf_solve_params& prm, double 
 }
 
 static int run_plain(Solver& S, Fields& F, const mdwf_solve_params& prm, double tol, int maxiter,
-                     cudaGraphExec_t* gexec, bool use_graph) {
+                     std::vector<double>& last_true, cudaGraphExec_t* gexec, bool use_graph) {
     mdwf_ctx* c = S.c;
     const int nrhs = S.nrhs;
     int st;
@@ -449,6 +459,7 @@ static int run_plain(Solver& S, Fields& F, const mdwf_solve_params& prm, double 
         for (int r = 0; r < nrhs; ++r) {
             if (S.hsc[S_ACTIVE * kMaxRhs + r] == 0.0) continue;
             const double rr = S.hsc[S_AUX * kMaxRhs + r];
+            last_true[r] = rr;
             S.hsc[S_RR * kMaxRhs + r] = rr;
             if (rr <= tol * tol * S.hsc[S_SRC2 * kMaxRhs + r]) S.hsc[S_ACTIVE * kMaxRhs + r] = 0.0;
             else any = true;
@@ -496,6 +507,156 @@ static int run_plain(Solver& S, Fields& F, const mdwf_solve_params& prm, double 
     return MDWF_OK;
 }
 
+// Re <a, b> (or |a|^2 when b == a) per right-hand side of FP64 fields -> partials
+__global__ void __launch_bounds__(kRedThreads) k_dot64(Field<MDWF_F64> a, Field<MDWF_F64> b, double* part, Geom g) {
+    const int rhs = blockIdx.y;
+    double acc = 0;
+    SITE_LOOP(g) {
+        const int s = (int)(i % g.Ls);
+        const long long sr = rhs * g.Vh + i / g.Ls;
+        double av[24], bv[24];
+        a.load(sr, s, av);
+        b.load(sr, s, bv);
+#pragma unroll
+        for (int k = 0; k < 24; ++k) acc += av[k] * bv[k];
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[rhs * gridDim.x + blockIdx.x] = acc;
+}
+
+__global__ void k_sum_partials(const double* part, int nb, double* out) {
+    const int rhs = blockIdx.x;
+    double v = 0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) v += part[rhs * nb + i];
+    v = block_sum(v);
+    if (threadIdx.x == 0) out[rhs] = v;
+}
+
+constexpr int kDotBlocks = 2 * 152;
+
+int field_dot64(mdwf_ctx* c, const void* a, const void* b, int nrhs, double* out_host) {
+    const size_t need = (size_t)nrhs * kDotBlocks + kMaxRhs;
+    if (c->red_partials_len < need) {
+        cudaFree(c->red_partials);
+        c->red_partials = nullptr;
+        c->red_partials_len = 0;
+        int st = cuda_status(cudaMalloc(&c->red_partials, need * sizeof(double)));
+        if (st) return st;
+        c->red_partials_len = need;
+    }
+    const Geom& g = c->g;
+    const double n5 = (double)g.Vh * g.Ls * nrhs;
+    {
+        LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, n5 * 2.0 * 192.0, n5 * 48.0);
+        k_dot64<<<dim3(kDotBlocks, nrhs), kRedThreads, 0, c->stream>>>(
+            make_field<MDWF_F64>(const_cast<void*>(a), g, nrhs), make_field<MDWF_F64>(const_cast<void*>(b), g, nrhs),
+            c->red_partials, g);
+    }
+    int st = check_launch();
+    if (st) return st;
+    double* dout = c->red_partials + (size_t)nrhs * kDotBlocks;
+    {
+        LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, 8.0 * nrhs * kDotBlocks, 0.0);
+        k_sum_partials<<<nrhs, kRedThreads, 0, c->stream>>>(c->red_partials, kDotBlocks, dout);
+    }
+    if ((st = check_launch())) return st;
+    if ((st = cuda_status(cudaMemcpyAsync(out_host, dout, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, c->stream))))
+        return st;
+    return cuda_status(cudaStreamSynchronize(c->stream));
+}
+
+// Solves M^dag M x = src for nrhs FP64 internal odd fields (x starts at zero).
+// Plain FP64 CG or mixed precision with FP64 reliable updates (prm.inner_prec).
+int solve_normal(mdwf_ctx* c, int nrhs, void* xo, const void* src, const mdwf_solve_params& prm,
+                 NormalResult& res) {
+    const double tol = prm.tol > 0 ? prm.tol : 1e-10;
+    const int maxiter = prm.maxiter > 0 ? prm.maxiter : 20000;
+    const int inner = prm.inner_prec;
+    if (inner != MDWF_F64 && inner != MDWF_F32 && inner != MDWF_F16N) return MDWF_EINVAL;
+    res.status.assign(nrhs, MDWF_OK);
+    res.iters.assign(nrhs, 0);
+    res.rupd.assign(nrhs, 0);
+    res.rel.assign(nrhs, 0.0);
+
+    // a captured graph needs a stream other than the legacy default one
+    cudaStream_t user_stream = c->stream, own = nullptr;
+    const bool use_graph = prm.use_graph != 0 && !c->prof_on;
+    int st;
+    if (use_graph && user_stream == nullptr) {
+        if ((st = cuda_status(cudaStreamCreate(&own)))) return st;
+        c->stream = own;
+    }
+    const Geom g = c->g;
+    const size_t f64 = field_bytes(MDWF_F64, g, nrhs), f32 = field_bytes(MDWF_F32, g, nrhs);
+    const size_t fpp = field_bytes(inner, g, nrhs);
+    auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+    const int nb = 2 * 152;
+    const size_t need = up(f64) * 3 + (inner == MDWF_F64 ? up(f64) * 3 : up(f32) * 2 + up(fpp) * 3) +
+                        up(sizeof(double) * S_NUM * kMaxRhs) + up(sizeof(double) * nrhs * nb);
+    Fields F{};
+    Solver S{};
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<double> maxr(nrhs, 0.0);
+    double* hsc = nullptr;
+    int ret = MDWF_OK;
+    do {
+        if ((st = ensure_workspace(c->solver, need))) { ret = st; break; }
+        if ((st = ensure_workspace(c->tmp[0], f64)) || (st = ensure_workspace(c->tmp[1], f64))) { ret = st; break; }
+        char* w = (char*)c->solver.p;
+        auto take = [&](size_t bytes) { void* p = w; w += up(bytes); return p; };
+        F.xo = xo;
+        F.src = const_cast<void*>(src);
+        F.r = take(f64); F.t64 = take(f64); F.ap64 = take(f64);
+        if (inner == MDWF_F64) {
+            F.p = take(f64); F.t = take(f64); F.ap = take(f64);
+        } else {
+            F.xs = take(f32); F.rs = take(f32); F.p = take(fpp); F.t = take(fpp); F.ap = take(fpp);
+        }
+        S.c = c; S.g = g; S.nrhs = nrhs; S.nb = nb;
+        S.sc = (double*)take(sizeof(double) * S_NUM * kMaxRhs);
+        S.part = (double*)take(sizeof(double) * nrhs * nb);
+        if ((st = cuda_status(cudaMallocHost(&hsc, sizeof(double) * S_NUM * kMaxRhs)))) { ret = st; break; }
+        S.hsc = hsc;
+        memset(hsc, 0, sizeof(double) * S_NUM * kMaxRhs);
+        for (int r = 0; r < nrhs; ++r) hsc[S_ACTIVE * kMaxRhs + r] = 1.0;
+        if ((st = S.push())) { ret = st; break; }
+        if ((st = S.norm<MDWF_F64>(F.src, false, S_SRC2))) { ret = st; break; }
+        if ((st = cuda_status(cudaMemsetAsync(F.xo, 0, f64, c->stream)))) { ret = st; break; }
+        // zero right-hand sides are solved by x = 0
+        if ((st = S.pull())) { ret = st; break; }
+        for (int r = 0; r < nrhs; ++r)
+            if (S.hsc[S_SRC2 * kMaxRhs + r] == 0.0) S.hsc[S_ACTIVE * kMaxRhs + r] = 0.0;
+        if ((st = S.push())) { ret = st; break; }
+
+        std::vector<double> last_true(nrhs, 0.0);
+        if (inner == MDWF_F64)
+            st = run_plain(S, F, prm, tol, maxiter, last_true, &gexec, use_graph);
+        else if (inner == MDWF_F32)
+            st = run_mixed<MDWF_F32>(S, F, prm, tol, maxiter, maxr, res.rupd, last_true, &gexec, use_graph);
+        else
+            st = run_mixed<MDWF_F16N>(S, F, prm, tol, maxiter, maxr, res.rupd, last_true, &gexec, use_graph);
+        if (st) { ret = st; break; }
+
+        if ((st = S.pull())) { ret = st; break; }
+        // the last FP64 true residual |src - M^dag M x| / |src| of every right-hand side
+        for (int r = 0; r < nrhs; ++r) {
+            res.status[r] = (int)S.hsc[S_STATUS * kMaxRhs + r];
+            res.iters[r] = (int)S.hsc[S_ITERS * kMaxRhs + r];
+            const double src2 = S.hsc[S_SRC2 * kMaxRhs + r];
+            res.rel[r] = src2 > 0 ? sqrt(last_true[r] / src2) : 0.0;
+            if (res.status[r] == MDWF_OK && res.rel[r] > tol) res.status[r] = MDWF_ENOCONV;
+        }
+    } while (0);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (hsc) cudaFreeHost(hsc);
+    if (own) {
+        cudaStreamSynchronize(own);
+        cudaStreamDestroy(own);
+        c->stream = user_stream;
+    }
+    return ret;
+}
+
 }  // namespace mdwf
 
 using namespace mdwf;
@@ -508,158 +669,87 @@ extern "C" int mdwf_cgne(mdwf_ctx* c, double* x, const double* b, int nrhs, cons
     if (!c->have_gauge) return MDWF_ENOGAUGE;
     mdwf_solve_params prm{};
     if (params) prm = *params;
-    const double tol = prm.tol > 0 ? prm.tol : 1e-10;
-    const int maxiter = prm.maxiter > 0 ? prm.maxiter : 20000;
-    const int inner = prm.inner_prec;
-    if (inner != MDWF_F64 && inner != MDWF_F32 && inner != MDWF_F16N) return MDWF_EINVAL;
+    if (prm.inner_prec != MDWF_F64 && prm.inner_prec != MDWF_F32 && prm.inner_prec != MDWF_F16N) return MDWF_EINVAL;
     int st;
     if ((st = cuda_status(cudaSetDevice(c->device)))) return st;
     if ((st = ensure_tables(c, nrhs, mf_per_rhs))) return st;
-
-    // a captured graph needs a stream other than the legacy default one
-    cudaStream_t user_stream = c->stream, own = nullptr;
-    const bool use_graph = prm.use_graph != 0 && !c->prof_on;
-    if (use_graph && user_stream == nullptr) {
-        if ((st = cuda_status(cudaStreamCreate(&own)))) return st;
-        c->stream = own;
-    }
-
     const Geom g = c->g;
-    const size_t f64 = field_bytes(MDWF_F64, g, nrhs), f32 = field_bytes(MDWF_F32, g, nrhs);
-    const size_t fpp = field_bytes(inner, g, nrhs);
+    const size_t f64 = field_bytes(MDWF_F64, g, nrhs);
     const size_t full = (size_t)nrhs * g.Ls * 2 * g.Vh * 24 * sizeof(double);
-    const size_t align = 256;
-    auto up = [&](size_t v) { return (v + align - 1) / align * align; };
-    const int nb = 2 * 152;
-    size_t need = up(f64) * 8 + (inner == MDWF_F64 ? up(f64) * 3 : up(f32) * 2 + up(fpp) * 3) +
-                  (where == MDWF_HOST ? 2 * up(full) : 0) + up(sizeof(double) * S_NUM * kMaxRhs) +
-                  up(sizeof(double) * nrhs * nb);
-    Fields F{};
-    Solver S{};
-    cudaGraphExec_t gexec = nullptr;
-    std::vector<double> maxr(nrhs, 0.0);
-    std::vector<int> rupd(nrhs, 0);
-    double* hsc = nullptr;
+    auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+    const size_t need = up(f64) * 6 + (where == MDWF_HOST ? 2 * up(full) : 0);
+    if ((st = ensure_workspace(c->io, need))) return st;
+    if ((st = ensure_workspace(c->tmp[0], f64)) || (st = ensure_workspace(c->tmp[1], f64))) return st;
+    char* w = (char*)c->io.p;
+    auto take = [&](size_t bytes) { void* p = w; w += up(bytes); return p; };
+    void *be = take(f64), *bp = take(f64), *xo = take(f64), *xe = take(f64), *src = take(f64), *t = take(f64);
+    void* stage_b = where == MDWF_HOST ? take(full) : nullptr;
+    void* stage_x = where == MDWF_HOST ? take(full) : nullptr;
+
+    // b -> (b_e, b_o)
+    const double* bdev = b;
+    if (where == MDWF_HOST) {
+        if ((st = cuda_status(cudaMemcpyAsync(stage_b, b, full, cudaMemcpyHostToDevice, c->stream)))) return st;
+        bdev = (const double*)stage_b;
+    }
+    if ((st = launch_split_full(c, be, bp, bdev, MDWF_F64, nrhs))) return st;
+    // b'_o = A b_o + 1/2 A H_oe M_phi (A b_e), A = I^-1 (D_br = -1/2 H_oe M_phi)
+    M5Launch m{};
+    m.nrhs = nrhs; m.coef = 1.0; m.x = nullptr;
+    set_sop(c, MDWF_F64, SOP_A, 0, m);
+    m.out = xe; m.in = be;
+    if ((st = launch_m5(c, MDWF_F64, m))) return st;
+    m.out = t; m.in = bp;
+    if ((st = launch_m5(c, MDWF_F64, m))) return st;
+    HopLaunch h{};
+    h.nrhs = nrhs; h.b5 = c->b5; h.c5 = c->c5; h.mass = c->mass64;
+    h.out = bp; h.in = xe; h.x = t; h.coef = 0.5; h.out_parity = 1; h.gather = 1; h.dagger = 0;
+    set_sop(c, MDWF_F64, SOP_A, 0, h);
+    if ((st = launch_hop(c, MDWF_F64, h))) return st;
+    // src = M^dag b'
+    if ((st = apply_op(c, src, bp, MDWF_F64, nrhs, 1))) return st;
+
+    NormalResult res;
+    if ((st = solve_normal(c, nrhs, xo, src, prm, res))) return st;
+
+    // |b' - M x| / |b'|
+    std::vector<double> bb(nrhs), rr(nrhs);
+    if ((st = apply_op(c, t, xo, MDWF_F64, nrhs, 0))) return st;
+    {
+        // t = b' - M x
+        M5Launch d{};
+        d.nrhs = nrhs; d.out = t; d.in = t; d.x = bp; d.coef = -1.0;
+        set_sop(c, MDWF_F64, SOP_ID, 0, d);
+        if ((st = launch_m5(c, MDWF_F64, d))) return st;
+    }
+    if ((st = field_dot64(c, t, t, nrhs, rr.data()))) return st;
+    if ((st = field_dot64(c, bp, bp, nrhs, bb.data()))) return st;
+
+    // x_e = A b_e + 1/2 A H_eo M_phi x_o
+    h.out = t; h.in = xo; h.x = nullptr; h.coef = 0.5; h.out_parity = 0; h.gather = 1; h.dagger = 0;
+    set_sop(c, MDWF_F64, SOP_A, 0, h);
+    if ((st = launch_hop(c, MDWF_F64, h))) return st;
+    m.out = xe; m.in = be; m.x = t; m.coef = 1.0;
+    set_sop(c, MDWF_F64, SOP_A, 0, m);
+    if ((st = launch_m5(c, MDWF_F64, m))) return st;
+    double* xdev = where == MDWF_HOST ? (double*)stage_x : x;
+    if ((st = launch_join_full(c, xdev, xe, xo, MDWF_F64, nrhs))) return st;
+    if (where == MDWF_HOST &&
+        (st = cuda_status(cudaMemcpyAsync(x, stage_x, full, cudaMemcpyDeviceToHost, c->stream))))
+        return st;
+    if ((st = cuda_status(cudaStreamSynchronize(c->stream)))) return st;
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     int ret = MDWF_OK;
-    do {
-        if ((st = ensure_workspace(c->solver, need))) { ret = st; break; }
-        // the apply temporaries for both precisions used below
-        if ((st = ensure_workspace(c->tmp[0], f64)) || (st = ensure_workspace(c->tmp[1], f64))) { ret = st; break; }
-        char* w = (char*)c->solver.p;
-        auto take = [&](size_t bytes) { void* p = w; w += up(bytes); return p; };
-        F.be = take(f64); F.bp = take(f64); F.xo = take(f64); F.xe = take(f64);
-        F.r = take(f64); F.src = take(f64); F.t64 = take(f64); F.ap64 = take(f64);
-        if (inner == MDWF_F64) {
-            F.p = take(f64); F.t = take(f64); F.ap = take(f64);
-        } else {
-            F.xs = take(f32); F.rs = take(f32); F.p = take(fpp); F.t = take(fpp); F.ap = take(fpp);
+    for (int r = 0; r < nrhs; ++r) {
+        if (res.status[r] > ret) ret = res.status[r];
+        if (info) {
+            info[r].status = res.status[r];
+            info[r].iters = res.iters[r];
+            info[r].reliable_updates = res.rupd[r];
+            info[r].true_res = res.rel[r];
+            info[r].res_m = bb[r] > 0 ? sqrt(rr[r] / bb[r]) : 0.0;
+            info[r].seconds = secs;
         }
-        if (where == MDWF_HOST) { F.stage_b = take(full); F.stage_x = take(full); }
-        S.c = c; S.g = g; S.nrhs = nrhs; S.nb = nb;
-        S.sc = (double*)take(sizeof(double) * S_NUM * kMaxRhs);
-        S.part = (double*)take(sizeof(double) * nrhs * nb);
-        if ((st = cuda_status(cudaMallocHost(&hsc, sizeof(double) * S_NUM * kMaxRhs)))) { ret = st; break; }
-        S.hsc = hsc;
-        memset(hsc, 0, sizeof(double) * S_NUM * kMaxRhs);
-        for (int r = 0; r < nrhs; ++r) hsc[S_ACTIVE * kMaxRhs + r] = 1.0;
-        if ((st = S.push())) { ret = st; break; }
-
-        // source: b -> (b_e, b_o)
-        const double* bdev = b;
-        if (where == MDWF_HOST) {
-            if ((st = cuda_status(cudaMemcpyAsync(F.stage_b, b, full, cudaMemcpyHostToDevice, c->stream)))) { ret = st; break; }
-            bdev = (const double*)F.stage_b;
-        }
-        if ((st = launch_split_full(c, F.be, F.bp, bdev, MDWF_F64, nrhs))) { ret = st; break; }
-        // b'_o = A b_o + 1/2 A H_oe M_phi (A b_e), A = I^-1 (D_br = -1/2 H_oe M_phi)
-        M5Launch m{};
-        m.nrhs = nrhs; m.coef = 1.0; m.x = nullptr; m.mat = table_ptr(c, MDWF_F64, T_A);
-        m.out = F.xe; m.in = F.be;
-        if ((st = launch_m5(c, MDWF_F64, m))) { ret = st; break; }
-        m.out = F.r; m.in = F.bp;
-        if ((st = launch_m5(c, MDWF_F64, m))) { ret = st; break; }
-        HopLaunch h{};
-        h.nrhs = nrhs; h.b5 = c->b5; h.c5 = c->c5; h.mass = c->mass64;
-        h.out = F.bp; h.in = F.xe; h.x = F.r; h.coef = 0.5; h.out_parity = 1; h.gather = 1; h.dagger = 0;
-        h.mat = table_ptr(c, MDWF_F64, T_A);
-        if ((st = launch_hop(c, MDWF_F64, h))) { ret = st; break; }
-        // src = M^dag b', |src|^2
-        if ((st = apply_op(c, F.src, F.bp, MDWF_F64, nrhs, 1))) { ret = st; break; }
-        if ((st = S.norm<MDWF_F64>(F.src, false, S_SRC2))) { ret = st; break; }
-        if ((st = cuda_status(cudaMemsetAsync(F.xo, 0, f64, c->stream)))) { ret = st; break; }
-        // zero-source right-hand sides are solved by x = 0
-        if ((st = S.pull())) { ret = st; break; }
-        for (int r = 0; r < nrhs; ++r)
-            if (S.hsc[S_SRC2 * kMaxRhs + r] == 0.0) S.hsc[S_ACTIVE * kMaxRhs + r] = 0.0;
-        if ((st = S.push())) { ret = st; break; }
-
-        if (inner == MDWF_F64) st = run_plain(S, F, prm, tol, maxiter, &gexec, use_graph);
-        else if (inner == MDWF_F32) st = run_mixed<MDWF_F32>(S, F, prm, tol, maxiter, maxr, rupd, &gexec, use_graph);
-        else st = run_mixed<MDWF_F16N>(S, F, prm, tol, maxiter, maxr, rupd, &gexec, use_graph);
-        if (st) { ret = st; break; }
-
-        // final FP64 residuals for every right-hand side
-        std::vector<double> keep_active(nrhs), status(nrhs), iters(nrhs), src2(nrhs);
-        if ((st = S.pull())) { ret = st; break; }
-        for (int r = 0; r < nrhs; ++r) {
-            keep_active[r] = S.hsc[S_ACTIVE * kMaxRhs + r];
-            status[r] = S.hsc[S_STATUS * kMaxRhs + r];
-            iters[r] = S.hsc[S_ITERS * kMaxRhs + r];
-            src2[r] = S.hsc[S_SRC2 * kMaxRhs + r];
-        }
-        if ((st = true_residual<MDWF_F64, false>(S, F.r, nullptr, F.src, F.xo, F.t64, F.ap64, false))) { ret = st; break; }
-        if ((st = S.pull())) { ret = st; break; }
-        std::vector<double> rel(nrhs);
-        for (int r = 0; r < nrhs; ++r) rel[r] = src2[r] > 0 ? sqrt(S.hsc[S_AUX * kMaxRhs + r] / src2[r]) : 0.0;
-        // |b' - M x| / |b'|
-        if ((st = apply_op(c, F.t64, F.xo, MDWF_F64, nrhs, 0))) { ret = st; break; }
-        {
-        LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, S.n5() * 3.0 * 192.0, S.n5() * 48.0);
-        k_residual<MDWF_F64, false><<<S.grid(), kRedThreads, 0, c->stream>>>(
-            make_field<MDWF_F64>(F.ap64, g, nrhs), make_field<MDWF_F64>(F.ap64, g, nrhs),
-            make_field<MDWF_F64>(F.bp, g, nrhs), make_field<MDWF_F64>(F.t64, g, nrhs), S.part, nullptr, g);
-        }
-        if ((st = check_launch()) || (st = S.fin(FIN_STORE, S_AUX))) { ret = st; break; }
-        if ((st = S.norm<MDWF_F64>(F.bp, false, S_PAP))) { ret = st; break; }
-        if ((st = S.pull())) { ret = st; break; }
-
-        // x_e = A b_e + 1/2 A H_eo M_phi x_o
-        h.out = F.t64; h.in = F.xo; h.x = nullptr; h.coef = 0.5; h.out_parity = 0; h.gather = 1; h.dagger = 0;
-        h.mat = table_ptr(c, MDWF_F64, T_A);
-        if ((st = launch_hop(c, MDWF_F64, h))) { ret = st; break; }
-        m.out = F.xe; m.in = F.be; m.x = F.t64; m.coef = 1.0; m.mat = table_ptr(c, MDWF_F64, T_A);
-        if ((st = launch_m5(c, MDWF_F64, m))) { ret = st; break; }
-        double* xdev = where == MDWF_HOST ? (double*)F.stage_x : x;
-        if ((st = launch_join_full(c, xdev, F.xe, F.xo, MDWF_F64, nrhs))) { ret = st; break; }
-        if (where == MDWF_HOST &&
-            (st = cuda_status(cudaMemcpyAsync(x, F.stage_x, full, cudaMemcpyDeviceToHost, c->stream)))) {
-            ret = st;
-            break;
-        }
-        if ((st = cuda_status(cudaStreamSynchronize(c->stream)))) { ret = st; break; }
-        const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-        for (int r = 0; r < nrhs; ++r) {
-            int rs = (int)status[r];
-            if (rs == MDWF_OK && rel[r] > tol) rs = MDWF_ENOCONV;
-            if (rs > ret) ret = rs;
-            if (info) {
-                info[r].status = rs;
-                info[r].iters = (int)iters[r];
-                info[r].reliable_updates = rupd[r];
-                info[r].true_res = rel[r];
-                const double bb = S.hsc[S_PAP * kMaxRhs + r];
-                info[r].res_m = bb > 0 ? sqrt(S.hsc[S_AUX * kMaxRhs + r] / bb) : 0.0;
-                info[r].seconds = secs;
-            }
-        }
-        (void)keep_active;
-    } while (0);
-    if (gexec) cudaGraphExecDestroy(gexec);
-    if (hsc) cudaFreeHost(hsc);
-    if (own) {
-        cudaStreamSynchronize(own);
-        cudaStreamDestroy(own);
-        c->stream = user_stream;
     }
     return ret;
 }

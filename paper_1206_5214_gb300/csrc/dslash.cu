@@ -23,9 +23,15 @@ namespace mdwf {
 template <typename R> struct HopParams {
     Geom g;
     int out_parity;
-    R coef, b5, c5;
-    const R* mass;  // [rhs]
-    const R* mat;   // [rhs][chir][s'][s]
+    R coef;
+    // input gather w = gscale * (gown psi_s + gfac (P+ psi_{s-1} + P- psi_{s+1})) = M_phi psi;
+    // gscale is applied once to the accumulated hop instead of per neighbour
+    R gown, gfac, gscale;
+    const R* mass;   // [rhs]
+    const R* mat;    // dense tables [rhs][chir][s'][s] (sop == SOP_DENSE)
+    const int4* nbr; // [parity][site][2] = cb index of x+mu (mu = 0..3), then of x-mu
+    int sop, swap;
+    SCoef<R> sc;
 };
 
 // --------------------------------------------------------- spin structure
@@ -105,23 +111,25 @@ __device__ __forceinline__ void su3_mul(const R* U, const R* h, R* g) {
         }
 }
 
-// w = psi(s) or M_phi psi at s for the neighbour column sr
+// w = psi(s), or M_phi psi at s up to the factor gscale, for the neighbour column sr
 template <int P, bool GATHER, typename R>
-__device__ __forceinline__ void load_input(const Field<P>& in, long long sr, int s, int Ls, R b5, R c5,
+__device__ __forceinline__ void load_input(const Field<P>& in, long long sr, int s, int Ls, const HopParams<R>& hp,
                                            R mass, R* w) {
     in.load(sr, s, w);
     if (GATHER) {
+        if (hp.gown != R(1)) {
 #pragma unroll
-        for (int k = 0; k < 24; ++k) w[k] *= b5;
-        if (c5 != R(0)) {
+            for (int k = 0; k < 24; ++k) w[k] *= hp.gown;
+        }
+        if (hp.gfac != R(0)) {
             R t[12];
             const int sm = s > 0 ? s - 1 : Ls - 1;
-            const R fm = s > 0 ? c5 : -mass * c5;
+            const R fm = s > 0 ? hp.gfac : -mass * hp.gfac;
             in.load_half(sr, sm, 0, t);  // P+ psi_{s-1}
 #pragma unroll
             for (int k = 0; k < 12; ++k) w[k] += fm * t[k];
             const int sp = s < Ls - 1 ? s + 1 : 0;
-            const R fp = s < Ls - 1 ? c5 : -mass * c5;
+            const R fp = s < Ls - 1 ? hp.gfac : -mass * hp.gfac;
             in.load_half(sr, sp, 1, t);  // P- psi_{s+1}
 #pragma unroll
             for (int k = 0; k < 12; ++k) w[12 + k] += fp * t[k];
@@ -131,19 +139,12 @@ __device__ __forceinline__ void load_input(const Field<P>& in, long long sr, int
 
 template <int P, int MU, bool GATHER, bool DAG, typename R>
 __device__ __forceinline__ void hop_dir(R* acc, const Field<P>& in, const Gauge<P>& U, const HopParams<R>& hp,
-                                        const int* c, long long site, int s, long long rbase, R mass) {
+                                        long long jf, long long jb, long long site, int s, long long rbase, R mass) {
     const Geom& g = hp.g;
-    const int Lmu = MU == 0 ? g.X : MU == 1 ? g.Y : MU == 2 ? g.Z : g.T;
-    int f[4] = {c[0], c[1], c[2], c[3]};
-    int b[4] = {c[0], c[1], c[2], c[3]};
-    f[MU] = c[MU] + 1 == Lmu ? 0 : c[MU] + 1;
-    b[MU] = c[MU] == 0 ? Lmu - 1 : c[MU] - 1;
-    const long long jf = cb_index(g, f[0], f[1], f[2], f[3]);
-    const long long jb = cb_index(g, b[0], b[1], b[2], b[3]);
     constexpr int SF = DAG ? +1 : -1;  // forward projector 1 + SF g_mu
     {
         R w[24], h[12], u[18], gg[12];
-        load_input<P, GATHER>(in, rbase + jf, s, g.Ls, hp.b5, hp.c5, mass, w);
+        load_input<P, GATHER>(in, rbase + jf, s, g.Ls, hp, mass, w);
         project<MU, SF>(w, h);
         U.load(((long long)hp.out_parity * 4 + MU) * g.Vh + site, u);
         su3_mul<false>(u, h, gg);
@@ -151,7 +152,7 @@ __device__ __forceinline__ void hop_dir(R* acc, const Field<P>& in, const Gauge<
     }
     {
         R w[24], h[12], u[18], gg[12];
-        load_input<P, GATHER>(in, rbase + jb, s, g.Ls, hp.b5, hp.c5, mass, w);
+        load_input<P, GATHER>(in, rbase + jb, s, g.Ls, hp, mass, w);
         project<MU, -SF>(w, h);
         U.load(((long long)(1 - hp.out_parity) * 4 + MU) * g.Vh + jb, u);
         su3_mul<true>(u, h, gg);
@@ -160,54 +161,65 @@ __device__ __forceinline__ void hop_dir(R* acc, const Field<P>& in, const Gauge<
 }
 
 template <int P, bool GATHER, bool DAG, bool XPAY>
-__global__ void __launch_bounds__(256) hop_kernel(Field<P> out, Field<P> in, Field<P> xf, Gauge<P> U,
+__global__ void __launch_bounds__(128, PrecTraits<P>::min_blocks - (GATHER ? 1 : 0)) hop_kernel(Field<P> out, Field<P> in, Field<P> xf, Gauge<P> U,
                                                   HopParams<typename PrecTraits<P>::real> hp) {
     typedef typename PrecTraits<P>::real R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Ls = hp.g.Ls;
-    R* mat = reinterpret_cast<R*>(smem_raw);  // [chir][s'][s]
-    R* hs = mat + 2 * Ls * Ls;                // [SB][Ls][24]
+    const bool dense = hp.sop == SOP_DENSE;
+    R* mat = reinterpret_cast<R*>(smem_raw);          // [chir][s'][s] (dense only)
+    R* hs = mat + (dense ? 2 * Ls * Ls : 0);          // [SB][Ls][24]
     const int s = threadIdx.x, ly = threadIdx.y;
     const int rhs = blockIdx.y;
     const int tid = ly * blockDim.x + s, nthr = blockDim.x * blockDim.y;
-    const R* gm = hp.mat + (size_t)rhs * 2 * Ls * Ls;
-    for (int i = tid; i < 2 * Ls * Ls; i += nthr) mat[i] = gm[i];
-
+    if (dense) {
+        const R* gm = hp.mat + (size_t)rhs * 2 * Ls * Ls;
+        for (int i = tid; i < 2 * Ls * Ls; i += nthr) mat[i] = gm[i];
+    }
     const long long site = (long long)blockIdx.x * blockDim.y + ly;
     const bool active = site < hp.g.Vh;
     const long long rbase = (long long)rhs * hp.g.Vh;
+    const R mass = hp.mass[rhs];
     R acc[24];
 #pragma unroll
     for (int k = 0; k < 24; ++k) acc[k] = 0;
     if (active) {
-        int c[4];
-        cb_coords(hp.g, site, hp.out_parity, c);
-        const R mass = GATHER ? hp.mass[rhs] : R(0);
-        hop_dir<P, 0, GATHER, DAG>(acc, in, U, hp, c, site, s, rbase, mass);
-        hop_dir<P, 1, GATHER, DAG>(acc, in, U, hp, c, site, s, rbase, mass);
-        hop_dir<P, 2, GATHER, DAG>(acc, in, U, hp, c, site, s, rbase, mass);
-        hop_dir<P, 3, GATHER, DAG>(acc, in, U, hp, c, site, s, rbase, mass);
+        const int4* nb = hp.nbr + ((long long)hp.out_parity * hp.g.Vh + site) * 2;
+        const int4 f = __ldg(nb), b = __ldg(nb + 1);
+        hop_dir<P, 0, GATHER, DAG>(acc, in, U, hp, f.x, b.x, site, s, rbase, mass);
+        hop_dir<P, 1, GATHER, DAG>(acc, in, U, hp, f.y, b.y, site, s, rbase, mass);
+        hop_dir<P, 2, GATHER, DAG>(acc, in, U, hp, f.z, b.z, site, s, rbase, mass);
+        hop_dir<P, 3, GATHER, DAG>(acc, in, U, hp, f.w, b.w, site, s, rbase, mass);
     }
     R* mine = hs + ((size_t)ly * Ls + s) * 24;
 #pragma unroll
     for (int k = 0; k < 24; ++k) mine[k] = acc[k];
     __syncthreads();
-    if (!active) return;
     R res[24];
+    if (dense) {
+        if (!active) return;
 #pragma unroll
-    for (int k = 0; k < 24; ++k) res[k] = 0;
-    const R* col = hs + (size_t)ly * Ls * 24;
-    for (int sp = 0; sp < Ls; ++sp) {
-        const R mp = mat[sp * Ls + s];            // (s, s') of the P+ matrix
-        const R mm = mat[(Ls + sp) * Ls + s];     // (s, s') of the P- matrix
-        const R* h = col + sp * 24;
+        for (int k = 0; k < 24; ++k) res[k] = 0;
+        const R* col = hs + (size_t)ly * Ls * 24;
+        for (int sp = 0; sp < Ls; ++sp) {
+            const R mp = mat[sp * Ls + s];         // (s, s') of the P+ matrix
+            const R mm = mat[(Ls + sp) * Ls + s];  // (s, s') of the P- matrix
+            const R* h = col + sp * 24;
 #pragma unroll
-        for (int k = 0; k < 12; ++k) res[k] += mp * h[k];
+            for (int k = 0; k < 12; ++k) res[k] += mp * h[k];
 #pragma unroll
-        for (int k = 12; k < 24; ++k) res[k] += mm * h[k];
+            for (int k = 12; k < 24; ++k) res[k] += mm * h[k];
+        }
+    } else {
+        block_columns(hs, blockDim.y, Ls, hp.sop, hp.swap != 0, hp.sc, mass, tid, nthr);
+        __syncthreads();
+        if (!active) return;
+#pragma unroll
+        for (int k = 0; k < 24; ++k) res[k] = mine[k];
     }
+    const R cf = hp.coef * hp.gscale;
 #pragma unroll
-    for (int k = 0; k < 24; ++k) res[k] *= hp.coef;
+    for (int k = 0; k < 24; ++k) res[k] *= cf;
     if (XPAY) {
         R xv[24];
         xf.load(rbase + site, s, xv);
@@ -230,7 +242,7 @@ static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<t
     const Geom& g = c->g;
     const int SB = sites_per_block(g.Ls);
     dim3 block(g.Ls, SB), grid((unsigned)((g.Vh + SB - 1) / SB), h.nrhs);
-    size_t smem = (size_t)(2 * g.Ls * g.Ls + SB * g.Ls * 24) * sizeof(R);
+    size_t smem = (size_t)((hp.sop == SOP_DENSE ? 2 * g.Ls * g.Ls : 0) + SB * g.Ls * 24) * sizeof(R);
     auto kern = hop_kernel<P, G, D, X>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -240,7 +252,7 @@ static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<t
     Field<P> in = make_field<P>(const_cast<void*>(h.in), g, h.nrhs);
     Field<P> xf = h.x ? make_field<P>(const_cast<void*>(h.x), g, h.nrhs) : out;
     Gauge<P> U;
-    U.u = reinterpret_cast<decltype(U.u)>(c->gauge[P]);
+    U.u = reinterpret_cast<decltype(U.u)>(c->gauge[link_copy(P)]);
     const int base = D ? (X ? KB_HOP_DAG_XPAY : KB_HOP_DAG)
                        : G ? (X ? KB_HOP_GATHER_XPAY : KB_HOP_GATHER) : (X ? KB_HOP_XPAY : KB_HOP);
     const double n5 = (double)g.Vh * g.Ls * h.nrhs;
@@ -258,10 +270,22 @@ static int launch_hop_t(mdwf_ctx* c, const HopLaunch& h) {
     hp.g = c->g;
     hp.out_parity = h.out_parity;
     hp.coef = (R)h.coef;
-    hp.b5 = (R)h.b5;
-    hp.c5 = (R)h.c5;
+    // M_phi = b5 + c5 C folded as b5 (1 + (c5/b5) C) when b5 != 0
+    if (h.b5 != 0.0) {
+        hp.gown = R(1); hp.gfac = (R)(h.c5 / h.b5); hp.gscale = (R)h.b5;
+    } else {
+        hp.gown = R(0); hp.gfac = (R)h.c5; hp.gscale = R(1);
+    }
+    if (!h.gather) { hp.gown = R(1); hp.gfac = R(0); hp.gscale = R(1); }
     hp.mass = reinterpret_cast<const R*>(h.mass);
     hp.mat = reinterpret_cast<const R*>(h.mat);
+    hp.nbr = reinterpret_cast<const int4*>(c->nbr);
+    hp.sop = h.sop;
+    hp.swap = h.swap;
+    hp.sc.b5 = (R)c->b5;
+    hp.sc.c5 = (R)c->c5;
+    hp.sc.Mp = (R)(c->b5 * (4.0 - c->M5) + 1.0);
+    hp.sc.Mm = (R)(c->c5 * (4.0 - c->M5) - 1.0);
     const bool X = h.x != nullptr;
     if (h.gather) {
         if (h.dagger) return MDWF_EINVAL;

@@ -69,7 +69,7 @@ __global__ void full_kernel(Field<P> even, Field<P> odd, double* full, Geom g, i
     }
 }
 
-__global__ void gauge_pack_kernel(double2* u64, float2* u32, __half2* u16, const double2* __restrict__ U, Geom g) {
+__global__ void gauge_pack_kernel(double2* u64, float* u32, const double2* __restrict__ U, Geom g) {
     const long long V = 2 * g.Vh;
     const long long n = V * 4;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -81,14 +81,35 @@ __global__ void gauge_pack_kernel(double2* u64, float2* u32, __half2* u16, const
         const int z = (int)(q % g.Z); q /= g.Z;
         const int t = (int)q;
         const int par = (x + y + z + t) & 1;
-        const long long o = (((long long)par * 4 + mu) * g.Vh + (lex >> 1)) * 9;
+        const long long l = ((long long)par * 4 + mu) * g.Vh + (lex >> 1);
         const double2* src = U + i * 9;
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
             double2 d = src[k];
-            u64[o + k] = d;
-            u32[o + k] = make_float2((float)d.x, (float)d.y);
-            u16[o + k] = __floats2half2_rn((float)d.x, (float)d.y);
+            u64[l * 9 + k] = d;
+            u32[l * 20 + 2 * k] = (float)d.x;
+            u32[l * 20 + 2 * k + 1] = (float)d.y;
+        }
+        u32[l * 20 + 18] = 0.f;
+        u32[l * 20 + 19] = 0.f;
+    }
+}
+
+__global__ void neighbour_kernel(int* nbr, Geom g) {
+    const long long n = 2 * g.Vh;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int par = (int)(i / g.Vh);
+        const long long j = i % g.Vh;
+        int c[4];
+        cb_coords(g, j, par, c);
+        const int L[4] = {g.X, g.Y, g.Z, g.T};
+        int* o = nbr + i * 8;
+        for (int mu = 0; mu < 4; ++mu) {
+            int f[4] = {c[0], c[1], c[2], c[3]}, b[4] = {c[0], c[1], c[2], c[3]};
+            f[mu] = c[mu] + 1 == L[mu] ? 0 : c[mu] + 1;
+            b[mu] = c[mu] == 0 ? L[mu] - 1 : c[mu] - 1;
+            o[mu] = (int)cb_index(g, f[0], f[1], f[2], f[3]);
+            o[4 + mu] = (int)cb_index(g, b[0], b[1], b[2], b[3]);
         }
     }
 }
@@ -167,10 +188,19 @@ int launch_join_full(mdwf_ctx* c, double* full, const void* even, const void* od
 
 int launch_gauge_pack(mdwf_ctx* c, const double* U) {
     const long long n = 2 * c->g.Vh * 4;
-    LaunchScope scope(c, KB_LAYOUT * 3 + MDWF_F64, n * (144.0 * 2 + 72.0 + 36.0), 0.0);
-    gauge_pack_kernel<<<grid_for(n, 256), 256, 0, c->stream>>>(
-        (double2*)c->gauge[0], (float2*)c->gauge[1], (__half2*)c->gauge[2], (const double2*)U, c->g);
+    LaunchScope scope(c, KB_LAYOUT * 3 + MDWF_F64, n * (144.0 * 2 + 80.0), 0.0);
+    gauge_pack_kernel<<<grid_for(n, 256), 256, 0, c->stream>>>((double2*)c->gauge[0], (float*)c->gauge[1],
+                                                                (const double2*)U, c->g);
     return check_launch();
 }
 
+}  // namespace mdwf
+
+namespace mdwf {
+int launch_build_neighbours(mdwf_ctx* c) {
+    const long long n = 2 * c->g.Vh;
+    LaunchScope scope(c, KB_LAYOUT * 3 + MDWF_F64, n * 32.0, 0.0);
+    neighbour_kernel<<<grid_for(n, 256), 256, 0, c->stream>>>(c->nbr, c->g);
+    return check_launch();
+}
 }  // namespace mdwf

@@ -1,8 +1,8 @@
-// Site-local fifth-dimension operators: out = coef * Mat in (+ x), with Mat a
-// real Ls x Ls matrix per chirality (I^-1, its adjoint, M_phi, ...). The
-// Ls x Ls blocks of Sec. 4 (I_rr = A P- + A^T P+) are applied as dense
-// matrices built on the host, not by the paper's elimination recursion: a
-// dense row per thread keeps all Ls threads of a column busy at once.
+// Site-local fifth-dimension operators: out = coef * Op in (+ x), Op one of
+// the s-operators of each chirality (I^-1 by the closed-form elimination of
+// Sec. 4, M_phi, K = M_phi I^-1, the shift C, or a dense Ls x Ls table), or
+// their adjoints (chirality swapped). The Ls spinors of a 4d site are staged
+// in shared memory and each (site, component) column is solved by one thread.
 #include "mdwf_internal.cuh"
 
 namespace mdwf {
@@ -10,16 +10,21 @@ namespace mdwf {
 template <int P, bool XPAY>
 __global__ void __launch_bounds__(256) m5_kernel(Field<P> out, Field<P> in, Field<P> xf,
                                                  const typename PrecTraits<P>::real* tab,
-                                                 typename PrecTraits<P>::real coef, Geom g) {
+                                                 const typename PrecTraits<P>::real* mass,
+                                                 typename PrecTraits<P>::real coef, Geom g, int sop, int swap,
+                                                 SCoef<typename PrecTraits<P>::real> sc) {
     typedef typename PrecTraits<P>::real R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Ls = g.Ls;
+    const bool dense = sop == SOP_DENSE;
     R* mat = reinterpret_cast<R*>(smem_raw);
-    R* cs = mat + 2 * Ls * Ls;
+    R* cs = mat + (dense ? 2 * Ls * Ls : 0);
     const int s = threadIdx.x, ly = threadIdx.y, rhs = blockIdx.y;
     const int tid = ly * blockDim.x + s, nthr = blockDim.x * blockDim.y;
-    const R* gm = tab + (size_t)rhs * 2 * Ls * Ls;
-    for (int i = tid; i < 2 * Ls * Ls; i += nthr) mat[i] = gm[i];
+    if (dense) {
+        const R* gm = tab + (size_t)rhs * 2 * Ls * Ls;
+        for (int i = tid; i < 2 * Ls * Ls; i += nthr) mat[i] = gm[i];
+    }
     const long long site = (long long)blockIdx.x * blockDim.y + ly;
     const bool active = site < g.Vh;
     const long long sr = (long long)rhs * g.Vh + site;
@@ -33,18 +38,26 @@ __global__ void __launch_bounds__(256) m5_kernel(Field<P> out, Field<P> in, Fiel
 #pragma unroll
     for (int k = 0; k < 24; ++k) mine[k] = v[k];
     __syncthreads();
-    if (!active) return;
     R res[24];
+    if (dense) {
+        if (!active) return;
 #pragma unroll
-    for (int k = 0; k < 24; ++k) res[k] = 0;
-    const R* col = cs + (size_t)ly * Ls * 24;
-    for (int sp = 0; sp < Ls; ++sp) {
-        const R mp = mat[sp * Ls + s], mm = mat[(Ls + sp) * Ls + s];
-        const R* h = col + sp * 24;
+        for (int k = 0; k < 24; ++k) res[k] = 0;
+        const R* col = cs + (size_t)ly * Ls * 24;
+        for (int sp = 0; sp < Ls; ++sp) {
+            const R mp = mat[sp * Ls + s], mm = mat[(Ls + sp) * Ls + s];
+            const R* h = col + sp * 24;
 #pragma unroll
-        for (int k = 0; k < 12; ++k) res[k] += mp * h[k];
+            for (int k = 0; k < 12; ++k) res[k] += mp * h[k];
 #pragma unroll
-        for (int k = 12; k < 24; ++k) res[k] += mm * h[k];
+            for (int k = 12; k < 24; ++k) res[k] += mm * h[k];
+        }
+    } else {
+        block_columns(cs, blockDim.y, Ls, sop, swap != 0, sc, mass[rhs], tid, nthr);
+        __syncthreads();
+        if (!active) return;
+#pragma unroll
+        for (int k = 0; k < 24; ++k) res[k] = mine[k];
     }
 #pragma unroll
     for (int k = 0; k < 24; ++k) res[k] *= coef;
@@ -64,22 +77,28 @@ static int launch_m5_t(mdwf_ctx* c, const M5Launch& m) {
     int SB = 128 / g.Ls;
     if (SB < 1) SB = 1;
     dim3 block(g.Ls, SB), grid((unsigned)((g.Vh + SB - 1) / SB), m.nrhs);
-    size_t smem = (size_t)(2 * g.Ls * g.Ls + SB * g.Ls * 24) * sizeof(R);
+    size_t smem = (size_t)((m.sop == SOP_DENSE ? 2 * g.Ls * g.Ls : 0) + SB * g.Ls * 24) * sizeof(R);
     Field<P> out = make_field<P>(m.out, g, m.nrhs);
     Field<P> in = make_field<P>(const_cast<void*>(m.in), g, m.nrhs);
     Field<P> xf = m.x ? make_field<P>(const_cast<void*>(m.x), g, m.nrhs) : out;
     const R* tab = reinterpret_cast<const R*>(m.mat);
+    const R* mass = P == MDWF_F64 ? reinterpret_cast<const R*>(c->mass64) : reinterpret_cast<const R*>(c->mass32);
+    SCoef<R> sc;
+    sc.b5 = (R)c->b5;
+    sc.c5 = (R)c->c5;
+    sc.Mp = (R)(c->b5 * (4.0 - c->M5) + 1.0);
+    sc.Mm = (R)(c->c5 * (4.0 - c->M5) - 1.0);
     const double n5 = (double)g.Vh * g.Ls * m.nrhs;
     LaunchScope scope(c, (m.x ? KB_M5_XPAY : KB_M5) * 3 + P, n5 * site_bytes(P) * (m.x ? 3.0 : 2.0),
                       n5 * (144.0 + (m.x ? 24.0 : 0.0)));
     if (m.x) {
         auto k = m5_kernel<P, true>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<grid, block, smem, c->stream>>>(out, in, xf, tab, (R)m.coef, g);
+        k<<<grid, block, smem, c->stream>>>(out, in, xf, tab, mass, (R)m.coef, g, m.sop, m.swap, sc);
     } else {
         auto k = m5_kernel<P, false>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<grid, block, smem, c->stream>>>(out, in, xf, tab, (R)m.coef, g);
+        k<<<grid, block, smem, c->stream>>>(out, in, xf, tab, mass, (R)m.coef, g, m.sop, m.swap, sc);
     }
     return check_launch();
 }

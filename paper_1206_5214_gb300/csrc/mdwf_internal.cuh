@@ -12,8 +12,9 @@
 //   Chunks 0 .. NC/2-1 hold spins 0, 1 (the P+ half), the rest spins 2, 3 (P-).
 //   Sites of a parity are ordered lexicographically (x fastest): the site
 //   (x, y, z, t) of that parity has index (((t Z + z) Y + y) X + x) / 2.
-// Gauge links: [parity][mu][site of that parity][3][3] complex, in FP64,
-//   FP32 and FP16 copies (18 reals per link).
+// Gauge links: [parity][mu][site of that parity][3][3] complex, an FP64 copy
+//   (144 B per link) and an FP32 copy padded to 80 B (read by the FP32 and
+//   FP16+norm operators).
 #pragma once
 
 #include <cuda_fp16.h>
@@ -38,16 +39,19 @@ struct Geom {
 template <int P> struct PrecTraits;
 template <> struct PrecTraits<MDWF_F64> {
     typedef double real;
+    static constexpr int min_blocks = 3;  // 128-thread blocks per SM the hop kernel is compiled for
     static constexpr int W = 2, NC = 12;
     static constexpr size_t site_bytes = 192;
 };
 template <> struct PrecTraits<MDWF_F32> {
     typedef float real;
+    static constexpr int min_blocks = 6;
     static constexpr int W = 4, NC = 6;
     static constexpr size_t site_bytes = 96;
 };
 template <> struct PrecTraits<MDWF_F16N> {
     typedef float real;
+    static constexpr int min_blocks = 6;
     static constexpr int W = 4, NC = 6;
     static constexpr size_t site_bytes = 52;
 };
@@ -189,22 +193,28 @@ template <> struct Gauge<MDWF_F64> {
         for (int k = 0; k < 9; ++k) { double2 d = __ldg(p + k); o[2 * k] = d.x; o[2 * k + 1] = d.y; }
     }
 };
+// FP32 links are padded to 20 floats (five 16-byte loads), FP16 links to 24
+// halves (three 16-byte loads); the padding is never read into arithmetic.
 template <> struct Gauge<MDWF_F32> {
-    const float2* u;
+    const float4* u;
     __device__ __forceinline__ void load(long long idx, float* o) const {
-        const float2* p = u + idx * 9;
+        const float4* p = u + idx * 5;
+        float t[20];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) { float2 d = __ldg(p + k); o[2 * k] = d.x; o[2 * k + 1] = d.y; }
+        for (int k = 0; k < 5; ++k) {
+            float4 d = __ldg(p + k);
+            t[4 * k] = d.x; t[4 * k + 1] = d.y; t[4 * k + 2] = d.z; t[4 * k + 3] = d.w;
+        }
+#pragma unroll
+        for (int k = 0; k < 18; ++k) o[k] = t[k];
     }
 };
-template <> struct Gauge<MDWF_F16N> {
-    const __half2* u;
-    __device__ __forceinline__ void load(long long idx, float* o) const {
-        const __half2* p = u + idx * 9;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) { float2 d = __half22float2(p[k]); o[2 * k] = d.x; o[2 * k + 1] = d.y; }
-    }
-};
+// The FP16+norm operator reads the FP32 links: FP16 (11 significant bits)
+// links would bound its accuracy below what the inner solve needs.
+template <> struct Gauge<MDWF_F16N> : Gauge<MDWF_F32> {};
+// link storage bytes per precision (with padding); the F16N operator uses the FP32 copy
+inline size_t link_store_bytes(int prec) { return prec == MDWF_F64 ? 144 : 80; }
+inline int link_copy(int prec) { return prec == MDWF_F64 ? 0 : 1; }
 
 // ----------------------------------------------------------------- geometry
 
@@ -222,13 +232,105 @@ __device__ __forceinline__ long long cb_index(const Geom& g, int x, int y, int z
     return ((((long long)t * g.Z + z) * g.Y + y) * g.X + x) >> 1;
 }
 
+// ------------------------------------------------------- s-operators
+//
+// Every s-mixing factor of M and M^dag is a function of the fifth-dimension
+// shift C restricted to one chirality: on P- it is N' (psi_{s+1}, row Ls-1
+// takes -m psi_0), on P+ its transpose N'^T (psi_{s-1}, row 0 takes
+// -m psi_{Ls-1}); the adjoint of an operator swaps the two. Reflecting
+// s -> Ls-1-s turns N'^T into N', so one routine on a reflected index covers
+// both. With M+ = b5 (4 - M5) + 1, M- = c5 (4 - M5) - 1:
+//   SOP_C    : C psi
+//   SOP_MPHI : M_phi psi = b5 psi + c5 C psi
+//   SOP_A    : A psi = (M+ + M- C)^-1 psi by the closed-form elimination of
+//              Sec. 4: with r = M-/M+, kappa = m r,
+//                Psi_{Ls-1} = [b_{Ls-1} + kappa sum_{s<Ls-1} (-r)^s b_s] / (M+ (1 - kappa (-r)^{Ls-1}))
+//                Psi_s      = b_s / M+ - r Psi_{s+1}   (s = Ls-2 .. 0)
+//   SOP_K    : K psi = M_phi A psi, fused into the back substitution
+//   SOP_DENSE: a dense Ls x Ls table (any coefficients)
+enum SOp { SOP_DENSE = 0, SOP_ID = 1, SOP_A = 2, SOP_MPHI = 3, SOP_K = 4, SOP_C = 5 };
+
+template <typename R> struct SCoef {
+    R b5, c5, Mp, Mm;
+};
+
+// In place on one complex column: element s at base[k(s) * stride] (re) and
+// base[k(s) * stride + 1] (im), k(s) = up ? s : Ls-1-s. m = this rhs's mass.
+template <typename R>
+__device__ __forceinline__ void column_op(R* base, int stride, int Ls, int op, bool up, const SCoef<R>& sc, R m) {
+    auto at = [&](int s) -> R* { return base + (up ? s : Ls - 1 - s) * stride; };
+    if (op == SOP_A || op == SOP_K) {
+        const R r = sc.Mm / sc.Mp, kappa = m * r, inv = R(1) / sc.Mp;
+        R ar = at(Ls - 1)[0], ai = at(Ls - 1)[1], pw = kappa;
+        for (int s = 0; s < Ls - 1; ++s) {
+            const R* q = at(s);
+            ar += pw * q[0];
+            ai += pw * q[1];
+            pw *= -r;
+        }
+        const R den = sc.Mp * (R(1) - pw);
+        R pr = ar / den, pi = ai / den;  // Psi_{Ls-1}
+        const R lr = pr, li = pi;
+        if (op == SOP_A) {
+            R* q = at(Ls - 1);
+            q[0] = pr;
+            q[1] = pi;
+            for (int s = Ls - 2; s >= 0; --s) {
+                R* t = at(s);
+                pr = t[0] * inv - r * pr;
+                pi = t[1] * inv - r * pi;
+                t[0] = pr;
+                t[1] = pi;
+            }
+        } else {
+            for (int s = Ls - 2; s >= 0; --s) {
+                R* t = at(s);
+                const R nr = t[0] * inv - r * pr, ni = t[1] * inv - r * pi;  // Psi_s
+                t[0] = sc.b5 * nr + sc.c5 * pr;                             // (M_phi Psi)_s
+                t[1] = sc.b5 * ni + sc.c5 * pi;
+                pr = nr;
+                pi = ni;
+            }
+            R* q = at(Ls - 1);  // row Ls-1 wraps to Psi_0 (now in pr, pi) with -m
+            q[0] = sc.b5 * lr - m * sc.c5 * pr;
+            q[1] = sc.b5 * li - m * sc.c5 * pi;
+        }
+    } else if (op == SOP_MPHI || op == SOP_C) {
+        const R w0 = op == SOP_MPHI ? sc.b5 : R(0), w1 = op == SOP_MPHI ? sc.c5 : R(1);
+        const R f0r = at(0)[0], f0i = at(0)[1];
+        for (int s = 0; s < Ls - 1; ++s) {
+            R* t = at(s);
+            const R* u = at(s + 1);
+            t[0] = w0 * t[0] + w1 * u[0];
+            t[1] = w0 * t[1] + w1 * u[1];
+        }
+        R* q = at(Ls - 1);
+        q[0] = w0 * q[0] - m * w1 * f0r;
+        q[1] = w0 * q[1] - m * w1 * f0i;
+    }
+}
+
+// Applies the s-operator to the SB staged columns hs[site][s][24] of a block
+// (tasks = (site, complex component); P+ components are j < 6). Dense tables
+// are applied by the caller instead.
+template <typename R>
+__device__ __forceinline__ void block_columns(R* hs, int SB, int Ls, int op, bool swap, const SCoef<R>& sc,
+                                              R m, int tid, int nthr) {
+    for (int t = tid; t < SB * 12; t += nthr) {
+        const int ly = t / 12, j = t - 12 * (t / 12);
+        const bool up = (j >= 6) != swap;  // P- uses N' unless the adjoint swaps
+        column_op(hs + (size_t)ly * Ls * 24 + 2 * j, 24, Ls, op, up, sc, m);
+    }
+}
+
 // ------------------------------------------------------------------ tables
 //
-// Ls x Ls real matrices acting along s, one per chirality, for each operator
-// in the chain: table[op][rhs][chir][s'][s] holds element (s, s') (transposed,
-// so that the Ls threads of a column read consecutive words). chir 0 is the
-// P+ half (spins 0, 1), chir 1 the P- half.
-enum TableOp { T_K = 0, T_A = 1, T_ADAG = 2, T_KDAG = 3, T_MPHIDAG = 4, T_ID = 5, T_NUM = 6 };
+// Dense Ls x Ls real matrices of the s-operators, one per chirality:
+// table[t][rhs][chir][s'][s] holds element (s, s') (transposed, so that the
+// Ls threads of a column read consecutive words); chir 0 is the P+ half
+// (spins 0, 1), chir 1 the P- half; t = table_index(sop, swap).
+constexpr int kNumTables = 10;
+inline int table_index(int sop, int swap) { return (sop - 1) * 2 + (swap ? 1 : 0); }
 
 // ---------------------------------------------------------------- context
 
@@ -256,7 +358,7 @@ struct ProfRec {
 
 // algorithmic bytes per 5d site and per link, by precision
 inline double site_bytes(int prec) { return prec == MDWF_F64 ? 192.0 : prec == MDWF_F32 ? 96.0 : 52.0; }
-inline double link_bytes(int prec) { return prec == MDWF_F64 ? 144.0 : prec == MDWF_F32 ? 72.0 : 36.0; }
+inline double link_bytes(int prec) { return prec == MDWF_F64 ? 144.0 : 72.0; }
 
 }  // namespace mdwf
 
@@ -266,7 +368,7 @@ struct mdwf_ctx {
     mdwf::Geom g{};
     double M5 = 0, b5 = 0, c5 = 0, mf = 0;
     bool have_gauge = false;
-    void* gauge[3] = {nullptr, nullptr, nullptr};  // F64, F32, F16 copies
+    void* gauge[2] = {nullptr, nullptr};  // FP64 and FP32 copies
     // Ls x Ls tables for the current mass list, FP64 and FP32, plus per-rhs masses
     double* tab64 = nullptr;
     float* tab32 = nullptr;
@@ -276,10 +378,16 @@ struct mdwf_ctx {
     double* tab_host = nullptr;     // pinned staging for the tables
     double tab_masses[64] = {0};
     bool tab_valid = false;
+    // neighbour table [parity][site][8]: cb index of x+mu (0..3) and x-mu (4..7)
+    int* nbr = nullptr;
+    // 1: apply every s-operator as a dense table (any coefficients); 0: the
+    // closed-form recursions where they are stable (|M-/M+| <= 0.9)
+    bool dense_s = false;
     // scratch fields used inside one apply: [0] even-parity z, [1] odd-parity v
     mdwf::Workspace tmp[2];
-    // solver workspace
+    // solver workspace (CG fields) and the fields of the entry points around it
     mdwf::Workspace solver;
+    mdwf::Workspace io;
     // reduction scratch: per-rhs block partials and scalars
     double* red_partials = nullptr;
     size_t red_partials_len = 0;
@@ -323,11 +431,25 @@ int check_launch();
 int ensure_workspace(Workspace& w, size_t bytes);
 int ensure_tables(mdwf_ctx* c, int nrhs, const double* mf_per_rhs);
 
-// table pointers for op, precision
-inline const void* table_ptr(const mdwf_ctx* c, int prec, int op) {
+// table pointers for table t, precision
+inline const void* table_ptr(const mdwf_ctx* c, int prec, int t) {
     size_t per_op = (size_t)c->tab_nrhs * 2 * c->g.Ls * c->g.Ls;
-    if (prec == MDWF_F64) return c->tab64 + op * per_op;
-    return c->tab32 + op * per_op;
+    if (prec == MDWF_F64) return c->tab64 + t * per_op;
+    return c->tab32 + t * per_op;
+}
+
+// Selects the s-operator of a launch: the closed-form recursion, or the dense
+// table when the context asks for dense tables (or the recursion is not stable).
+template <class L> inline void set_sop(const mdwf_ctx* c, int prec, int sop, int swap, L& l) {
+    if (c->dense_s) {
+        l.sop = SOP_DENSE;
+        l.swap = 0;
+        l.mat = table_ptr(c, prec, table_index(sop, swap));
+    } else {
+        l.sop = sop;
+        l.swap = swap;
+        l.mat = nullptr;
+    }
 }
 
 // launchers (dslash.cu, m5.cu)
@@ -339,7 +461,9 @@ struct HopLaunch {
     int out_parity;
     int gather;           // 1: apply M_phi (b5 + c5 C) to the input column before the hop
     int dagger;           // 1: hopping term of D_W^dag (projector signs flipped)
-    const void* mat;      // table of the output Ls x Ls matrix (this precision), per rhs
+    const void* mat;      // dense table of the output Ls x Ls matrix (sop == SOP_DENSE), per rhs
+    int sop;              // output s-operator (SOp)
+    int swap;             // 1: the adjoint (chirality-swapped) s-operator
     const void* mass;     // per-rhs masses (double for F64, float otherwise)
     double b5, c5;
     int nrhs;
@@ -351,7 +475,9 @@ struct M5Launch {
     const void* in;
     const void* x;    // optional addend
     double coef;      // out = coef * Mat in [+ x]
-    const void* mat;
+    const void* mat;  // dense table (sop == SOP_DENSE)
+    int sop;
+    int swap;
     int nrhs;
 };
 int launch_m5(mdwf_ctx* c, int prec, const M5Launch& m);
@@ -359,11 +485,21 @@ int launch_m5(mdwf_ctx* c, int prec, const M5Launch& m);
 // operator chains (api.cu)
 int apply_op(mdwf_ctx* c, void* out, const void* in, int prec, int nrhs, int dagger);
 
+// solver (cg.cu)
+struct NormalResult {
+    std::vector<int> status, iters, rupd;
+    std::vector<double> rel;  // |src - M^dag M x| / |src| in FP64
+};
+int solve_normal(mdwf_ctx* c, int nrhs, void* xo, const void* src, const mdwf_solve_params& prm, NormalResult& res);
+// Re <a, b> of FP64 internal fields per right-hand side into host memory (synchronises)
+int field_dot64(mdwf_ctx* c, const void* a, const void* b, int nrhs, double* out_host);
+
 // layout kernels (layout.cu)
 int launch_import_odd(mdwf_ctx* c, void* dst, const double* src_dev, int prec, int nrhs);
 int launch_export_odd(mdwf_ctx* c, double* dst_dev, const void* src, int prec, int nrhs);
 int launch_split_full(mdwf_ctx* c, void* dst_even, void* dst_odd, const double* full_dev, int prec, int nrhs);
 int launch_join_full(mdwf_ctx* c, double* full_dev, const void* even, const void* odd, int prec, int nrhs);
 int launch_gauge_pack(mdwf_ctx* c, const double* U_dev);
+int launch_build_neighbours(mdwf_ctx* c);
 
 }  // namespace mdwf

@@ -11,11 +11,11 @@ PREC_NAME = {mdwf.MDWF_F64: "f64", mdwf.MDWF_F32: "f32", mdwf.MDWF_F16N: "f16n"}
 
 
 class Ctx:
-    def __init__(self, dims, Ls, M5, b5, c5, mf, U: np.ndarray):
+    def __init__(self, dims, Ls, M5, b5, c5, mf, U: np.ndarray, dense_s: bool = False):
         self.dims, self.Ls = tuple(dims), Ls
         x, y, z, t = dims
         self.Vh = x * y * z * t // 2
-        self.h = mdwf.mdwf_create(dims, Ls, M5, b5, c5, mf)
+        self.h = mdwf.mdwf_create(dims, Ls, M5, b5, c5, mf, dense_s=dense_s)
         Ud = torch.from_numpy(np.ascontiguousarray(U)).cuda()
         mdwf.mdwf_load_gauge(self.h, Ud)
         torch.cuda.synchronize()

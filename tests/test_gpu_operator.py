@@ -78,6 +78,22 @@ def test_apply_parity_4x4x4x4(b5, c5, prec, dagger):
     check(got, ref, prec)
 
 
+@pytest.mark.parametrize("b5,c5", [(1.5, 0.5), (1.0, 0.0), (2.5, 1.5)])
+@pytest.mark.parametrize("dagger", [False, True])
+def test_dense_tables_match_recursion(b5, c5, dagger):
+    """The Ls x Ls factors applied as dense host-built matrices and by the
+    closed-form elimination give the same operator; both match the oracle."""
+    dims, Ls = (4, 4, 2, 4), 12
+    U, odd, p = setup(dims, Ls, b5, c5, 0.03, 0.3, 6)
+    ref = oracle.m(odd, U, p, dagger=dagger)
+    with Ctx(dims, Ls, 1.8, b5, c5, 0.03, U, dense_s=True) as cd, Ctx(dims, Ls, 1.8, b5, c5, 0.03, U) as cr:
+        for prec in (F64, F32):
+            a = cd.apply(odd, prec, dagger)[0]
+            b = cr.apply(odd, prec, dagger)[0]
+            check(a, ref, prec)
+            check(b, ref, prec)
+
+
 @pytest.mark.parametrize("dims,Ls", [((6, 2, 2, 4), 4), ((4, 2, 2, 2), 12), ((2, 2, 2, 2), 2), ((8, 2, 4, 2), 16)],
                          ids=["Vh48-Ls4", "Vh16-Ls12", "Vh8-Ls2", "Vh64-Ls16"])
 @pytest.mark.parametrize("dagger", [False, True])
