@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-f64", action="store_true", help="skip the plain FP64 solve comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--quick", action="store_true", help="small lattice, for debugging only")
+    ap.add_argument("--solve-only", action="store_true",
+                    help="only the warm-up and timed solves (a short, fixed launch sequence for ncu)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the per-precision Dslash loops, the second inner precision and the e2e leg")
     ap.add_argument("--apply-only", choices=["f64", "f32", "f16n"], default=None,
@@ -280,6 +282,12 @@ def main() -> None:
         torch.cuda.synchronize()
     launches1, applies1 = mdwf.mdwf_counters(h)
     ms = sum(a.elapsed_time(bb) for a, bb in ev)
+    if args.solve_only:
+        print(json.dumps({"solve_only": args.inner, "ms_per_solve": ms / args.steps, "iters": infos[-1].iters,
+                          "true_res": infos[-1].true_res, "launches_per_solve": (launches1 - launches0) / args.steps}),
+              flush=True)
+        mdwf.mdwf_destroy(h)
+        return
     applies = sum(applies1) - sum(applies0)
     flops = applies * FLOPS_PER_SITE * n5
     t = torch.tensor([ms], dtype=torch.float64, device="cuda")

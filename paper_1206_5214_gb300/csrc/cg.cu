@@ -166,6 +166,94 @@ __global__ void __launch_bounds__(kRedThreads) k_pupdate(Field<PP> p, Field<PR> 
     }
 }
 
+// x += alpha p; p = r + beta p (the old p feeds both)
+template <int PX, int PR, int PP>
+__global__ void __launch_bounds__(kRedThreads) k_pupd(Field<PX> x, Field<PR> r, Field<PP> p, const double* sc,
+                                                     Geom g) {
+    typedef typename PrecTraits<PX>::real RX;
+    typedef typename PrecTraits<PR>::real RR;
+    typedef typename PrecTraits<PP>::real RP;
+    const int rhs = blockIdx.y;
+    if (SC(S_ACTIVE, rhs) == 0.0) return;
+    const double alpha = SC(S_ALPHA, rhs);
+    const RP beta = (RP)SC(S_BETA, rhs);
+    SITE_LOOP(g) {
+        const int s = (int)(i % g.Ls);
+        const long long sr = rhs * g.Vh + i / g.Ls;
+        RX xv[24];
+        RR rv[24];
+        RP pv[24];
+        x.load(sr, s, xv);
+        r.load(sr, s, rv);
+        p.load(sr, s, pv);
+#pragma unroll
+        for (int k = 0; k < 24; ++k) {
+            xv[k] += (RX)alpha * (RX)pv[k];
+            pv[k] = (RP)rv[k] + beta * pv[k];
+        }
+        x.store(sr, s, xv);
+        p.store(sr, s, pv);
+    }
+}
+
+// Column-blocked update for the fused iteration: block = (Ls, SB) threads
+// covering SB whole s-columns. x += alpha p; p = r + beta p; then
+// w = M_phi p = b5 p_s + c5 (P+ p_{s-1} + P- p_{s+1}) (mass -m on the
+// wrap-around) with the new p of the neighbouring slices taken from shared
+// memory, so that the first hop of the next iteration reads w without
+// gathering along s.
+template <int PX, int PR, int PP>
+__global__ void __launch_bounds__(128) k_pupd_w(Field<PX> x, Field<PR> r, Field<PP> p, Field<PP> w,
+                                               const double* sc, const typename PrecTraits<PP>::real* mass,
+                                               Geom g, double b5, double c5) {
+    typedef typename PrecTraits<PX>::real RX;
+    typedef typename PrecTraits<PR>::real RR;
+    typedef typename PrecTraits<PP>::real RP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RP* hs = reinterpret_cast<RP*>(smem_raw);
+    const int rhs = blockIdx.y;
+    if (SC(S_ACTIVE, rhs) == 0.0) return;  // uniform over the block
+    const int Ls = g.Ls, s = threadIdx.x, ly = threadIdx.y;
+    const long long site = (long long)blockIdx.x * blockDim.y + ly;
+    const bool active = site < g.Vh;
+    const long long sr = (long long)rhs * g.Vh + site;
+    const double alpha = SC(S_ALPHA, rhs);
+    const RP beta = (RP)SC(S_BETA, rhs);
+    const int sst = site_stride(Ls);
+    RP* row = hs + (size_t)ly * sst;
+    RP pv[24];
+    if (active) {
+        RX xv[24];
+        RR rv[24];
+        x.load(sr, s, xv);
+        r.load(sr, s, rv);
+        p.load(sr, s, pv);
+#pragma unroll
+        for (int k = 0; k < 24; ++k) {
+            xv[k] += (RX)alpha * (RX)pv[k];
+            pv[k] = (RP)rv[k] + beta * pv[k];
+        }
+        x.store(sr, s, xv);
+        p.store(sr, s, pv);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 24; ++k) pv[k] = 0;
+    }
+#pragma unroll
+    for (int k = 0; k < 24; ++k) row[s * kRowStride + k] = pv[k];
+    __syncthreads();
+    if (!active) return;
+    const RP m = mass[rhs];
+    const int sm = s > 0 ? s - 1 : Ls - 1, sp = s < Ls - 1 ? s + 1 : 0;
+    const RP fm = (RP)c5 * (s > 0 ? RP(1) : -m), fp = (RP)c5 * (s < Ls - 1 ? RP(1) : -m);
+    RP wv[24];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) wv[k] = (RP)b5 * pv[k] + fm * row[sm * kRowStride + k];
+#pragma unroll
+    for (int k = 12; k < 24; ++k) wv[k] = (RP)b5 * pv[k] + fp * row[sp * kRowStride + k];
+    w.store(sr, s, wv);
+}
+
 // dst = src (precision conversion); only active right-hand sides when sc != null
 template <int PD, int PS>
 __global__ void __launch_bounds__(kRedThreads) k_copy(Field<PD> d, Field<PS> src, const double* sc, Geom g) {
@@ -253,6 +341,8 @@ struct Solver {
     int nb;             // reduction blocks per right-hand side
     double* sc;         // device scalars [S_NUM][kMaxRhs]
     double* part;       // device partials [nrhs][nb]
+    double* hpart;      // partials of the fused hop epilogues [nrhs][hop blocks]
+    int hb;             // hop blocks per right-hand side
     double* hsc;        // pinned host copy of sc
 
     dim3 grid() const { return dim3(nb, nrhs); }
@@ -261,6 +351,11 @@ struct Solver {
     int fin(int mode, int slot = 0) {
         LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, 8.0 * nrhs * nb, 0.0);
         k_finalize<<<nrhs, kRedThreads, 0, c->stream>>>(part, nb, sc, mode, slot);
+        return check_launch();
+    }
+    int fin_hop(int mode) {
+        LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, 8.0 * nrhs * hb, 0.0);
+        k_finalize<<<nrhs, kRedThreads, 0, c->stream>>>(hpart, hb, sc, mode, 0);
         return check_launch();
     }
     template <int P>
@@ -328,6 +423,82 @@ static int cg_iteration(Solver& S, void* x, void* r, void* p, void* t, void* ap)
     return check_launch();
 }
 
+struct Fields {
+    // FP64: solution, right-hand side of the normal equations, residual, operator temporaries
+    void *xo, *src, *r, *t64, *ap64;
+    // inner iteration (w = M_phi p for the fused iteration)
+    void *xs, *rs, *p, *t, *ap, *w;
+};
+
+template <int PR, int PP>
+static int launch_pupd_w(Solver& S, void* x, void* r, void* p, void* w) {
+    mdwf_ctx* c = S.c;
+    typedef typename PrecTraits<PP>::real RP;
+    const int SB = (128 / S.g.Ls) < 1 ? 1 : 128 / S.g.Ls;
+    dim3 block(S.g.Ls, SB), grid((unsigned)((S.g.Vh + SB - 1) / SB), S.nrhs);
+    const size_t smem = (size_t)SB * site_stride(S.g.Ls) * sizeof(RP);
+    const RP* mass = reinterpret_cast<const RP*>(PP == MDWF_F64 ? (const void*)c->mass64 : (const void*)c->mass32);
+    LaunchScope scope(c, KB_BLAS * 3 + PP, S.n5() * (3.0 * site_bytes(PR) + 3.0 * site_bytes(PP)), S.n5() * 144.0);
+    k_pupd_w<PR, PR, PP><<<grid, block, smem, c->stream>>>(make_field<PR>(x, S.g, S.nrhs),
+                                                            make_field<PR>(r, S.g, S.nrhs),
+                                                            make_field<PP>(p, S.g, S.nrhs),
+                                                            make_field<PP>(w, S.g, S.nrhs), S.sc, mass, S.g,
+                                                            c->b5, c->c5);
+    return check_launch();
+}
+
+// w = M_phi p (the fused iteration's first hop reads w)
+template <int PP>
+static int init_w(Solver& S, void* w, const void* p) {
+    if (S.c->dense_s) return MDWF_OK;
+    M5Launch m{};
+    m.out = w; m.in = p; m.x = nullptr; m.coef = 1.0; m.nrhs = S.nrhs;
+    set_sop(S.c, PP, SOP_MPHI, 0, m);
+    return launch_m5(S.c, PP, m);
+}
+
+// The same iteration with the BLAS folded into the operator kernels:
+//   z = K H_eo M_phi p;  t = p - 1/4 A H_oe z, v = A^dag t, |t|^2 (-> alpha);
+//   z = K^dag H'_eo v;   r -= alpha (t - 1/4 M_phi^dag H'_oe z), |r|^2 (-> beta);
+//   x += alpha p, p = r + beta p.
+template <int PR, int PP>
+static int cg_iteration_fused(Solver& S, void* x, void* r, void* p, void* t, void* w) {
+    mdwf_ctx* c = S.c;
+    int st;
+    note_apply(c, PP);
+    note_apply(c, PP);
+    HopLaunch h{};
+    h.nrhs = S.nrhs;
+    h.b5 = c->b5;
+    h.c5 = c->c5;
+    h.mass = PP == MDWF_F64 ? (const void*)c->mass64 : (const void*)c->mass32;
+    // z = K H_eo w, w = M_phi p (formed by the previous update)
+    h.out = c->tmp[0].p; h.in = w; h.x = nullptr; h.coef = 1.0; h.out_parity = 0; h.gather = 0; h.dagger = 0;
+    set_sop(c, PP, SOP_K, 0, h);
+    if ((st = launch_hop(c, PP, h))) return st;
+    h.out = t; h.in = c->tmp[0].p; h.x = p; h.coef = -0.25; h.out_parity = 1; h.gather = 0; h.dagger = 0;
+    set_sop(c, PP, SOP_A, 0, h);
+    h.fuse = 1; h.out2 = c->tmp[1].p; h.part = S.hpart; h.sc = S.sc;
+    if ((st = launch_hop(c, PP, h))) return st;
+    if ((st = S.fin_hop(FIN_ALPHA))) return st;
+    h.out = c->tmp[0].p; h.in = c->tmp[1].p; h.x = nullptr; h.coef = 1.0; h.out_parity = 0; h.dagger = 1;
+    set_sop(c, PP, SOP_K, 1, h);
+    h.fuse = 0;
+    if ((st = launch_hop(c, PP, h))) return st;
+    h.out = c->tmp[1].p; h.in = c->tmp[0].p; h.x = t; h.coef = -0.25; h.out_parity = 1; h.dagger = 1;
+    set_sop(c, PP, SOP_MPHI, 1, h);
+    h.fuse = 2; h.rfield = r; h.part = S.hpart; h.sc = S.sc;
+    if ((st = launch_hop(c, PP, h))) return st;
+    if ((st = S.fin_hop(FIN_BETA))) return st;
+    return launch_pupd_w<PR, PP>(S, x, r, p, w);
+}
+
+template <int PR, int PP>
+static int iterate(Solver& S, Fields& F, void* x, void* r) {
+    if (!S.c->dense_s) return cg_iteration_fused<PR, PP>(S, x, r, F.p, F.t, F.w);
+    return cg_iteration<PR, PP>(S, x, r, F.p, F.t, F.ap);
+}
+
 // r = src - M^dag M x in FP64 (active rhs), r_s = r in precision PS; |r|^2 -> S_AUX
 template <int PS, bool COPY>
 static int true_residual(Solver& S, void* r, void* rs, const void* src, const void* x, void* t64, void* ap64,
@@ -346,12 +517,6 @@ static int true_residual(Solver& S, void* r, void* rs, const void* src, const vo
     return S.fin(FIN_STORE, S_AUX);
 }
 
-struct Fields {
-    // FP64: solution, right-hand side of the normal equations, residual, operator temporaries
-    void *xo, *src, *r, *t64, *ap64;
-    // inner iteration
-    void *xs, *rs, *p, *t, *ap;
-};
 
 // last_true[r] receives |src - M^dag M x|^2 of the FP64 solution x each time
 // it is recomputed; x changes only at those points, so the final value
@@ -368,6 +533,7 @@ static int run_mixed(Solver& S, Fields& F, const mdwf_solve_params& prm, double 
     if ((st = S.copy<MDWF_F32, MDWF_F64>(F.rs, F.src, false))) return st;
     if ((st = cuda_status(cudaMemsetAsync(F.xs, 0, field_bytes(MDWF_F32, S.g, nrhs), c->stream)))) return st;
     if ((st = S.copy<PP, MDWF_F64>(F.p, F.src, false))) return st;
+    if ((st = init_w<PP>(S, F.w, F.p))) return st;
     if ((st = S.norm<MDWF_F64>(F.src, false, S_RR))) return st;
     if ((st = S.pull())) return st;
     for (int r = 0; r < nrhs; ++r) {
@@ -387,7 +553,7 @@ static int run_mixed(Solver& S, Fields& F, const mdwf_solve_params& prm, double 
                 cudaGraph_t graph;
                 if ((st = cuda_status(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal)))) return st;
                 begin_capture(c);
-                int st2 = cg_iteration<MDWF_F32, PP>(S, F.xs, F.rs, F.p, F.t, F.ap);
+                int st2 = iterate<MDWF_F32, PP>(S, F, F.xs, F.rs);
                 c->capturing = false;
                 st = cuda_status(cudaStreamEndCapture(c->stream, &graph));
                 if (st2) return st2;
@@ -403,7 +569,7 @@ static int run_mixed(Solver& S, Fields& F, const mdwf_solve_params& prm, double 
             }
         } else {
             for (int k = 0; k < steps; ++k)
-                if ((st = cg_iteration<MDWF_F32, PP>(S, F.xs, F.rs, F.p, F.t, F.ap))) return st;
+                if ((st = iterate<MDWF_F32, PP>(S, F, F.xs, F.rs))) return st;
         }
         it += steps;
         if ((st = S.pull())) return st;
@@ -467,6 +633,7 @@ static int run_plain(Solver& S, Fields& F, const mdwf_solve_params& prm, double 
         if ((st = S.push())) return st;
         if (!any || it >= maxiter) break;
         if ((st = S.copy<MDWF_F64, MDWF_F64>(F.p, F.r, true))) return st;
+        if ((st = init_w<MDWF_F64>(S, F.w, F.p))) return st;
         while (it < maxiter) {
             const int steps = (maxiter - it) < every ? (maxiter - it) : every;
             if (use_graph) {
@@ -475,7 +642,7 @@ static int run_plain(Solver& S, Fields& F, const mdwf_solve_params& prm, double 
                     if ((st = cuda_status(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal))))
                         return st;
                     begin_capture(c);
-                    int st2 = cg_iteration<MDWF_F64, MDWF_F64>(S, F.xo, F.r, F.p, F.t, F.ap);
+                    int st2 = iterate<MDWF_F64, MDWF_F64>(S, F, F.xo, F.r);
                     c->capturing = false;
                     st = cuda_status(cudaStreamEndCapture(c->stream, &graph));
                     if (st2) return st2;
@@ -491,7 +658,7 @@ static int run_plain(Solver& S, Fields& F, const mdwf_solve_params& prm, double 
                 }
             } else {
                 for (int k = 0; k < steps; ++k)
-                    if ((st = cg_iteration<MDWF_F64, MDWF_F64>(S, F.xo, F.r, F.p, F.t, F.ap))) return st;
+                    if ((st = iterate<MDWF_F64, MDWF_F64>(S, F, F.xo, F.r))) return st;
             }
             it += steps;
             if ((st = S.pull())) return st;
@@ -591,8 +758,10 @@ int solve_normal(mdwf_ctx* c, int nrhs, void* xo, const void* src, const mdwf_so
     const size_t fpp = field_bytes(inner, g, nrhs);
     auto up = [](size_t v) { return (v + 255) / 256 * 256; };
     const int nb = 2 * 152;
-    const size_t need = up(f64) * 3 + (inner == MDWF_F64 ? up(f64) * 3 : up(f32) * 2 + up(fpp) * 3) +
-                        up(sizeof(double) * S_NUM * kMaxRhs) + up(sizeof(double) * nrhs * nb);
+    const int hb = hop_blocks(c);
+    const size_t need = up(f64) * 3 + (inner == MDWF_F64 ? up(f64) * 4 : up(f32) * 2 + up(fpp) * 4) +
+                        up(sizeof(double) * S_NUM * kMaxRhs) + up(sizeof(double) * nrhs * nb) +
+                        up(sizeof(double) * nrhs * hb);
     Fields F{};
     Solver S{};
     cudaGraphExec_t gexec = nullptr;
@@ -608,13 +777,15 @@ int solve_normal(mdwf_ctx* c, int nrhs, void* xo, const void* src, const mdwf_so
         F.src = const_cast<void*>(src);
         F.r = take(f64); F.t64 = take(f64); F.ap64 = take(f64);
         if (inner == MDWF_F64) {
-            F.p = take(f64); F.t = take(f64); F.ap = take(f64);
+            F.p = take(f64); F.t = take(f64); F.ap = take(f64); F.w = take(f64);
         } else {
-            F.xs = take(f32); F.rs = take(f32); F.p = take(fpp); F.t = take(fpp); F.ap = take(fpp);
+            F.xs = take(f32); F.rs = take(f32); F.p = take(fpp); F.t = take(fpp); F.ap = take(fpp); F.w = take(fpp);
         }
         S.c = c; S.g = g; S.nrhs = nrhs; S.nb = nb;
         S.sc = (double*)take(sizeof(double) * S_NUM * kMaxRhs);
         S.part = (double*)take(sizeof(double) * nrhs * nb);
+        S.hpart = (double*)take(sizeof(double) * nrhs * hb);
+        S.hb = hb;
         if ((st = cuda_status(cudaMallocHost(&hsc, sizeof(double) * S_NUM * kMaxRhs)))) { ret = st; break; }
         S.hsc = hsc;
         memset(hsc, 0, sizeof(double) * S_NUM * kMaxRhs);

@@ -160,15 +160,46 @@ __device__ __forceinline__ void hop_dir(R* acc, const Field<P>& in, const Gauge<
     }
 }
 
-template <int P, bool GATHER, bool DAG, bool XPAY>
-__global__ void __launch_bounds__(128, PrecTraits<P>::min_blocks - (GATHER ? 1 : 0)) hop_kernel(Field<P> out, Field<P> in, Field<P> xf, Gauge<P> U,
-                                                  HopParams<typename PrecTraits<P>::real> hp) {
+// Fused CG epilogues (structured s-operators only):
+//   FUSE_T : after out = t = M p is formed, also write v = A^dag t (the first
+//            factor of M^dag) to out2 and the block's partial |t|^2 to part
+//   FUSE_R : out = Ap = M^dag t is not stored; instead r -= alpha Ap in the
+//            residual field (precision PR) and the partial |r|^2 goes to part
+enum { FUSE_NONE = 0, FUSE_T = 1, FUSE_R = 2 };
+
+template <int P> struct ResPrec { static constexpr int value = P == MDWF_F64 ? MDWF_F64 : MDWF_F32; };
+
+template <int P> struct FuseArgs {
+    Field<P> out2;                     // FUSE_T: v = A^dag t
+    Field<ResPrec<P>::value> rf;       // FUSE_R: residual r
+    double* part;                      // [rhs][blockIdx.x] partial sums
+    const double* sc;                  // CG scalars [slot][64]: alpha at slot 2, active flag at slot 5
+};
+
+__device__ __forceinline__ double block_sum128(double v, double* red) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthr = blockDim.x * blockDim.y;
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    double tot = 0;
+    if (tid == 0)
+        for (int w = 0; w < (nthr + 31) / 32; ++w) tot += red[w];
+    return tot;
+}
+
+template <int P, bool GATHER, bool DAG, bool XPAY, int FUSE>
+__global__ void __launch_bounds__(128, PrecTraits<P>::min_blocks - (GATHER ? 1 : 0))
+    hop_kernel(Field<P> out, Field<P> in, Field<P> xf, Gauge<P> U, HopParams<typename PrecTraits<P>::real> hp,
+               FuseArgs<P> fa) {
     typedef typename PrecTraits<P>::real R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Ls = hp.g.Ls;
     const bool dense = hp.sop == SOP_DENSE;
-    R* mat = reinterpret_cast<R*>(smem_raw);          // [chir][s'][s] (dense only)
-    R* hs = mat + (dense ? 2 * Ls * Ls : 0);          // [SB][Ls][24]
+    double* red = reinterpret_cast<double*>(smem_raw);          // [4] block reduction
+    R* mat = reinterpret_cast<R*>(smem_raw + 4 * sizeof(double)); // [chir][s'][s] (dense only)
+    R* hs = mat + (dense ? 2 * Ls * Ls : 0);                      // [SB][site_stride], rows of kRowStride
     const int s = threadIdx.x, ly = threadIdx.y;
     const int rhs = blockIdx.y;
     const int tid = ly * blockDim.x + s, nthr = blockDim.x * blockDim.y;
@@ -191,20 +222,20 @@ __global__ void __launch_bounds__(128, PrecTraits<P>::min_blocks - (GATHER ? 1 :
         hop_dir<P, 2, GATHER, DAG>(acc, in, U, hp, f.z, b.z, site, s, rbase, mass);
         hop_dir<P, 3, GATHER, DAG>(acc, in, U, hp, f.w, b.w, site, s, rbase, mass);
     }
-    R* mine = hs + ((size_t)ly * Ls + s) * 24;
+    const int sst = site_stride(Ls);
+    R* mine = hs + (size_t)ly * sst + s * kRowStride;
 #pragma unroll
     for (int k = 0; k < 24; ++k) mine[k] = acc[k];
     __syncthreads();
     R res[24];
     if (dense) {
-        if (!active) return;
 #pragma unroll
         for (int k = 0; k < 24; ++k) res[k] = 0;
-        const R* col = hs + (size_t)ly * Ls * 24;
+        const R* col = hs + (size_t)ly * sst;
         for (int sp = 0; sp < Ls; ++sp) {
             const R mp = mat[sp * Ls + s];         // (s, s') of the P+ matrix
             const R mm = mat[(Ls + sp) * Ls + s];  // (s, s') of the P- matrix
-            const R* h = col + sp * 24;
+            const R* h = col + sp * kRowStride;
 #pragma unroll
             for (int k = 0; k < 12; ++k) res[k] += mp * h[k];
 #pragma unroll
@@ -213,20 +244,59 @@ __global__ void __launch_bounds__(128, PrecTraits<P>::min_blocks - (GATHER ? 1 :
     } else {
         block_columns(hs, blockDim.y, Ls, hp.sop, hp.swap != 0, hp.sc, mass, tid, nthr);
         __syncthreads();
-        if (!active) return;
 #pragma unroll
         for (int k = 0; k < 24; ++k) res[k] = mine[k];
     }
+    if (FUSE == FUSE_NONE && !active) return;
     const R cf = hp.coef * hp.gscale;
 #pragma unroll
     for (int k = 0; k < 24; ++k) res[k] *= cf;
-    if (XPAY) {
+    if (XPAY && active) {
         R xv[24];
         xf.load(rbase + site, s, xv);
 #pragma unroll
         for (int k = 0; k < 24; ++k) res[k] += xv[k];
     }
-    out.store(rbase + site, s, res);
+    if (FUSE == FUSE_NONE) {
+        out.store(rbase + site, s, res);
+        return;
+    }
+    double sq = 0;
+    if (FUSE == FUSE_T) {
+        if (active) {
+            out.store(rbase + site, s, res);
+#pragma unroll
+            for (int k = 0; k < 24; ++k) sq += (double)res[k] * (double)res[k];
+        }
+        // v = A^dag t through the same column machinery
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 24; ++k) mine[k] = active ? res[k] : R(0);
+        __syncthreads();
+        block_columns(hs, blockDim.y, Ls, SOP_A, true, hp.sc, mass, tid, nthr);
+        __syncthreads();
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < 24; ++k) res[k] = mine[k];
+            fa.out2.store(rbase + site, s, res);
+        }
+    } else {  // FUSE_R
+        typedef typename PrecTraits<ResPrec<P>::value>::real RR;
+        const bool live = fa.sc[5 * 64 + rhs] != 0.0;
+        if (active && live) {
+            const RR alpha = (RR)fa.sc[2 * 64 + rhs];
+            RR rv[24];
+            fa.rf.load(rbase + site, s, rv);
+#pragma unroll
+            for (int k = 0; k < 24; ++k) {
+                rv[k] -= alpha * (RR)res[k];
+                sq += (double)rv[k] * (double)rv[k];
+            }
+            fa.rf.store(rbase + site, s, rv);
+        }
+    }
+    const double tot = block_sum128(sq, red);
+    if (tid == 0) fa.part[(size_t)rhs * gridDim.x + blockIdx.x] = tot;
 }
 
 // ---------------------------------------------------------------- launcher
@@ -236,14 +306,19 @@ static int sites_per_block(int Ls) {
     return sb < 1 ? 1 : sb;
 }
 
-template <int P, bool G, bool D, bool X>
+int hop_blocks(const mdwf_ctx* c) {
+    const int SB = sites_per_block(c->g.Ls);
+    return (int)((c->g.Vh + SB - 1) / SB);
+}
+
+template <int P, bool G, bool D, bool X, int FU>
 static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<typename PrecTraits<P>::real>& hp) {
     typedef typename PrecTraits<P>::real R;
     const Geom& g = c->g;
     const int SB = sites_per_block(g.Ls);
     dim3 block(g.Ls, SB), grid((unsigned)((g.Vh + SB - 1) / SB), h.nrhs);
-    size_t smem = (size_t)((hp.sop == SOP_DENSE ? 2 * g.Ls * g.Ls : 0) + SB * g.Ls * 24) * sizeof(R);
-    auto kern = hop_kernel<P, G, D, X>;
+    size_t smem = 4 * sizeof(double) + (size_t)((hp.sop == SOP_DENSE ? 2 * g.Ls * g.Ls : 0) + SB * site_stride(g.Ls)) * sizeof(R);
+    auto kern = hop_kernel<P, G, D, X, FU>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_status(e);
@@ -251,15 +326,25 @@ static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<t
     Field<P> out = make_field<P>(h.out, g, h.nrhs);
     Field<P> in = make_field<P>(const_cast<void*>(h.in), g, h.nrhs);
     Field<P> xf = h.x ? make_field<P>(const_cast<void*>(h.x), g, h.nrhs) : out;
+    FuseArgs<P> fa;
+    fa.out2 = make_field<P>(h.out2 ? h.out2 : h.out, g, h.nrhs);
+    fa.rf = make_field<ResPrec<P>::value>(h.rfield ? h.rfield : h.out, g, h.nrhs);
+    fa.part = h.part;
+    fa.sc = h.sc;
     Gauge<P> U;
     U.u = reinterpret_cast<decltype(U.u)>(c->gauge[link_copy(P)]);
     const int base = D ? (X ? KB_HOP_DAG_XPAY : KB_HOP_DAG)
                        : G ? (X ? KB_HOP_GATHER_XPAY : KB_HOP_GATHER) : (X ? KB_HOP_XPAY : KB_HOP);
     const double n5 = (double)g.Vh * g.Ls * h.nrhs;
-    const double bytes = n5 * site_bytes(P) * (X ? 3.0 : 2.0) + 8.0 * g.Vh * link_bytes(P);
-    const double flops = n5 * (1320.0 + (G ? 72.0 : 0.0) + 144.0 + (X ? 48.0 : 0.0));
+    // fields moved: in, out (+x), and for the fused epilogues v (FUSE_T) or r read+write instead of out (FUSE_R)
+    const double sp = site_bytes(P), sr = site_bytes(ResPrec<P>::value);
+    double fields = sp + sp + (X ? sp : 0.0);
+    if (FU == FUSE_T) fields += sp;
+    if (FU == FUSE_R) fields += 2.0 * sr - sp;
+    const double bytes = n5 * fields + 8.0 * g.Vh * link_bytes(P);
+    const double flops = n5 * (1320.0 + (G ? 72.0 : 0.0) + 144.0 + (X ? 48.0 : 0.0) + (FU ? 144.0 : 0.0));
     LaunchScope scope(c, base * 3 + P, bytes, flops);
-    kern<<<grid, block, smem, c->stream>>>(out, in, xf, U, hp);
+    kern<<<grid, block, smem, c->stream>>>(out, in, xf, U, hp, fa);
     return check_launch();
 }
 
@@ -287,16 +372,23 @@ static int launch_hop_t(mdwf_ctx* c, const HopLaunch& h) {
     hp.sc.Mp = (R)(c->b5 * (4.0 - c->M5) + 1.0);
     hp.sc.Mm = (R)(c->c5 * (4.0 - c->M5) - 1.0);
     const bool X = h.x != nullptr;
+    if (h.fuse != FUSE_NONE) {
+        // fused CG epilogues: t = M p with v = A^dag t, or Ap = M^dag t folded into r
+        if (h.sop == SOP_DENSE || !X || h.gather || !h.part || !h.sc) return MDWF_EINVAL;
+        if (h.fuse == FUSE_T && !h.dagger && h.out2) return launch_hop_variant<P, false, false, true, FUSE_T>(c, h, hp);
+        if (h.fuse == FUSE_R && h.dagger && h.rfield) return launch_hop_variant<P, false, true, true, FUSE_R>(c, h, hp);
+        return MDWF_EINVAL;
+    }
     if (h.gather) {
         if (h.dagger) return MDWF_EINVAL;
-        return X ? launch_hop_variant<P, true, false, true>(c, h, hp)
-                 : launch_hop_variant<P, true, false, false>(c, h, hp);
+        return X ? launch_hop_variant<P, true, false, true, FUSE_NONE>(c, h, hp)
+                 : launch_hop_variant<P, true, false, false, FUSE_NONE>(c, h, hp);
     }
     if (h.dagger)
-        return X ? launch_hop_variant<P, false, true, true>(c, h, hp)
-                 : launch_hop_variant<P, false, true, false>(c, h, hp);
-    return X ? launch_hop_variant<P, false, false, true>(c, h, hp)
-             : launch_hop_variant<P, false, false, false>(c, h, hp);
+        return X ? launch_hop_variant<P, false, true, true, FUSE_NONE>(c, h, hp)
+                 : launch_hop_variant<P, false, true, false, FUSE_NONE>(c, h, hp);
+    return X ? launch_hop_variant<P, false, false, true, FUSE_NONE>(c, h, hp)
+             : launch_hop_variant<P, false, false, false, FUSE_NONE>(c, h, hp);
 }
 
 int launch_hop(mdwf_ctx* c, int prec, const HopLaunch& h) {

@@ -34,7 +34,8 @@ __global__ void __launch_bounds__(256) m5_kernel(Field<P> out, Field<P> in, Fiel
 #pragma unroll
         for (int k = 0; k < 24; ++k) v[k] = 0;
     }
-    R* mine = cs + ((size_t)ly * Ls + s) * 24;
+    const int sst = site_stride(Ls);
+    R* mine = cs + (size_t)ly * sst + s * kRowStride;
 #pragma unroll
     for (int k = 0; k < 24; ++k) mine[k] = v[k];
     __syncthreads();
@@ -43,10 +44,10 @@ __global__ void __launch_bounds__(256) m5_kernel(Field<P> out, Field<P> in, Fiel
         if (!active) return;
 #pragma unroll
         for (int k = 0; k < 24; ++k) res[k] = 0;
-        const R* col = cs + (size_t)ly * Ls * 24;
+        const R* col = cs + (size_t)ly * sst;
         for (int sp = 0; sp < Ls; ++sp) {
             const R mp = mat[sp * Ls + s], mm = mat[(Ls + sp) * Ls + s];
-            const R* h = col + sp * 24;
+            const R* h = col + sp * kRowStride;
 #pragma unroll
             for (int k = 0; k < 12; ++k) res[k] += mp * h[k];
 #pragma unroll
@@ -77,7 +78,7 @@ static int launch_m5_t(mdwf_ctx* c, const M5Launch& m) {
     int SB = 128 / g.Ls;
     if (SB < 1) SB = 1;
     dim3 block(g.Ls, SB), grid((unsigned)((g.Vh + SB - 1) / SB), m.nrhs);
-    size_t smem = (size_t)((m.sop == SOP_DENSE ? 2 * g.Ls * g.Ls : 0) + SB * g.Ls * 24) * sizeof(R);
+    size_t smem = (size_t)((m.sop == SOP_DENSE ? 2 * g.Ls * g.Ls : 0) + SB * site_stride(g.Ls)) * sizeof(R);
     Field<P> out = make_field<P>(m.out, g, m.nrhs);
     Field<P> in = make_field<P>(const_cast<void*>(m.in), g, m.nrhs);
     Field<P> xf = m.x ? make_field<P>(const_cast<void*>(m.x), g, m.nrhs) : out;

@@ -310,16 +310,28 @@ __device__ __forceinline__ void column_op(R* base, int stride, int Ls, int op, b
     }
 }
 
-// Applies the s-operator to the SB staged columns hs[site][s][24] of a block
-// (tasks = (site, complex component); P+ components are j < 6). Dense tables
-// are applied by the caller instead.
+// Shared-memory staging of a block's columns: spinor (site ly, slice s) at
+// hs + ly * site_stride + s * kRowStride. The row stride of 28 words keeps the
+// 16-byte row accesses of 8 consecutive threads on distinct banks, and a site
+// stride = 24 (mod 32) words keeps the 64-bit column accesses of a warp
+// (12 components of consecutive sites) conflict-free.
+constexpr int kRowStride = 28;
+__host__ __device__ inline int site_stride(int Ls) {
+    const int base = Ls * kRowStride;
+    return base + ((24 - base % 32) + 32) % 32;
+}
+
+// Applies the s-operator to the SB staged columns of a block (tasks = (site,
+// complex component); P+ components are j < 6). Dense tables are applied by
+// the caller instead.
 template <typename R>
 __device__ __forceinline__ void block_columns(R* hs, int SB, int Ls, int op, bool swap, const SCoef<R>& sc,
                                               R m, int tid, int nthr) {
+    const int ss = site_stride(Ls);
     for (int t = tid; t < SB * 12; t += nthr) {
         const int ly = t / 12, j = t - 12 * (t / 12);
         const bool up = (j >= 6) != swap;  // P- uses N' unless the adjoint swaps
-        column_op(hs + (size_t)ly * Ls * 24 + 2 * j, 24, Ls, op, up, sc, m);
+        column_op(hs + (size_t)ly * ss + 2 * j, kRowStride, Ls, op, up, sc, m);
     }
 }
 
@@ -467,8 +479,16 @@ struct HopLaunch {
     const void* mass;     // per-rhs masses (double for F64, float otherwise)
     double b5, c5;
     int nrhs;
+    // fused CG epilogues (0: none; 1: also v = A^dag out into out2 and |out|^2
+    // partials; 2: r -= alpha out into rfield with |r|^2 partials, out not stored)
+    int fuse;
+    void* out2;
+    void* rfield;         // FP64 field for FP64 operators, FP32 otherwise
+    double* part;         // [rhs][hop_blocks] partial sums
+    const double* sc;     // CG scalars
 };
 int launch_hop(mdwf_ctx* c, int prec, const HopLaunch& h);
+int hop_blocks(const mdwf_ctx* c);
 
 struct M5Launch {
     void* out;
