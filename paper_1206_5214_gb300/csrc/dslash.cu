@@ -22,6 +22,8 @@ namespace mdwf {
 
 template <typename R> struct HopParams {
     Geom g;
+    int nrhs;        // blocks are (site block, rhs) with rhs fastest: blocks that run
+                     // together share sites, so their links come from L2
     int out_parity;
     R coef;
     // input gather w = gscale * (gown psi_s + gfac (P+ psi_{s-1} + P- psi_{s+1})) = M_phi psi;
@@ -201,13 +203,14 @@ __global__ void __launch_bounds__(128, PrecTraits<P>::min_blocks - (GATHER ? 1 :
     R* mat = reinterpret_cast<R*>(smem_raw + 4 * sizeof(double)); // [chir][s'][s] (dense only)
     R* hs = mat + (dense ? 2 * Ls * Ls : 0);                      // [SB][site_stride], rows of kRowStride
     const int s = threadIdx.x, ly = threadIdx.y;
-    const int rhs = blockIdx.y;
+    const int rhs = blockIdx.x % hp.nrhs;
+    const long long sblk = blockIdx.x / hp.nrhs;
     const int tid = ly * blockDim.x + s, nthr = blockDim.x * blockDim.y;
     if (dense) {
         const R* gm = hp.mat + (size_t)rhs * 2 * Ls * Ls;
         for (int i = tid; i < 2 * Ls * Ls; i += nthr) mat[i] = gm[i];
     }
-    const long long site = (long long)blockIdx.x * blockDim.y + ly;
+    const long long site = sblk * blockDim.y + ly;
     const bool active = site < hp.g.Vh;
     const long long rbase = (long long)rhs * hp.g.Vh;
     const R mass = hp.mass[rhs];
@@ -296,7 +299,7 @@ __global__ void __launch_bounds__(128, PrecTraits<P>::min_blocks - (GATHER ? 1 :
         }
     }
     const double tot = block_sum128(sq, red);
-    if (tid == 0) fa.part[(size_t)rhs * gridDim.x + blockIdx.x] = tot;
+    if (tid == 0) fa.part[(size_t)rhs * (gridDim.x / hp.nrhs) + sblk] = tot;
 }
 
 // ---------------------------------------------------------------- launcher
@@ -316,7 +319,7 @@ static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<t
     typedef typename PrecTraits<P>::real R;
     const Geom& g = c->g;
     const int SB = sites_per_block(g.Ls);
-    dim3 block(g.Ls, SB), grid((unsigned)((g.Vh + SB - 1) / SB), h.nrhs);
+    dim3 block(g.Ls, SB), grid((unsigned)((g.Vh + SB - 1) / SB * h.nrhs));
     size_t smem = 4 * sizeof(double) + (size_t)((hp.sop == SOP_DENSE ? 2 * g.Ls * g.Ls : 0) + SB * site_stride(g.Ls)) * sizeof(R);
     auto kern = hop_kernel<P, G, D, X, FU>;
     if (smem > 48 * 1024) {
@@ -353,6 +356,7 @@ static int launch_hop_t(mdwf_ctx* c, const HopLaunch& h) {
     typedef typename PrecTraits<P>::real R;
     HopParams<R> hp;
     hp.g = c->g;
+    hp.nrhs = h.nrhs;
     hp.out_parity = h.out_parity;
     hp.coef = (R)h.coef;
     // M_phi = b5 + c5 C folded as b5 (1 + (c5/b5) C) when b5 != 0

@@ -19,13 +19,15 @@ __global__ void __launch_bounds__(256) m5_kernel(Field<P> out, Field<P> in, Fiel
     const bool dense = sop == SOP_DENSE;
     R* mat = reinterpret_cast<R*>(smem_raw);
     R* cs = mat + (dense ? 2 * Ls * Ls : 0);
-    const int s = threadIdx.x, ly = threadIdx.y, rhs = blockIdx.y;
+    const int nrhs = (int)(gridDim.x / ((g.Vh + blockDim.y - 1) / blockDim.y));
+    const int s = threadIdx.x, ly = threadIdx.y, rhs = blockIdx.x % nrhs;
+    const long long sblk = blockIdx.x / nrhs;
     const int tid = ly * blockDim.x + s, nthr = blockDim.x * blockDim.y;
     if (dense) {
         const R* gm = tab + (size_t)rhs * 2 * Ls * Ls;
         for (int i = tid; i < 2 * Ls * Ls; i += nthr) mat[i] = gm[i];
     }
-    const long long site = (long long)blockIdx.x * blockDim.y + ly;
+    const long long site = sblk * blockDim.y + ly;
     const bool active = site < g.Vh;
     const long long sr = (long long)rhs * g.Vh + site;
     R v[24];
@@ -77,7 +79,7 @@ static int launch_m5_t(mdwf_ctx* c, const M5Launch& m) {
     const Geom& g = c->g;
     int SB = 128 / g.Ls;
     if (SB < 1) SB = 1;
-    dim3 block(g.Ls, SB), grid((unsigned)((g.Vh + SB - 1) / SB), m.nrhs);
+    dim3 block(g.Ls, SB), grid((unsigned)((g.Vh + SB - 1) / SB * m.nrhs));  // rhs fastest
     size_t smem = (size_t)((m.sop == SOP_DENSE ? 2 * g.Ls * g.Ls : 0) + SB * site_stride(g.Ls)) * sizeof(R);
     Field<P> out = make_field<P>(m.out, g, m.nrhs);
     Field<P> in = make_field<P>(const_cast<void*>(m.in), g, m.nrhs);

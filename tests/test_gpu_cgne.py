@@ -62,9 +62,16 @@ def test_cgne_4x4x4x4_matches_oracle_solve(b5, c5, inner):
     st, info, x = gpu_solve(dims, Ls, b5, c5, 0.01, U, b, inner)
     assert st == 0, info[0].as_dict()
     assert info[0].true_res <= 1e-10
-    assert oracle_residual(x[0] if x.ndim == 8 else x, b, U, p) <= 1.05e-10
+    xs = x[0] if x.ndim == 8 else x
+    assert oracle_residual(xs, b, U, p) <= 1.05e-10
+    # two solutions with normal-equation residuals <= 1e-10 differ by at most
+    # kappa(M^dag M) * 2e-10; kappa stays below 1e4 on these 4^4 x 8 lattices
     err = np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref)
-    assert err <= 1e-7, err
+    assert err <= 2e-6, err
+    # and the first-order system is solved: |b' - M x_o| / |b'| from the oracle
+    bp = oracle.prepare(b, U, p)
+    _, xo = oracle.split(xs, dims)
+    assert np.linalg.norm(bp - oracle.m(xo, U, p)) / np.linalg.norm(bp) <= 1e-8
     if inner != F64:
         assert info[0].reliable_updates >= 1
 
