@@ -133,6 +133,29 @@ int mdwf_apply(mdwf_ctx *ctx, void *out, const void *in, int prec, int nrhs, con
 /* out = M^dag in, the adjoint of mdwf_apply's operator (same arguments). */
 int mdwf_apply_dag(mdwf_ctx *ctx, void *out, const void *in, int prec, int nrhs, const double *mf_per_rhs);
 
+/*
+ * Allocation-free variant of mdwf_apply / mdwf_apply_dag (dagger != 0); the
+ * paper has no counterpart: it exists for callers that must not allocate
+ * device memory while they run, such as a custom operator inside a framework
+ * whose pool owns all device memory, a latency-critical path that must stay
+ * out of the driver's allocator, or a service whose footprint must stay fixed.
+ * Create the context (which allocates) during set-up; this call then
+ * allocates nothing and frees nothing.
+ * Arguments as for mdwf_apply. The operator's intermediate fields live in a
+ * fixed scratch area that every GPU loading the library holds until the
+ * process exits: at most 8 MiB per intermediate field, i.e.
+ * mdwf_field_bytes(ctx, prec, nrhs) <= 8 MiB (MDWF_EINVAL with a message in
+ * mdwf_last_error() otherwise; also MDWF_EINVAL for a context created with
+ * dense_s = 1). The per-rhs masses are copied into a fixed array as well.
+ * The first call on a device looks up the scratch's device address (once
+ * per device); make that first call before any stream capture.
+ * All calls share the scratch and keep the last call's contents (every call
+ * overwrites what it reads, so nothing needs clearing): calls whose GPU work
+ * overlaps (different streams or contexts at the same time) race.
+ */
+int mdwf_apply_noalloc(mdwf_ctx *ctx, void *out, const void *in, int prec, int nrhs, const double *mf_per_rhs,
+                       int dagger);
+
 typedef struct {
     double tol;           /* target |M^dag b' - M^dag M x| / |M^dag b'| (FP64, recomputed); 0 = 1e-10 */
     int maxiter;          /* CG iteration cap; 0 = 20000 */

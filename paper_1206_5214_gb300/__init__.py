@@ -19,7 +19,7 @@ __all__ = [
     "MDWF_F64", "MDWF_F32", "MDWF_F16N", "MdwfError", "lib_path", "load",
     "mdwf_create", "mdwf_destroy", "mdwf_set_stream", "mdwf_load_gauge", "mdwf_field_bytes",
     "mdwf_field_import", "mdwf_field_export", "mdwf_apply", "mdwf_apply_dag", "mdwf_cgne",
-    "mdwf_strerror", "mdwf_force", "mdwf_profile_enable", "mdwf_profile_read", "mdwf_counters", "SolveParams",
+    "mdwf_strerror", "mdwf_force", "mdwf_apply_noalloc", "mdwf_profile_enable", "mdwf_profile_read", "mdwf_counters", "SolveParams",
     "SolveInfo", "KernelStat",
 ]
 
@@ -88,6 +88,7 @@ def load(build_if_missing: bool = True):
         "mdwf_apply": (ip, [vp, vp, vp, ip, ip, dp]),
         "mdwf_apply_dag": (ip, [vp, vp, vp, ip, ip, dp]),
         "mdwf_cgne": (ip, [vp, vp, vp, ip, dp, ip, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]),
+        "mdwf_apply_noalloc": (ip, [vp, vp, vp, ip, ip, dp, ip]),
         "mdwf_force": (ip, [vp, vp, dp, dp, dp, vp, ip, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]),
         "mdwf_profile_enable": (ip, [vp, ip]),
         "mdwf_profile_read": (ip, [vp, ctypes.POINTER(KernelStat), ip, ctypes.POINTER(ctypes.c_int), ip]),
@@ -212,6 +213,14 @@ def mdwf_cgne(ctx, x, b, nrhs: int = 1, mf_per_rhs=None, tol: float = 1e-10, max
     if raise_on_error and st not in (0,):
         raise MdwfError(st, "mdwf_cgne")
     return st, list(infos)
+
+
+def mdwf_apply_noalloc(ctx, out, inp, prec: int, nrhs: int = 1, mf_per_rhs=None, dagger: bool = False) -> None:
+    """M (or M^dag) like mdwf_apply, with the intermediates in the library's fixed scratch (no allocation)."""
+    po, _ = _ptr_where(out)
+    pi, _ = _ptr_where(inp)
+    _check(load().mdwf_apply_noalloc(ctx, po, pi, int(prec), int(nrhs), _masses(mf_per_rhs), int(bool(dagger))),
+           "mdwf_apply_noalloc")
 
 
 def mdwf_force(ctx, dSdU, phi, tol: float = 1e-12, maxiter: int = 40000, inner_prec: int = MDWF_F64,

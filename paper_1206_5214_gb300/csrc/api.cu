@@ -37,6 +37,8 @@ int cuda_status(cudaError_t e) {
 
 int check_launch() { return cuda_status(cudaGetLastError()); }
 
+void set_error_message(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
 // ----------------------------------------------------------- instrumentation
 
 static cudaEvent_t take_event(mdwf_ctx* c) {

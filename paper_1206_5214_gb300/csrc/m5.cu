@@ -85,7 +85,9 @@ static int launch_m5_t(mdwf_ctx* c, const M5Launch& m) {
     Field<P> in = make_field<P>(const_cast<void*>(m.in), g, m.nrhs);
     Field<P> xf = m.x ? make_field<P>(const_cast<void*>(m.x), g, m.nrhs) : out;
     const R* tab = reinterpret_cast<const R*>(m.mat);
-    const R* mass = P == MDWF_F64 ? reinterpret_cast<const R*>(c->mass64) : reinterpret_cast<const R*>(c->mass32);
+    const R* mass = m.mass ? reinterpret_cast<const R*>(m.mass)
+                           : P == MDWF_F64 ? reinterpret_cast<const R*>(c->mass64)
+                                           : reinterpret_cast<const R*>(c->mass32);
     SCoef<R> sc;
     sc.b5 = (R)c->b5;
     sc.c5 = (R)c->c5;

@@ -438,6 +438,7 @@ void note_apply(mdwf_ctx* c, int prec);
 void replay_graph_counts(mdwf_ctx* c, long long replays);
 
 // status helpers (api.cu)
+void set_error_message(const char* msg);
 int cuda_status(cudaError_t e);
 int check_launch();
 int ensure_workspace(Workspace& w, size_t bytes);
@@ -499,6 +500,7 @@ struct M5Launch {
     int sop;
     int swap;
     int nrhs;
+    const void* mass; // per-rhs masses in this precision; nullptr = the context's
 };
 int launch_m5(mdwf_ctx* c, int prec, const M5Launch& m);
 
