@@ -192,6 +192,24 @@ def run_reference(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------- multi-rank logic
+
+def rank_source_seed(rank: int) -> int:
+    """Every rank solves its own source (independent problems, no data exchange)."""
+    return SOURCE_SEED + 100 * rank
+
+
+def combine_ranks(ms: float, flops: float, dist=None, device: str = "cpu") -> tuple[float, float]:
+    """Whole-job timing: the slowest rank's time and the sum of all ranks' flops."""
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    f = torch.tensor([flops], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(f, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(f.item())
+
+
 # --------------------------------------------------------------- GPU arm
 
 def apply_only(args, h, b, dims, Ls, n5, flush) -> None:
@@ -243,7 +261,7 @@ def main() -> None:
     n5 = dims[0] * dims[1] * dims[2] * dims[3] // 2 * Ls
     inner = mdwf.MDWF_F32 if args.inner == "f32" else mdwf.MDWF_F16N
     U = sy.gauge_field(dims, EPS, GAUGE_SEED)
-    b = sy.gaussian_field(dims, Ls, SOURCE_SEED + 100 * rank)
+    b = sy.gaussian_field(dims, Ls, rank_source_seed(rank))
     h = mdwf.mdwf_create(dims, Ls, M5, B5, C5, MF)
     Ud = torch.from_numpy(U).cuda()
     mdwf.mdwf_load_gauge(h, Ud)
@@ -290,12 +308,7 @@ def main() -> None:
         return
     applies = sum(applies1) - sum(applies0)
     flops = applies * FLOPS_PER_SITE * n5
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    f = torch.tensor([flops], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(f, op=dist.ReduceOp.SUM)
-    ms_max, flops_all = float(t.item()), float(f.item())
+    ms_max, flops_all = combine_ranks(ms, flops, dist, device="cuda")
     value = flops_all / (ms_max * 1e-3) / 1e9
 
     if rank != 0:

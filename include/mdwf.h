@@ -80,6 +80,8 @@ typedef struct {
     int dense_s;          /* 1: apply the Ls x Ls factors (I^-1, K, M_phi) as dense matrices built on
                              the host; 0: by the closed-form elimination of Sec. 4 wherever
                              |M-/M+| <= 0.9 (dense otherwise) */
+    int autotune;         /* 1: the first solve of each (precision, nrhs) tunes the hop kernels'
+                             block shape (see mdwf_autotune) */
 } mdwf_opts;
 
 /*
@@ -236,6 +238,20 @@ int mdwf_profile_read(mdwf_ctx *ctx, mdwf_kernel_stat *out, int max, int *n_out,
  * count per right-hand side batch). Either pointer may be NULL.
  */
 int mdwf_counters(const mdwf_ctx *ctx, long long *launches, long long applies[3]);
+
+/*
+ * Tunes the block shape of the hopping kernels (4d sites per thread block,
+ * each site a whole s-column) for fields of precision prec and nrhs
+ * right-hand sides: every candidate is timed with CUDA events on an M and an
+ * M^dag application of the context's own scratch fields, and the fastest is
+ * kept for later launches of that (prec, nrhs). Allocates scratch fields and
+ * synchronises the stream. *sites_per_block receives the choice (may be NULL).
+ * mdwf_set_tuning / mdwf_get_tuning store and read a choice directly, so a
+ * caller can keep tuned values across runs (0 = the default shape).
+ */
+int mdwf_autotune(mdwf_ctx *ctx, int prec, int nrhs, int *sites_per_block);
+int mdwf_set_tuning(mdwf_ctx *ctx, int prec, int nrhs, int sites_per_block);
+int mdwf_get_tuning(const mdwf_ctx *ctx, int prec, int nrhs, int *sites_per_block);
 
 /* Human-readable name of a status code (static string). */
 const char *mdwf_strerror(int status);

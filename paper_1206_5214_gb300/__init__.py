@@ -19,7 +19,8 @@ __all__ = [
     "MDWF_F64", "MDWF_F32", "MDWF_F16N", "MdwfError", "lib_path", "load",
     "mdwf_create", "mdwf_destroy", "mdwf_set_stream", "mdwf_load_gauge", "mdwf_field_bytes",
     "mdwf_field_import", "mdwf_field_export", "mdwf_apply", "mdwf_apply_dag", "mdwf_cgne",
-    "mdwf_strerror", "mdwf_force", "mdwf_apply_noalloc", "mdwf_profile_enable", "mdwf_profile_read", "mdwf_counters", "SolveParams",
+    "mdwf_strerror", "mdwf_force", "mdwf_apply_noalloc", "mdwf_autotune", "mdwf_set_tuning",
+    "mdwf_get_tuning", "mdwf_profile_enable", "mdwf_profile_read", "mdwf_counters", "SolveParams",
     "SolveInfo", "KernelStat",
 ]
 
@@ -40,7 +41,8 @@ class MdwfError(RuntimeError):
 
 
 class _Opts(ctypes.Structure):
-    _fields_ = [("stream", ctypes.c_void_p), ("device", ctypes.c_int), ("dense_s", ctypes.c_int)]
+    _fields_ = [("stream", ctypes.c_void_p), ("device", ctypes.c_int), ("dense_s", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
 
 
 class SolveParams(ctypes.Structure):
@@ -93,6 +95,9 @@ def load(build_if_missing: bool = True):
         "mdwf_profile_enable": (ip, [vp, ip]),
         "mdwf_profile_read": (ip, [vp, ctypes.POINTER(KernelStat), ip, ctypes.POINTER(ctypes.c_int), ip]),
         "mdwf_counters": (ip, [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+        "mdwf_autotune": (ip, [vp, ip, ip, ctypes.POINTER(ctypes.c_int)]),
+        "mdwf_set_tuning": (ip, [vp, ip, ip, ip]),
+        "mdwf_get_tuning": (ip, [vp, ip, ip, ctypes.POINTER(ctypes.c_int)]),
         "mdwf_strerror": (ctypes.c_char_p, [ip]),
         "mdwf_last_error": (ctypes.c_char_p, []),
     }
@@ -134,13 +139,13 @@ def mdwf_strerror(status: int) -> str:
 
 
 def mdwf_create(dims, Ls: int, M5: float, b5: float, c5: float, mf: float, stream=None, device: int = -1,
-                dense_s: bool = False):
+                dense_s: bool = False, autotune: bool = False):
     """Create a context; returns an opaque handle (int). ``stream``: torch.cuda.Stream, raw handle or None.
     ``dense_s``: apply the Ls x Ls factors as dense matrices instead of the closed-form elimination."""
     lib = load()
     h = ctypes.c_void_p()
     d = (ctypes.c_int * 4)(*[int(x) for x in dims])
-    opts = _Opts(_stream_handle(stream), int(device), int(bool(dense_s)))
+    opts = _Opts(_stream_handle(stream), int(device), int(bool(dense_s)), int(bool(autotune)))
     _check(lib.mdwf_create(ctypes.byref(h), d, int(Ls), float(M5), float(b5), float(c5), float(mf),
                            ctypes.byref(opts)), "mdwf_create")
     return h.value
@@ -265,3 +270,20 @@ def mdwf_counters(ctx) -> tuple[int, list[int]]:
     applies = (ctypes.c_longlong * 3)()
     _check(load().mdwf_counters(ctx, ctypes.byref(launches), applies), "mdwf_counters")
     return int(launches.value), [int(a) for a in applies]
+
+
+def mdwf_autotune(ctx, prec: int, nrhs: int = 1) -> int:
+    """Tune the hop kernels' block shape for (prec, nrhs); returns the chosen 4d sites per block."""
+    sb = ctypes.c_int(0)
+    _check(load().mdwf_autotune(ctx, int(prec), int(nrhs), ctypes.byref(sb)), "mdwf_autotune")
+    return int(sb.value)
+
+
+def mdwf_set_tuning(ctx, prec: int, nrhs: int, sites_per_block: int) -> None:
+    _check(load().mdwf_set_tuning(ctx, int(prec), int(nrhs), int(sites_per_block)), "mdwf_set_tuning")
+
+
+def mdwf_get_tuning(ctx, prec: int, nrhs: int = 1) -> int:
+    sb = ctypes.c_int(0)
+    _check(load().mdwf_get_tuning(ctx, int(prec), int(nrhs), ctypes.byref(sb)), "mdwf_get_tuning")
+    return int(sb.value)

@@ -291,6 +291,57 @@ int apply_op(mdwf_ctx* c, void* out, const void* in, int prec, int nrhs, int dag
     return launch_hop(c, prec, h);
 }
 
+// Times M + M^dag for every candidate block shape on scratch fields and keeps
+// the fastest for (prec, nrhs). Candidates: whole s-columns per block with
+// 32, 64 or 128 threads at most (the hop kernels are built for 128).
+int tune_hop(mdwf_ctx* c, int prec, int nrhs, int* chosen) {
+    const size_t fb = field_bytes(prec, c->g, nrhs);
+    int st;
+    // its own scratch: the solver's and the entry points' fields stay untouched
+    if ((st = ensure_workspace(c->tune, 2 * ((fb + 255) / 256 * 256)))) return st;
+    void* a = c->tune.p;
+    void* b = (char*)c->tune.p + (fb + 255) / 256 * 256;
+    if ((st = cuda_status(cudaMemsetAsync(a, 0, fb, c->stream)))) return st;
+    cudaEvent_t e0, e1;
+    if ((st = cuda_status(cudaEventCreate(&e0)))) return st;
+    if ((st = cuda_status(cudaEventCreate(&e1)))) { cudaEventDestroy(e0); return st; }
+    const int Ls = c->g.Ls;
+    int cands[3], nc = 0;
+    for (int threads = 128; threads >= 32; threads /= 2) {
+        const int sb = threads / Ls;
+        if (sb >= 1 && (nc == 0 || cands[nc - 1] != sb)) cands[nc++] = sb;
+    }
+    if (nc == 0) cands[nc++] = 1;
+    const bool prof = c->prof_on;
+    c->prof_on = false;
+    float best = 1e30f;
+    int best_sb = cands[0];
+    for (int k = 0; k < nc && !st; ++k) {
+        c->sb_tune[prec][nrhs] = cands[k];
+        st = apply_op(c, b, a, prec, nrhs, 0);  // warm-up
+        if (!st) st = apply_op(c, a, b, prec, nrhs, 1);
+        if (!st) st = cuda_status(cudaEventRecord(e0, c->stream));
+        for (int rep = 0; rep < 3 && !st; ++rep) {
+            st = apply_op(c, b, a, prec, nrhs, 0);
+            if (!st) st = apply_op(c, a, b, prec, nrhs, 1);
+        }
+        if (!st) st = cuda_status(cudaEventRecord(e1, c->stream));
+        if (!st) st = cuda_status(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        if (!st) st = cuda_status(cudaEventElapsedTime(&ms, e0, e1));
+        if (!st && ms < best) {
+            best = ms;
+            best_sb = cands[k];
+        }
+    }
+    c->prof_on = prof;
+    c->sb_tune[prec][nrhs] = best_sb;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (chosen) *chosen = best_sb;
+    return st;
+}
+
 }  // namespace mdwf
 
 using namespace mdwf;
@@ -342,6 +393,7 @@ int mdwf_create(mdwf_ctx** out, const int dims[4], int Ls, double M5, double b5,
         const double Mp = b5 * (4.0 - M5) + 1.0, Mm = c5 * (4.0 - M5) - 1.0;
         c->dense_s = (opts && opts->dense_s) || Mp == 0.0 || fabs(Mm / Mp) > 0.9;
     }
+    c->autotune = opts && opts->autotune;
     // the default mass tables, so that an apply needs no host round trip
     if ((st = ensure_tables(c, 1, nullptr)) ||
         (st = cuda_status(cudaMalloc(&c->nbr, sizeof(int) * 16 * (size_t)c->g.Vh))) ||
@@ -363,6 +415,7 @@ int mdwf_destroy(mdwf_ctx* c) {
     cudaFree(c->tmp[0].p); cudaFree(c->tmp[1].p);
     cudaFree(c->solver.p);
     cudaFree(c->io.p);
+    cudaFree(c->tune.p);
     cudaFree(c->red_partials);
     cudaFree(c->nbr);
     for (auto& r : c->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -498,6 +551,31 @@ int mdwf_profile_read(mdwf_ctx* c, mdwf_kernel_stat* out, int max, int* n_out, i
     if (n_out) *n_out = n < max ? n : max;
     if (reset)
         for (int k = 0; k < KK_NUM; ++k) c->kstat[k] = KStat{};
+    return MDWF_OK;
+}
+
+int mdwf_autotune(mdwf_ctx* c, int prec, int nrhs, int* sites_per_block) {
+    if (!c || !valid_prec(prec) || nrhs < 1 || nrhs > 64) return MDWF_EINVAL;
+    if (!c->have_gauge) return MDWF_ENOGAUGE;
+    int st;
+    if ((st = cuda_status(cudaSetDevice(c->device)))) return st;
+    if ((st = ensure_tables(c, nrhs, nullptr))) return st;
+    int sb = 0;
+    if ((st = tune_hop(c, prec, nrhs, &sb))) return st;
+    if (sites_per_block) *sites_per_block = sb;
+    return MDWF_OK;
+}
+
+int mdwf_set_tuning(mdwf_ctx* c, int prec, int nrhs, int sites_per_block) {
+    if (!c || !valid_prec(prec) || nrhs < 1 || nrhs > 64 || sites_per_block < 0) return MDWF_EINVAL;
+    if (sites_per_block > 0 && sites_per_block * c->g.Ls > 128) return MDWF_EINVAL;
+    c->sb_tune[prec][nrhs] = sites_per_block;
+    return MDWF_OK;
+}
+
+int mdwf_get_tuning(const mdwf_ctx* c, int prec, int nrhs, int* sites_per_block) {
+    if (!c || !valid_prec(prec) || nrhs < 1 || nrhs > 64 || !sites_per_block) return MDWF_EINVAL;
+    *sites_per_block = hop_sites_per_block(c, prec, nrhs);
     return MDWF_OK;
 }
 

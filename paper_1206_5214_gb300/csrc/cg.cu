@@ -239,8 +239,7 @@ __global__ void __launch_bounds__(128) k_pupd_w(Field<PX> x, Field<PR> r, Field<
 #pragma unroll
         for (int k = 0; k < 24; ++k) pv[k] = 0;
     }
-#pragma unroll
-    for (int k = 0; k < 24; ++k) row[s * kRowStride + k] = pv[k];
+    row_store(row + s * kRowStride, pv);
     __syncthreads();
     if (!active) return;
     const RP m = mass[rhs];
@@ -758,7 +757,15 @@ int solve_normal(mdwf_ctx* c, int nrhs, void* xo, const void* src, const mdwf_so
     const size_t fpp = field_bytes(inner, g, nrhs);
     auto up = [](size_t v) { return (v + 255) / 256 * 256; };
     const int nb = 2 * 152;
-    const int hb = hop_blocks(c);
+    if (c->autotune && c->sb_tune[inner][nrhs] == 0) {
+        int sb;
+        if ((st = tune_hop(c, inner, nrhs, &sb))) return st;
+    }
+    if (c->autotune && inner != MDWF_F64 && c->sb_tune[MDWF_F64][nrhs] == 0) {
+        int sb;
+        if ((st = tune_hop(c, MDWF_F64, nrhs, &sb))) return st;
+    }
+    const int hb = hop_blocks(c, inner, nrhs);
     const size_t need = up(f64) * 3 + (inner == MDWF_F64 ? up(f64) * 4 : up(f32) * 2 + up(fpp) * 4) +
                         up(sizeof(double) * S_NUM * kMaxRhs) + up(sizeof(double) * nrhs * nb) +
                         up(sizeof(double) * nrhs * hb);

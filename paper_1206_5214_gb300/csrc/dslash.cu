@@ -227,8 +227,7 @@ __global__ void __launch_bounds__(128, PrecTraits<P>::min_blocks - (GATHER ? 1 :
     }
     const int sst = site_stride(Ls);
     R* mine = hs + (size_t)ly * sst + s * kRowStride;
-#pragma unroll
-    for (int k = 0; k < 24; ++k) mine[k] = acc[k];
+    row_store(mine, acc);
     __syncthreads();
     R res[24];
     if (dense) {
@@ -247,8 +246,7 @@ __global__ void __launch_bounds__(128, PrecTraits<P>::min_blocks - (GATHER ? 1 :
     } else {
         block_columns(hs, blockDim.y, Ls, hp.sop, hp.swap != 0, hp.sc, mass, tid, nthr);
         __syncthreads();
-#pragma unroll
-        for (int k = 0; k < 24; ++k) res[k] = mine[k];
+        row_load(mine, res);
     }
     if (FUSE == FUSE_NONE && !active) return;
     const R cf = hp.coef * hp.gscale;
@@ -273,14 +271,16 @@ __global__ void __launch_bounds__(128, PrecTraits<P>::min_blocks - (GATHER ? 1 :
         }
         // v = A^dag t through the same column machinery
         __syncthreads();
+        if (!active) {
 #pragma unroll
-        for (int k = 0; k < 24; ++k) mine[k] = active ? res[k] : R(0);
+            for (int k = 0; k < 24; ++k) res[k] = R(0);
+        }
+        row_store(mine, res);
         __syncthreads();
         block_columns(hs, blockDim.y, Ls, SOP_A, true, hp.sc, mass, tid, nthr);
         __syncthreads();
         if (active) {
-#pragma unroll
-            for (int k = 0; k < 24; ++k) res[k] = mine[k];
+            row_load(mine, res);
             fa.out2.store(rbase + site, s, res);
         }
     } else {  // FUSE_R
@@ -304,13 +304,17 @@ __global__ void __launch_bounds__(128, PrecTraits<P>::min_blocks - (GATHER ? 1 :
 
 // ---------------------------------------------------------------- launcher
 
-static int sites_per_block(int Ls) {
-    int sb = 128 / Ls;
+// 4d sites per block: the autotuned value for (precision, nrhs) if there is
+// one, else as many whole s-columns as fit 128 threads.
+int hop_sites_per_block(const mdwf_ctx* c, int prec, int nrhs) {
+    const int t = (nrhs >= 1 && nrhs <= 64) ? c->sb_tune[prec][nrhs] : 0;
+    if (t > 0) return t;
+    const int sb = 128 / c->g.Ls;
     return sb < 1 ? 1 : sb;
 }
 
-int hop_blocks(const mdwf_ctx* c) {
-    const int SB = sites_per_block(c->g.Ls);
+int hop_blocks(const mdwf_ctx* c, int prec, int nrhs) {
+    const int SB = hop_sites_per_block(c, prec, nrhs);
     return (int)((c->g.Vh + SB - 1) / SB);
 }
 
@@ -318,7 +322,7 @@ template <int P, bool G, bool D, bool X, int FU>
 static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<typename PrecTraits<P>::real>& hp) {
     typedef typename PrecTraits<P>::real R;
     const Geom& g = c->g;
-    const int SB = sites_per_block(g.Ls);
+    const int SB = hop_sites_per_block(c, P, h.nrhs);
     dim3 block(g.Ls, SB), grid((unsigned)((g.Vh + SB - 1) / SB * h.nrhs));
     size_t smem = 4 * sizeof(double) + (size_t)((hp.sop == SOP_DENSE ? 2 * g.Ls * g.Ls : 0) + SB * site_stride(g.Ls)) * sizeof(R);
     auto kern = hop_kernel<P, G, D, X, FU>;

@@ -38,8 +38,7 @@ __global__ void __launch_bounds__(256) m5_kernel(Field<P> out, Field<P> in, Fiel
     }
     const int sst = site_stride(Ls);
     R* mine = cs + (size_t)ly * sst + s * kRowStride;
-#pragma unroll
-    for (int k = 0; k < 24; ++k) mine[k] = v[k];
+    row_store(mine, v);
     __syncthreads();
     R res[24];
     if (dense) {
@@ -59,8 +58,7 @@ __global__ void __launch_bounds__(256) m5_kernel(Field<P> out, Field<P> in, Fiel
         block_columns(cs, blockDim.y, Ls, sop, swap != 0, sc, mass[rhs], tid, nthr);
         __syncthreads();
         if (!active) return;
-#pragma unroll
-        for (int k = 0; k < 24; ++k) res[k] = mine[k];
+        row_load(mine, res);
     }
 #pragma unroll
     for (int k = 0; k < 24; ++k) res[k] *= coef;

@@ -25,6 +25,15 @@
 
 #include "mdwf.h"
 
+// Blocks per SM the hop kernels are compiled for (register budget per thread:
+// 65536 / (128 * blocks)); overridable at build time.
+#ifndef MDWF_MINB_F64
+#define MDWF_MINB_F64 3
+#endif
+#ifndef MDWF_MINB_F32
+#define MDWF_MINB_F32 6
+#endif
+
 namespace mdwf {
 
 constexpr int kMaxLs = 32;
@@ -39,19 +48,19 @@ struct Geom {
 template <int P> struct PrecTraits;
 template <> struct PrecTraits<MDWF_F64> {
     typedef double real;
-    static constexpr int min_blocks = 3;  // 128-thread blocks per SM the hop kernel is compiled for
+    static constexpr int min_blocks = MDWF_MINB_F64;  // 128-thread blocks per SM the hop kernel is compiled for
     static constexpr int W = 2, NC = 12;
     static constexpr size_t site_bytes = 192;
 };
 template <> struct PrecTraits<MDWF_F32> {
     typedef float real;
-    static constexpr int min_blocks = 6;
+    static constexpr int min_blocks = MDWF_MINB_F32;
     static constexpr int W = 4, NC = 6;
     static constexpr size_t site_bytes = 96;
 };
 template <> struct PrecTraits<MDWF_F16N> {
     typedef float real;
-    static constexpr int min_blocks = 6;
+    static constexpr int min_blocks = MDWF_MINB_F32;
     static constexpr int W = 4, NC = 6;
     static constexpr size_t site_bytes = 52;
 };
@@ -254,59 +263,99 @@ template <typename R> struct SCoef {
     R b5, c5, Mp, Mm;
 };
 
-// In place on one complex column: element s at base[k(s) * stride] (re) and
-// base[k(s) * stride + 1] (im), k(s) = up ? s : Ls-1-s. m = this rhs's mass.
+// Complex element types for the column tasks (one 8- or 16-byte access each).
+template <typename R> struct CPair;
+template <> struct CPair<float> { typedef float2 T; };
+template <> struct CPair<double> { typedef double2 T; };
+
+// In place on one complex column: element s at base[k(s) * stride] (re, im as
+// one vector), k(s) = up ? s : Ls-1-s. m = this rhs's mass.
 template <typename R>
 __device__ __forceinline__ void column_op(R* base, int stride, int Ls, int op, bool up, const SCoef<R>& sc, R m) {
-    auto at = [&](int s) -> R* { return base + (up ? s : Ls - 1 - s) * stride; };
+    typedef typename CPair<R>::T C;
+    auto at = [&](int s) -> C* { return reinterpret_cast<C*>(base + (up ? s : Ls - 1 - s) * stride); };
     if (op == SOP_A || op == SOP_K) {
         const R r = sc.Mm / sc.Mp, kappa = m * r, inv = R(1) / sc.Mp;
-        R ar = at(Ls - 1)[0], ai = at(Ls - 1)[1], pw = kappa;
+        C last = *at(Ls - 1);
+        R ar = last.x, ai = last.y, pw = kappa;
         for (int s = 0; s < Ls - 1; ++s) {
-            const R* q = at(s);
-            ar += pw * q[0];
-            ai += pw * q[1];
+            const C q = *at(s);
+            ar += pw * q.x;
+            ai += pw * q.y;
             pw *= -r;
         }
         const R den = sc.Mp * (R(1) - pw);
         R pr = ar / den, pi = ai / den;  // Psi_{Ls-1}
         const R lr = pr, li = pi;
         if (op == SOP_A) {
-            R* q = at(Ls - 1);
-            q[0] = pr;
-            q[1] = pi;
+            C o; o.x = pr; o.y = pi;
+            *at(Ls - 1) = o;
             for (int s = Ls - 2; s >= 0; --s) {
-                R* t = at(s);
-                pr = t[0] * inv - r * pr;
-                pi = t[1] * inv - r * pi;
-                t[0] = pr;
-                t[1] = pi;
+                C* t = at(s);
+                const C b = *t;
+                pr = b.x * inv - r * pr;
+                pi = b.y * inv - r * pi;
+                o.x = pr; o.y = pi;
+                *t = o;
             }
         } else {
             for (int s = Ls - 2; s >= 0; --s) {
-                R* t = at(s);
-                const R nr = t[0] * inv - r * pr, ni = t[1] * inv - r * pi;  // Psi_s
-                t[0] = sc.b5 * nr + sc.c5 * pr;                             // (M_phi Psi)_s
-                t[1] = sc.b5 * ni + sc.c5 * pi;
+                C* t = at(s);
+                const C b = *t;
+                const R nr = b.x * inv - r * pr, ni = b.y * inv - r * pi;  // Psi_s
+                C o;
+                o.x = sc.b5 * nr + sc.c5 * pr;                             // (M_phi Psi)_s
+                o.y = sc.b5 * ni + sc.c5 * pi;
+                *t = o;
                 pr = nr;
                 pi = ni;
             }
-            R* q = at(Ls - 1);  // row Ls-1 wraps to Psi_0 (now in pr, pi) with -m
-            q[0] = sc.b5 * lr - m * sc.c5 * pr;
-            q[1] = sc.b5 * li - m * sc.c5 * pi;
+            C o;  // row Ls-1 wraps to Psi_0 (now in pr, pi) with -m
+            o.x = sc.b5 * lr - m * sc.c5 * pr;
+            o.y = sc.b5 * li - m * sc.c5 * pi;
+            *at(Ls - 1) = o;
         }
     } else if (op == SOP_MPHI || op == SOP_C) {
         const R w0 = op == SOP_MPHI ? sc.b5 : R(0), w1 = op == SOP_MPHI ? sc.c5 : R(1);
-        const R f0r = at(0)[0], f0i = at(0)[1];
+        const C f0 = *at(0);
+        C cur = f0;
         for (int s = 0; s < Ls - 1; ++s) {
-            R* t = at(s);
-            const R* u = at(s + 1);
-            t[0] = w0 * t[0] + w1 * u[0];
-            t[1] = w0 * t[1] + w1 * u[1];
+            const C nxt = *at(s + 1);
+            C o;
+            o.x = w0 * cur.x + w1 * nxt.x;
+            o.y = w0 * cur.y + w1 * nxt.y;
+            *at(s) = o;
+            cur = nxt;
         }
-        R* q = at(Ls - 1);
-        q[0] = w0 * q[0] - m * w1 * f0r;
-        q[1] = w0 * q[1] - m * w1 * f0i;
+        C o;
+        o.x = w0 * cur.x - m * w1 * f0.x;
+        o.y = w0 * cur.y - m * w1 * f0.y;
+        *at(Ls - 1) = o;
+    }
+}
+
+// 24 reals of one (site, s) row in shared memory, as 16-byte vector accesses.
+__device__ __forceinline__ void row_store(float* row, const float* v) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        reinterpret_cast<float4*>(row)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+}
+__device__ __forceinline__ void row_load(const float* row, float* v) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const float4 q = reinterpret_cast<const float4*>(row)[k];
+        v[4 * k] = q.x; v[4 * k + 1] = q.y; v[4 * k + 2] = q.z; v[4 * k + 3] = q.w;
+    }
+}
+__device__ __forceinline__ void row_store(double* row, const double* v) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) reinterpret_cast<double2*>(row)[k] = make_double2(v[2 * k], v[2 * k + 1]);
+}
+__device__ __forceinline__ void row_load(const double* row, double* v) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        const double2 q = reinterpret_cast<const double2*>(row)[k];
+        v[2 * k] = q.x; v[2 * k + 1] = q.y;
     }
 }
 
@@ -400,6 +449,7 @@ struct mdwf_ctx {
     // solver workspace (CG fields) and the fields of the entry points around it
     mdwf::Workspace solver;
     mdwf::Workspace io;
+    mdwf::Workspace tune;  // scratch fields of the autotuner
     // reduction scratch: per-rhs block partials and scalars
     double* red_partials = nullptr;
     size_t red_partials_len = 0;
@@ -412,6 +462,9 @@ struct mdwf_ctx {
     mdwf::KStat kstat[mdwf::KK_NUM];
     long long launches = 0;
     long long applies[3] = {0, 0, 0};
+    // autotuned 4d sites per hop block, [precision][nrhs] (0 = default)
+    int sb_tune[3][65] = {};
+    bool autotune = false;
     // content of the CUDA graph being captured (added once per replay)
     long long cap_launches = 0;
     long long cap_applies[3] = {0, 0, 0};
@@ -489,7 +542,8 @@ struct HopLaunch {
     const double* sc;     // CG scalars
 };
 int launch_hop(mdwf_ctx* c, int prec, const HopLaunch& h);
-int hop_blocks(const mdwf_ctx* c);
+int hop_sites_per_block(const mdwf_ctx* c, int prec, int nrhs);
+int hop_blocks(const mdwf_ctx* c, int prec, int nrhs);
 
 struct M5Launch {
     void* out;
@@ -506,6 +560,7 @@ int launch_m5(mdwf_ctx* c, int prec, const M5Launch& m);
 
 // operator chains (api.cu)
 int apply_op(mdwf_ctx* c, void* out, const void* in, int prec, int nrhs, int dagger);
+int tune_hop(mdwf_ctx* c, int prec, int nrhs, int* chosen);
 
 // solver (cg.cu)
 struct NormalResult {

@@ -191,3 +191,23 @@ def test_apply_parity_full_16x16x16x32_other_alpha(b5, c5):
     ref = oracle.m(odd, U, p)
     with Ctx(dims, Ls, 1.8, b5, c5, 0.01, U) as c:
         check(c.apply(odd, F32)[0], ref, F32)
+
+
+def test_autotune_keeps_results_and_cache(tmp_path):
+    """The autotuner's choice is one of the candidate shapes, the operator is
+    unchanged by it, and the JSON cache restores it without re-tuning."""
+    from paper_1206_5214_gb300 import tuning
+    dims, Ls = (8, 4, 4, 4), 16
+    U, odd, p = setup(dims, Ls, 1.5, 0.5, 0.02, 0.3, 7)
+    ref = oracle.m(odd, U, p)
+    with Ctx(dims, Ls, 1.8, 1.5, 0.5, 0.02, U) as c:
+        path = str(tmp_path / "tune.json")
+        sb = tuning.tuned(c.h, "test-gpu", dims, Ls, F32, 1, path)
+        assert sb in (128 // Ls, 64 // Ls, 32 // Ls)
+        assert mdwf.mdwf_get_tuning(c.h, F32, 1) == sb
+        check(c.apply(odd, F32)[0], ref, F32)
+        mdwf.mdwf_set_tuning(c.h, F32, 1, 0)
+        assert tuning.tuned(c.h, "test-gpu", dims, Ls, F32, 1, path) == sb   # from the cache
+        for shape in (1, 2, 4, 8):
+            mdwf.mdwf_set_tuning(c.h, F32, 1, shape)
+            check(c.apply(odd, F32)[0], ref, F32)
