@@ -67,7 +67,10 @@ __device__ __forceinline__ void project(const R* w, R* h) {
 }
 
 template <int MU, int S, typename R>
-__device__ __forceinline__ void reconstruct_add(R* acc, const R* g) {
+__device__ __forceinline__ void reconstruct_add(R* acc, const R* gin, R scale = R(1), bool scaled = false) {
+    R g[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) g[k] = scaled ? scale * gin[k] : gin[k];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const R g0r = g[2 * c], g0i = g[2 * c + 1], g1r = g[6 + 2 * c], g1i = g[7 + 2 * c];
@@ -113,10 +116,15 @@ __device__ __forceinline__ void su3_mul(const R* U, const R* h, R* g) {
         }
 }
 
-// w = psi(s), or M_phi psi at s up to the factor gscale, for the neighbour column sr
+// w = psi(s), or M_phi psi at s up to the factor gscale, for the neighbour column sr.
+// Returns a factor still to be applied to w (the FP16 norm of an ungathered
+// input, which is linear and is applied to the transported half spinor).
 template <int P, bool GATHER, typename R>
-__device__ __forceinline__ void load_input(const Field<P>& in, long long sr, int s, int Ls, const HopParams<R>& hp,
-                                           R mass, R* w) {
+__device__ __forceinline__ R load_input(const Field<P>& in, long long sr, int s, int Ls, const HopParams<R>& hp,
+                                        R mass, R* w) {
+    if constexpr (P == MDWF_F16N && !GATHER) {
+        return in.load_raw(sr, s, w);
+    }
     in.load(sr, s, w);
     if (GATHER) {
         if (hp.gown != R(1)) {
@@ -137,6 +145,7 @@ __device__ __forceinline__ void load_input(const Field<P>& in, long long sr, int
             for (int k = 0; k < 12; ++k) w[12 + k] += fp * t[k];
         }
     }
+    return R(1);
 }
 
 template <int P, int MU, bool GATHER, bool DAG, typename R>
@@ -144,21 +153,22 @@ __device__ __forceinline__ void hop_dir(R* acc, const Field<P>& in, const Gauge<
                                         long long jf, long long jb, long long site, int s, long long rbase, R mass) {
     const Geom& g = hp.g;
     constexpr int SF = DAG ? +1 : -1;  // forward projector 1 + SF g_mu
+    constexpr bool SCALED = P == MDWF_F16N && !GATHER;
     {
         R w[24], h[12], u[18], gg[12];
-        load_input<P, GATHER>(in, rbase + jf, s, g.Ls, hp, mass, w);
+        const R f = load_input<P, GATHER>(in, rbase + jf, s, g.Ls, hp, mass, w);
         project<MU, SF>(w, h);
         U.load(((long long)hp.out_parity * 4 + MU) * g.Vh + site, u);
         su3_mul<false>(u, h, gg);
-        reconstruct_add<MU, SF>(acc, gg);
+        reconstruct_add<MU, SF>(acc, gg, f, SCALED);
     }
     {
         R w[24], h[12], u[18], gg[12];
-        load_input<P, GATHER>(in, rbase + jb, s, g.Ls, hp, mass, w);
+        const R f = load_input<P, GATHER>(in, rbase + jb, s, g.Ls, hp, mass, w);
         project<MU, -SF>(w, h);
         U.load(((long long)(1 - hp.out_parity) * 4 + MU) * g.Vh + jb, u);
         su3_mul<true>(u, h, gg);
-        reconstruct_add<MU, -SF>(acc, gg);
+        reconstruct_add<MU, -SF>(acc, gg, f, SCALED);
     }
 }
 

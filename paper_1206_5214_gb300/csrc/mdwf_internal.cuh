@@ -31,7 +31,7 @@
 #define MDWF_MINB_F64 3
 #endif
 #ifndef MDWF_MINB_F32
-#define MDWF_MINB_F32 6
+#define MDWF_MINB_F32 8
 #endif
 
 namespace mdwf {
@@ -144,11 +144,25 @@ template <> struct Field<MDWF_F16N> {
         float2 fa = __half22float2(a), fb = __half22float2(b);
         o[0] = fa.x * nrm; o[1] = fa.y * nrm; o[2] = fb.x * nrm; o[3] = fb.y * nrm;
     }
+    __device__ __forceinline__ static void unpack_raw(uint2 d, float* o) {
+        __half2 a = *reinterpret_cast<__half2*>(&d.x);
+        __half2 b = *reinterpret_cast<__half2*>(&d.y);
+        float2 fa = __half22float2(a), fb = __half22float2(b);
+        o[0] = fa.x; o[1] = fa.y; o[2] = fb.x; o[3] = fb.y;
+    }
     __device__ __forceinline__ void load(long long sr, int s, float* o) const {
         const uint2* p = v + sr * 6 * Ls + s;
         float nrm = __ldg(norm + sr * Ls + s);
 #pragma unroll
         for (int k = 0; k < 6; ++k) unpack(__ldg(p + (long long)k * Ls), nrm, o + 4 * k);
+    }
+    // values without the norm; returns the norm (its factor is applied later)
+    __device__ __forceinline__ float load_raw(long long sr, int s, float* o) const {
+        const uint2* p = v + sr * 6 * Ls + s;
+        const float nrm = __ldg(norm + sr * Ls + s);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) unpack_raw(__ldg(p + (long long)k * Ls), o + 4 * k);
+        return nrm;
     }
     __device__ __forceinline__ void load_half(long long sr, int s, int half, float* o) const {
         const uint2* p = v + sr * 6 * Ls + (long long)(3 * half) * Ls + s;
@@ -361,25 +375,31 @@ __device__ __forceinline__ void row_load(const double* row, double* v) {
 
 // Shared-memory staging of a block's columns: spinor (site ly, slice s) at
 // hs + ly * site_stride + s * kRowStride. The row stride of 28 words keeps the
-// 16-byte row accesses of 8 consecutive threads on distinct banks, and a site
-// stride = 24 (mod 32) words keeps the 64-bit column accesses of a warp
-// (12 components of consecutive sites) conflict-free.
+// 16-byte row accesses of 8 consecutive threads on distinct banks. The column
+// tasks of a warp all belong to one chirality (6 complex components per
+// site, consecutive sites), so a site stride = 12 (mod 32) words puts the
+// 8-byte accesses of every half-warp on distinct banks.
 constexpr int kRowStride = 28;
 __host__ __device__ inline int site_stride(int Ls) {
     const int base = Ls * kRowStride;
-    return base + ((24 - base % 32) + 32) % 32;
+    return base + ((12 - base % 32) + 32) % 32;
 }
 
-// Applies the s-operator to the SB staged columns of a block (tasks = (site,
-// complex component); P+ components are j < 6). Dense tables are applied by
-// the caller instead.
+// Applies the s-operator to the SB staged columns of a block. Tasks are
+// (chirality, site, component): the P+ components (spins 0, 1) fill the first
+// half of the task slots and the P- components the second, each half rounded
+// up to whole warps so that a warp walks all its columns in one direction.
+// Dense tables are applied by the caller instead.
 template <typename R>
 __device__ __forceinline__ void block_columns(R* hs, int SB, int Ls, int op, bool swap, const SCoef<R>& sc,
                                               R m, int tid, int nthr) {
     const int ss = site_stride(Ls);
-    for (int t = tid; t < SB * 12; t += nthr) {
-        const int ly = t / 12, j = t - 12 * (t / 12);
-        const bool up = (j >= 6) != swap;  // P- uses N' unless the adjoint swaps
+    const int per = SB * 6, half = (per + 31) / 32 * 32;
+    for (int t = tid; t < 2 * half; t += nthr) {
+        const int chir = t >= half ? 1 : 0, r = t - chir * half;
+        if (r >= per) continue;
+        const int ly = r / 6, j = chir * 6 + (r - 6 * (r / 6));
+        const bool up = (chir == 1) != swap;  // P- uses N' unless the adjoint swaps
         column_op(hs + (size_t)ly * ss + 2 * j, kRowStride, Ls, op, up, sc, m);
     }
 }
