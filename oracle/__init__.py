@@ -44,30 +44,54 @@ def build(force: bool = False) -> str:
 
 class _Params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int * 4), ("Ls", ctypes.c_int), ("M5", ctypes.c_double),
-                ("b5", ctypes.c_double), ("c5", ctypes.c_double), ("mf", ctypes.c_double)]
+                ("b5", ctypes.c_double), ("c5", ctypes.c_double), ("mf", ctypes.c_double),
+                ("b5s", ctypes.POINTER(ctypes.c_double)), ("c5s", ctypes.POINTER(ctypes.c_double))]
 
 
 @dataclass(frozen=True)
 class Params:
-    """Physics parameters: dims = (X, Y, Z, T), Ls, wall height M5 (> 0), b5, c5, mf."""
+    """Physics parameters: dims = (X, Y, Z, T), Ls, wall height M5 (> 0), b5, c5, mf.
+
+    ``b5s`` / ``c5s`` (tuples of Ls values, or None) replace the constant b5 / c5
+    by per-slice coefficients b5(s), c5(s): row s of Eq. (MoebiusOp) then uses
+    D+ = b5(s) D_W + 1 and D- = c5(s) D_W - 1. The force supports constant
+    coefficients only.
+    """
     dims: tuple
     Ls: int
     M5: float
     b5: float
     c5: float
     mf: float
+    b5s: tuple | None = None
+    c5s: tuple | None = None
 
     def c(self) -> _Params:
         p = _Params()
         for k in range(4):
             p.L[k] = int(self.dims[k])
         p.Ls, p.M5, p.b5, p.c5, p.mf = int(self.Ls), float(self.M5), float(self.b5), float(self.c5), float(self.mf)
+        keep = []
+        for name in ("b5s", "c5s"):
+            vals = getattr(self, name)
+            if vals is not None:
+                if len(vals) != self.Ls or self.Ls > 64:
+                    raise ValueError(f"{name} needs Ls <= 64 values")
+                arr = (ctypes.c_double * self.Ls)(*[float(v) for v in vals])
+                keep.append(arr)
+                setattr(p, name, ctypes.cast(arr, ctypes.POINTER(ctypes.c_double)))
+        p._keep = keep   # the arrays live as long as the struct
         return p
 
     def with_(self, **kw) -> "Params":
-        d = dict(dims=self.dims, Ls=self.Ls, M5=self.M5, b5=self.b5, c5=self.c5, mf=self.mf)
+        d = dict(dims=self.dims, Ls=self.Ls, M5=self.M5, b5=self.b5, c5=self.c5, mf=self.mf,
+                 b5s=self.b5s, c5s=self.c5s)
         d.update(kw)
         return Params(**d)
+
+    @property
+    def s_dependent(self) -> bool:
+        return self.b5s is not None or self.c5s is not None
 
     @property
     def V(self) -> int:
@@ -226,7 +250,9 @@ def solve(b_full: np.ndarray, U: np.ndarray, p: Params, tol: float = 1e-10, maxi
 
 
 def dm_dparam(X: np.ndarray, U: np.ndarray, p: Params, which: str) -> np.ndarray:
-    """dM/db5 X (which='b5') or dM/dc5 X (which='c5')."""
+    """dM/db5 X (which='b5') or dM/dc5 X (which='c5'); constant b5, c5 only."""
+    if p.s_dependent:
+        raise ValueError("dM/db5, dM/dc5 are defined for constant b5, c5 only")
     X, U = _c(X), _c(U)
     out = np.empty_like(X)
     _load().or_dm_dparam(_ptr(out), _ptr(X), _ptr(U), ctypes.byref(p.c()), {"b5": 0, "c5": 1}[which])
@@ -239,6 +265,8 @@ def force(phi: np.ndarray, U: np.ndarray, p: Params, tol: float = 1e-12, maxiter
     dS/dU has the gauge field's shape; a variation dU changes S by
     Re sum(conj(dSdU) * dU). Returns (S, dSdU, dSdb5, dSdc5, status, iters).
     """
+    if p.s_dependent:
+        raise ValueError("the oracle force supports constant b5, c5 only")
     phi, U = _c(phi), _c(U)
     G = np.zeros_like(U)
     S, db5, dc5 = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)

@@ -53,7 +53,12 @@ typedef struct {
     double b5;
     double c5;
     double mf;    /* quark mass m of the walls */
+    const double *b5s;  /* b5(s), s = 0..Ls-1, or NULL for the constant b5 */
+    const double *c5s;  /* c5(s), or NULL for the constant c5 */
 } or_params;
+
+static double b5_of(const or_params *p, int s) { return p->b5s ? p->b5s[s] : p->b5; }
+static double c5_of(const or_params *p, int s) { return p->c5s ? p->c5s[s] : p->c5; }
 
 /* ------------------------------------------------------------------ gammas */
 
@@ -253,13 +258,15 @@ static void proj_field(cplx *out, cplx S[4][4], const cplx *in, long nsites)
 
 /*
  * out = D_DW(m) in (dagger: D_DW(m)^dag) on full 5d fields [s][site][12],
- * row by row from the tridiagonal matrix of Eq. (MoebiusOp) with constant
- * b5, c5:
- *   row s:  D+ psi_s + D- P- psi_{s+1} + D- P+ psi_{s-1},
- *   row 1:  the P+ term is -m D- P+ psi_Ls,   row Ls: the P- term is -m D- P- psi_1.
- * The adjoint takes (D^dag)_{s,s'} = (D_{s',s})^dag:
- *   row s:  D+^dag psi_s + P+ D-^dag psi_{s+1} + P- D-^dag psi_{s-1},
- *   row 1:  -m P- D-^dag psi_Ls,   row Ls: -m P+ D-^dag psi_1.
+ * row by row from the tridiagonal of Eq. (MoebiusOp) with the coefficients
+ * of row s, D+^(s) = b5(s) D_W + 1 and D-^(s) = c5(s) D_W - 1 (constant
+ * b5, c5 unless per-slice arrays are given):
+ *   row s:  D+^(s) psi_s + D-^(s) P- psi_{s+1} + D-^(s) P+ psi_{s-1},
+ *   row 1:  the P+ term is -m D-^(1) P+ psi_Ls,  row Ls: the P- term is -m D-^(Ls) P- psi_1.
+ * The adjoint takes (D^dag)_{s,s'} = (D_{s',s})^dag, so an off-diagonal term
+ * of row s carries the coefficient of the row it comes from:
+ *   row s:  D+^(s)dag psi_s + P+ D-^(s+1)dag psi_{s+1} + P- D-^(s-1)dag psi_{s-1},
+ *   row 1:  -m P- D-^(Ls)dag psi_Ls,   row Ls: -m P+ D-^(1)dag psi_1.
  */
 void or_ddw(cplx *out, const cplx *in, const cplx *U, const or_params *p, int dagger)
 {
@@ -269,22 +276,22 @@ void or_ddw(cplx *out, const cplx *in, const cplx *U, const or_params *p, int da
     cplx *t = malloc(sizeof(cplx) * n), *u = malloc(sizeof(cplx) * n);
     for (int s = 0; s < Ls; ++s) {
         cplx *o = out + s * n;
-        dw_affine(o, in + s * n, U, p->L, p->M5, dagger, p->b5, 1.0);   /* D+ psi_s */
+        dw_affine(o, in + s * n, U, p->L, p->M5, dagger, b5_of(p, s), 1.0);   /* D+ psi_s */
         int sp = (s + 1) % Ls, sm = (s - 1 + Ls) % Ls;
         double wp = (s == Ls - 1) ? -p->mf : 1.0;   /* coefficient of the s+1 block */
         double wm = (s == 0) ? -p->mf : 1.0;        /* coefficient of the s-1 block */
         if (!dagger) {
             proj_field(t, PM, in + sp * n, V);
-            dw_affine(u, t, U, p->L, p->M5, 0, p->c5, -1.0);
+            dw_affine(u, t, U, p->L, p->M5, 0, c5_of(p, s), -1.0);
             for (long k = 0; k < n; ++k) o[k] += wp * u[k];
             proj_field(t, PP, in + sm * n, V);
-            dw_affine(u, t, U, p->L, p->M5, 0, p->c5, -1.0);
+            dw_affine(u, t, U, p->L, p->M5, 0, c5_of(p, s), -1.0);
             for (long k = 0; k < n; ++k) o[k] += wm * u[k];
         } else {
-            dw_affine(t, in + sp * n, U, p->L, p->M5, 1, p->c5, -1.0);
+            dw_affine(t, in + sp * n, U, p->L, p->M5, 1, c5_of(p, sp), -1.0);
             proj_field(u, PP, t, V);
             for (long k = 0; k < n; ++k) o[k] += wp * u[k];
-            dw_affine(t, in + sm * n, U, p->L, p->M5, 1, p->c5, -1.0);
+            dw_affine(t, in + sm * n, U, p->L, p->M5, 1, c5_of(p, sm), -1.0);
             proj_field(u, PM, t, V);
             for (long k = 0; k < n; ++k) o[k] += wm * u[k];
         }
@@ -318,20 +325,21 @@ static void hop_half(cplx *out, const cplx *in, const cplx *U, const int L[4], i
 
 /*
  * One red/black block of the 5d operator, built from the tridiagonal of
- * Eq. (MoebiusOp) with every block entry replaced by one of its two parts:
- *   hop == 0 : the site-diagonal part (Eq. D_5d_matrix); D+ -> cd, D- -> co.
- *              With cd = M+, co = M- this is I_rr = I_bb.
- *   hop == 1 : the hopping part, D+ -> cd W, D- -> co W, W = -H/2 from
- *              parity 1 - po to parity po. With cd = b5, co = c5 this is
+ * Eq. (MoebiusOp) with every block entry replaced by one of its two parts
+ * (cd[s], co[s]: the coefficients of row s):
+ *   hop == 0 : the site-diagonal part (Eq. D_5d_matrix); D+^(s) -> cd[s], D-^(s) -> co[s].
+ *              With cd = M+(s), co = M-(s) this is I_rr = I_bb.
+ *   hop == 1 : the hopping part, D+^(s) -> cd[s] W, D-^(s) -> co[s] W, W = -H/2 from
+ *              parity 1 - po to parity po. With cd = b5(s), co = c5(s) this is
  *              D_rb (po even) or D_br (po odd).
- * Rows:    out_s = cd T psi_s + co T P- psi_{s+1} + co T P+ psi_{s-1}
- *          (row Ls: -m co T P- psi_1; row 1: -m co T P+ psi_Ls)
- * Adjoint: out_s = cd T^dag psi_s + co P+ T^dag psi_{s+1} + co P- T^dag psi_{s-1}
- *          (row Ls: -m co P+ T^dag psi_1; row 1: -m co P- T^dag psi_Ls)
+ * Rows:    out_s = cd[s] T psi_s + co[s] T P- psi_{s+1} + co[s] T P+ psi_{s-1}
+ *          (row Ls: -m co[Ls] T P- psi_1; row 1: -m co[1] T P+ psi_Ls)
+ * Adjoint: out_s = cd[s] T^dag psi_s + co[s+1] P+ T^dag psi_{s+1} + co[s-1] P- T^dag psi_{s-1}
+ *          (row Ls: -m co[1] P+ T^dag psi_1; row 1: -m co[Ls] P- T^dag psi_Ls)
  * Fields are half fields [s][half site][12].
  */
 static void rb_block(cplx *out, const cplx *in, const cplx *U, const or_params *p,
-                     int po, int hop, double cd, double co, int dagger)
+                     int po, int hop, const double *cd, const double *co, int dagger)
 {
     init_gammas();
     const int Ls = p->Ls;
@@ -340,10 +348,11 @@ static void rb_block(cplx *out, const cplx *in, const cplx *U, const or_params *
     for (int s = 0; s < Ls; ++s) {
         cplx *o = out + s * n;
         int sp = (s + 1) % Ls, sm = (s - 1 + Ls) % Ls;
-        double wp = co * ((s == Ls - 1) ? -p->mf : 1.0);
-        double wm = co * ((s == 0) ? -p->mf : 1.0);
+        /* the coefficient of row s (operator) or of the row the term comes from (adjoint) */
+        double wp = (dagger ? co[sp] : co[s]) * ((s == Ls - 1) ? -p->mf : 1.0);
+        double wm = (dagger ? co[sm] : co[s]) * ((s == 0) ? -p->mf : 1.0);
         if (hop) {
-            hop_half(o, in + s * n, U, p->L, po, dagger, cd, 0);
+            hop_half(o, in + s * n, U, p->L, po, dagger, cd[s], 0);
             if (!dagger) {
                 proj_field(t, PM, in + sp * n, Vh);
                 hop_half(o, t, U, p->L, po, 0, wp, 1);
@@ -358,9 +367,7 @@ static void rb_block(cplx *out, const cplx *in, const cplx *U, const or_params *
                 for (long k = 0; k < n; ++k) o[k] += u[k];
             }
         } else {
-            for (long k = 0; k < n; ++k) o[k] = cd * in[s * n + k];
-            /* the site-diagonal part commutes with nothing here; the projector
-               order of the adjoint is kept all the same */
+            for (long k = 0; k < n; ++k) o[k] = cd[s] * in[s * n + k];
             if (!dagger) {
                 proj_field(t, PM, in + sp * n, Vh);
                 for (long k = 0; k < n; ++k) o[k] += wp * t[k];
@@ -378,19 +385,54 @@ static void rb_block(cplx *out, const cplx *in, const cplx *U, const or_params *
     free(u);
 }
 
+/* per-row coefficient arrays (Ls <= 64) */
+typedef struct { double v[64]; } coefs;
+static coefs fill_const(int Ls, double x)
+{
+    coefs c = {{0}};
+    for (int s = 0; s < Ls; ++s) c.v[s] = x;
+    return c;
+}
+static coefs mplus_s(const or_params *p)
+{
+    coefs c = {{0}};
+    for (int s = 0; s < p->Ls; ++s) c.v[s] = b5_of(p, s) * (4.0 - p->M5) + 1.0;
+    return c;
+}
+static coefs mminus_s(const or_params *p)
+{
+    coefs c = {{0}};
+    for (int s = 0; s < p->Ls; ++s) c.v[s] = c5_of(p, s) * (4.0 - p->M5) - 1.0;
+    return c;
+}
+static coefs b5_s(const or_params *p)
+{
+    coefs c = {{0}};
+    for (int s = 0; s < p->Ls; ++s) c.v[s] = b5_of(p, s);
+    return c;
+}
+static coefs c5_s(const or_params *p)
+{
+    coefs c = {{0}};
+    for (int s = 0; s < p->Ls; ++s) c.v[s] = c5_of(p, s);
+    return c;
+}
+
 static double mplus(const or_params *p) { return p->b5 * (4.0 - p->M5) + 1.0; }
 static double mminus(const or_params *p) { return p->c5 * (4.0 - p->M5) - 1.0; }
 
 /* out = I_rr in (dagger: I_rr^dag); Eq. (D_5d_matrix). */
 void or_mee(cplx *out, const cplx *in, const or_params *p, int dagger)
 {
-    rb_block(out, in, NULL, p, 0, 0, mplus(p), mminus(p), dagger);
+    coefs cd = mplus_s(p), co = mminus_s(p);
+    rb_block(out, in, NULL, p, 0, 0, cd.v, co.v, dagger);
 }
 
 /* Hopping block from parity 1 - po to po (dagger: the block of D_DW^dag). */
 void or_dhop(cplx *out, const cplx *in, const cplx *U, const or_params *p, int po, int dagger)
 {
-    rb_block(out, in, U, p, po, 1, p->b5, p->c5, dagger);
+    coefs cd = b5_s(p), co = c5_s(p);
+    rb_block(out, in, U, p, po, 1, cd.v, co.v, dagger);
 }
 
 /*
@@ -424,6 +466,62 @@ static void solve_arr(cplx *psi, const cplx *b, long stride, int Ls, double Mp, 
 }
 
 /*
+ * With per-slice coefficients the two chiral blocks of I_rr (the rows of
+ * Eq. D_5d_matrix with M+-(s) = b5(s) (4 - M5) + 1, c5(s) (4 - M5) - 1) are
+ *   P- : A_{s,s} = M+(s), A_{s,s+1} = M-(s), A_{Ls,1} = -m M-(Ls)
+ *   P+ : B_{s,s} = M+(s), B_{s,s-1} = M-(s), B_{1,Ls} = -m M-(1)
+ * and no longer each other's transpose; the closed form of Sec. 4 needs
+ * constant coefficients, so these are inverted by plain Gauss-Jordan
+ * elimination with partial pivoting.
+ */
+static void chiral_block(double *a, const or_params *p, int minus, int transpose)
+{
+    const int Ls = p->Ls;
+    coefs mp = mplus_s(p), mm = mminus_s(p);
+    for (int i = 0; i < Ls * Ls; ++i) a[i] = 0.0;
+    for (int s = 0; s < Ls; ++s) {
+        a[s * Ls + s] += mp.v[s];
+        if (minus) a[s * Ls + (s + 1) % Ls] += (s == Ls - 1) ? -p->mf * mm.v[s] : mm.v[s];
+        else a[s * Ls + (s - 1 + Ls) % Ls] += (s == 0) ? -p->mf * mm.v[s] : mm.v[s];
+    }
+    if (transpose)
+        for (int i = 0; i < Ls; ++i)
+            for (int j = i + 1; j < Ls; ++j) {
+                double t = a[i * Ls + j];
+                a[i * Ls + j] = a[j * Ls + i];
+                a[j * Ls + i] = t;
+            }
+}
+
+static void invert_real(double *inv, const double *a, int n)
+{
+    const int w = 2 * n;
+    double *m = malloc(sizeof(double) * n * w);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < w; ++j) m[i * w + j] = j < n ? a[i * n + j] : (j - n == i ? 1.0 : 0.0);
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(m[r * w + c]) > fabs(m[piv * w + c])) piv = r;
+        for (int j = 0; j < w; ++j) {
+            double t = m[c * w + j];
+            m[c * w + j] = m[piv * w + j];
+            m[piv * w + j] = t;
+        }
+        double d = m[c * w + c];
+        for (int j = 0; j < w; ++j) m[c * w + j] /= d;
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            double f = m[r * w + c];
+            for (int j = 0; j < w; ++j) m[r * w + j] -= f * m[c * w + j];
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) inv[i * n + j] = m[i * w + n + j];
+    free(m);
+}
+
+/*
  * out = I_rr^-1 in = A^-1 P- in + A^{T,-1} P+ in   (Sec. 4)
  * dagger: out = I_rr^{-dag} in = A^{T,-1} P- in + A^-1 P+ in
  * (A_rr is real, so I_rr^dag = A^T P- + A P+). Half fields, nsites sites.
@@ -433,17 +531,38 @@ void or_mee_inv(cplx *out, const cplx *in, long nsites, const or_params *p, int 
     init_gammas();
     const int Ls = p->Ls;
     long n = 12 * nsites;
-    double Mp = mplus(p), Mm = mminus(p);
     cplx *bm = malloc(sizeof(cplx) * n * Ls), *bp = malloc(sizeof(cplx) * n * Ls);
     cplx *xm = malloc(sizeof(cplx) * n * Ls), *xp = malloc(sizeof(cplx) * n * Ls);
     for (int s = 0; s < Ls; ++s) {
         proj_field(bm + s * n, PM, in + s * n, nsites);
         proj_field(bp + s * n, PP, in + s * n, nsites);
     }
+    if (!p->b5s && !p->c5s) {
+        double Mp = mplus(p), Mm = mminus(p);
 #pragma omp parallel for schedule(static)
-    for (long k = 0; k < n; ++k) {
-        solve_arr(xm + k, bm + k, n, Ls, Mp, Mm, p->mf, dagger ? 1 : 0);
-        solve_arr(xp + k, bp + k, n, Ls, Mp, Mm, p->mf, dagger ? 0 : 1);
+        for (long k = 0; k < n; ++k) {
+            solve_arr(xm + k, bm + k, n, Ls, Mp, Mm, p->mf, dagger ? 1 : 0);
+            solve_arr(xp + k, bp + k, n, Ls, Mp, Mm, p->mf, dagger ? 0 : 1);
+        }
+    } else {
+        double *A = malloc(sizeof(double) * Ls * Ls), *B = malloc(sizeof(double) * Ls * Ls);
+        double *Ai = malloc(sizeof(double) * Ls * Ls), *Bi = malloc(sizeof(double) * Ls * Ls);
+        chiral_block(A, p, 1, dagger);   /* the P- block (its transpose for the adjoint) */
+        chiral_block(B, p, 0, dagger);   /* the P+ block */
+        invert_real(Ai, A, Ls);
+        invert_real(Bi, B, Ls);
+#pragma omp parallel for schedule(static)
+        for (long k = 0; k < n; ++k)
+            for (int s = 0; s < Ls; ++s) {
+                cplx am = 0, ap = 0;
+                for (int t = 0; t < Ls; ++t) {
+                    am += Ai[s * Ls + t] * bm[(long)t * n + k];
+                    ap += Bi[s * Ls + t] * bp[(long)t * n + k];
+                }
+                xm[(long)s * n + k] = am;
+                xp[(long)s * n + k] = ap;
+            }
+        free(A); free(B); free(Ai); free(Bi);
     }
     for (long k = 0; k < n * Ls; ++k) out[k] = xm[k] + xp[k];
     free(bm); free(bp); free(xm); free(xp);
@@ -706,21 +825,23 @@ void or_dm_dparam(cplx *out, const cplx *X, const cplx *U, const or_params *p, i
     /* term 1: dA D_br A D_rb X = -A dI A D_br e2 */
     or_dhop(t, e2, U, p, 1, 0);
     or_mee_inv(u, t, Vh, p, 0);
-    rb_block(t, u, NULL, p, 1, 0, dId, dIo, 0);
+    coefs cId = fill_const(p->Ls, dId), cIo = fill_const(p->Ls, dIo);
+    coefs cHd = fill_const(p->Ls, dHd), cHo = fill_const(p->Ls, dHo);
+    rb_block(t, u, NULL, p, 1, 0, cId.v, cIo.v, 0);
     or_mee_inv(u, t, Vh, p, 0);
     for (long k = 0; k < n; ++k) out[k] -= -u[k];
     /* term 2: A dD_br e2 */
-    rb_block(t, e2, U, p, 1, 1, dHd, dHo, 0);
+    rb_block(t, e2, U, p, 1, 1, cHd.v, cHo.v, 0);
     or_mee_inv(u, t, Vh, p, 0);
     for (long k = 0; k < n; ++k) out[k] -= u[k];
     /* term 3: A D_br dA e1 = -A D_br A dI A e1 */
-    rb_block(t, e2, NULL, p, 0, 0, dId, dIo, 0);
+    rb_block(t, e2, NULL, p, 0, 0, cId.v, cIo.v, 0);
     or_mee_inv(u, t, Vh, p, 0);
     or_dhop(t, u, U, p, 1, 0);
     or_mee_inv(u, t, Vh, p, 0);
     for (long k = 0; k < n; ++k) out[k] -= -u[k];
     /* term 4: A D_br A dD_rb X */
-    rb_block(t, X, U, p, 0, 1, dHd, dHo, 0);
+    rb_block(t, X, U, p, 0, 1, cHd.v, cHo.v, 0);
     or_mee_inv(u, t, Vh, p, 0);
     or_dhop(t, u, U, p, 1, 0);
     or_mee_inv(u, t, Vh, p, 0);
@@ -744,6 +865,7 @@ void or_dm_dparam(cplx *out, const cplx *X, const cplx *U, const or_params *p, i
 int or_force(cplx *dSdU, double *dSdb5, double *dSdc5, double *S, const cplx *phi,
              const cplx *U, const or_params *p, double tol, int maxiter, int *iters)
 {
+    if (p->b5s || p->c5s) return -1;   /* the derivatives below assume constant b5, c5 */
     long V = vol4(p->L), Vh = V / 2, n = 12 * Vh * p->Ls;
     cplx *X = calloc((size_t)n, sizeof(cplx)), *Y = malloc(sizeof(cplx) * n);
     cplx *a = malloc(sizeof(cplx) * n), *b = malloc(sizeof(cplx) * n);
@@ -759,9 +881,10 @@ int or_force(cplx *dSdU, double *dSdb5, double *dSdc5, double *S, const cplx *ph
     or_dhop(t, a, U, p, 0, 1);
     or_mee_inv(c, t, Vh, p, 1);             /* c = A^dag D_br^dag a (even) */
     memset(dSdU, 0, sizeof(cplx) * 9 * 4 * V);
-    rb_block(w, b, NULL, p, 0, 0, p->b5, p->c5, 0);   /* b~ (even) */
+    coefs cb5 = fill_const(p->Ls, p->b5), cc5 = fill_const(p->Ls, p->c5);
+    rb_block(w, b, NULL, p, 0, 0, cb5.v, cc5.v, 0);   /* b~ (even) */
     acc_link_derivative(dSdU, a, w, p, 1, 2.0);    /* 2 Re(a^dag dD_br b) */
-    rb_block(w, X, NULL, p, 1, 0, p->b5, p->c5, 0);   /* X~ (odd) */
+    rb_block(w, X, NULL, p, 1, 0, cb5.v, cc5.v, 0);   /* X~ (odd) */
     acc_link_derivative(dSdU, c, w, p, 0, 2.0);    /* 2 Re(c^dag dD_rb X) */
     or_dm_dparam(t, X, U, p, 0);
     *dSdb5 = -2.0 * creal(dotc(Y, t, n));
