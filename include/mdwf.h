@@ -11,8 +11,8 @@
  *           (Eq. D^Wilson with the Wilson mass -M5; M5 > 0 is the wall height).
  *   D_DW  = the tridiagonal of Eq. MoebiusOp with D+ = b5 D_W + 1,
  *           D- = c5 D_W - 1 and the mass-mf corners.
- *   red/black = checkerboard on x+y+z+t, the same for every s (Sec. 4).
- *   M     = 1 - I_bb^-1 D_br I_rr^-1 D_rb on the odd (black) sites (Sec. 4),
+ *   red/black = checkerboard on x+y+z+t, the same for every s (Sec. 3).
+ *   M     = 1 - I_bb^-1 D_br I_rr^-1 D_rb on the odd (black) sites (Sec. 3),
  *           the operator every mdwf_apply computes and mdwf_cgne inverts.
  *   Chiral gamma basis g_mu = [[0, A_mu], [A_mu^dag, 0]], A_k = -i sigma_k,
  *   A_4 = 1, g5 = diag(1, 1, -1, -1); P+ is spins 0, 1 and P- spins 2, 3.
@@ -78,7 +78,7 @@ typedef struct {
     void *stream;         /* cudaStream_t to enqueue on; NULL = the legacy default stream */
     int device;           /* CUDA device ordinal; -1 = the device current at mdwf_create */
     int dense_s;          /* 1: apply the Ls x Ls factors (I^-1, K, M_phi) as dense matrices built on
-                             the host; 0: by the closed-form elimination of Sec. 4 wherever
+                             the host; 0: by the closed-form elimination of Sec. 3 wherever
                              |M-/M+| <= 0.9 (dense otherwise) */
     int autotune;         /* 1: the first solve of each (precision, nrhs) tunes the hop kernels'
                              block shape (see mdwf_autotune) */
@@ -86,7 +86,7 @@ typedef struct {
 
 /*
  * Creates a context for one lattice and one set of Moebius parameters
- * (Eq. MoebiusOp with constant b5(s) = b5, c5(s) = c5, Sec. 3).
+ * (Eq. MoebiusOp with constant b5(s) = b5, c5(s) = c5, Sec. 2.1).
  * dims: {X, Y, Z, T}, each even and >= 2. Ls: even, 2 <= Ls <= 32.
  * M5: wall height (D_W diagonal 4 - M5). mf: wall mass m (Eq. DWaction).
  * opts may be NULL. On success *out owns device workspace until mdwf_destroy.
@@ -99,6 +99,26 @@ int mdwf_destroy(mdwf_ctx *ctx);
 
 /* Changes the stream later calls enqueue on. */
 int mdwf_set_stream(mdwf_ctx *ctx, void *stream);
+
+/*
+ * Per-slice Moebius coefficients (Sec. 2.1, Eq. DWaction with D+^(s) =
+ * b5(s) D_W + 1, D-^(s) = c5(s) D_W - 1; the Zolotarev form of Sec. 4.3 takes
+ * b5(s) - c5(s) fixed and b5(s) + c5(s) from the Zolotarev coefficients).
+ * b5s, c5s: Ls values each in host memory, index s = 0..Ls-1 for slices
+ * 1..Ls of the paper; copied, so the caller may free them on return. Both
+ * NULL: back to the constant b5, c5 of mdwf_create.
+ * While per-slice coefficients are set, every Ls x Ls factor is a dense
+ * matrix (the closed form of Sec. 3 needs constant coefficients), the CG
+ * iteration is the unfused one, and mdwf_force and mdwf_apply_noalloc
+ * return MDWF_EINVAL. Waits for the context's stream. Errors: MDWF_EINVAL for
+ * one array NULL and not the other, a non-finite value, or a singular
+ * I = diag(M+(s)) + diag(M-(s)) C (the previous coefficients stay in force).
+ */
+int mdwf_set_s_coefficients(mdwf_ctx *ctx, const double *b5s, const double *c5s);
+
+/* Writes the Ls coefficients in force to b5s, c5s (host, Ls values each) and
+ * sets *per_slice to 1 when they are per-slice, 0 when constant. */
+int mdwf_get_s_coefficients(const mdwf_ctx *ctx, double *b5s, double *c5s, int *per_slice);
 
 /*
  * Loads the SU(3) links U_mu(x) (Eq. D^Wilson) from complex128
@@ -125,7 +145,7 @@ int mdwf_field_import(mdwf_ctx *ctx, void *dst, const double *src, int prec, int
 int mdwf_field_export(mdwf_ctx *ctx, double *dst, const void *src, int prec, int nrhs, int where);
 
 /*
- * out = M in on the odd sites, M = 1 - I_bb^-1 D_br I_rr^-1 D_rb (Sec. 4),
+ * out = M in on the odd sites, M = 1 - I_bb^-1 D_br I_rr^-1 D_rb (Sec. 3),
  * for nrhs internal fields of precision prec (device buffers, in != out).
  * mf_per_rhs: NULL (every right-hand side uses the context's mf) or nrhs
  * masses (host memory), one per right-hand side.
@@ -180,7 +200,7 @@ typedef struct {
 /*
  * Solves D_DW(m) x = b for nrhs full 5d right-hand sides (user full format,
  * complex128, host or device as where says): b'_o = I_bb^-1 (b_o - D_br
- * I_rr^-1 b_e), CG on M^dag M x_o = M^dag b'_o (Sec. 3.2, Sec. 4), then
+ * I_rr^-1 b_e), CG on M^dag M x_o = M^dag b'_o (Sec. 3; the solver of Sec. 4), then
  * x_e = I_rr^-1 (b_e - D_rb x_o). x has b's format and location.
  * mf_per_rhs: NULL or nrhs masses (host). params may be NULL (defaults).
  * info: NULL or an array of nrhs entries. Synchronises the stream.
@@ -191,7 +211,7 @@ int mdwf_cgne(mdwf_ctx *ctx, double *x, const double *b, int nrhs, const double 
 
 /*
  * Derivatives of the action S = phi^dag (M^dag M)^-1 phi with M the operator
- * of mdwf_apply (the Schur complement of Sec. 4) at the context's mass:
+ * of mdwf_apply (the Schur complement of Sec. 3) at the context's mass:
  *   dSdU  : complex128 in the gauge layout U[t][z][y][x][mu][3][3]: for every
  *           link entry dS/dRe U + i dS/dIm U, so that a variation dU changes S
  *           by Re sum conj(dSdU) dU (the entries are treated as independent
@@ -252,6 +272,17 @@ int mdwf_counters(const mdwf_ctx *ctx, long long *launches, long long applies[3]
 int mdwf_autotune(mdwf_ctx *ctx, int prec, int nrhs, int *sites_per_block);
 int mdwf_set_tuning(mdwf_ctx *ctx, int prec, int nrhs, int sites_per_block);
 int mdwf_get_tuning(const mdwf_ctx *ctx, int prec, int nrhs, int *sites_per_block);
+
+/*
+ * Load strategy of the FP32 and FP16+norm hopping kernels (no counterpart in
+ * the paper; a GPU implementation choice): staged = 1 copies every neighbour
+ * spinor into shared memory with asynchronous copies one neighbour ahead of
+ * its use; 0 loads it into registers when needed. Results are identical up to
+ * nothing (the same arithmetic in the same order). prec MDWF_F64 accepts 0
+ * only. mdwf_get_staging reads the setting.
+ */
+int mdwf_set_staging(mdwf_ctx *ctx, int prec, int staged);
+int mdwf_get_staging(const mdwf_ctx *ctx, int prec, int *staged);
 
 /* Human-readable name of a status code (static string). */
 const char *mdwf_strerror(int status);

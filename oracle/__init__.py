@@ -5,7 +5,7 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
 library in ``paper_1206_5214_gb300`` never imports it, and the two share no
 code: this is a plain statement of what the paper defines (Eq. D^Wilson,
 Eq. MoebiusOp, the red/black Schur complement and the closed-form I_rr^-1 of
-Sec. 4), written in C (``mdwf_oracle.c``) and called through ctypes.
+Sec. 3), written in C (``mdwf_oracle.c``) and called through ctypes.
 
 Array conventions (numpy complex128, C order):
 
@@ -181,7 +181,7 @@ def mee(psi_h: np.ndarray, p: Params, dagger: bool = False) -> np.ndarray:
 
 
 def mee_inv(psi_h: np.ndarray, p: Params, dagger: bool = False) -> np.ndarray:
-    """I_rr^-1 (or I_rr^-dag) by the closed form of Sec. 4 on a half field."""
+    """I_rr^-1 (or I_rr^-dag) by the closed form of Sec. 3 on a half field."""
     psi_h = _c(psi_h)
     out = np.empty_like(psi_h)
     nsites = psi_h.size // (12 * p.Ls)

@@ -17,14 +17,14 @@
  *   - 5d operator, Eq. (MoebiusOp) / Eq. (DWmatrix): block tridiagonal in s with
  *     D+ = b5 D_W + 1 on the diagonal, D- P- above, D- P+ below and
  *     -m D- P+ (row 1, column Ls), -m D- P- (row Ls, column 1) in the corners.
- *   - red/black blocks, Sec. 4: colour x1+x2+x3+x4 even/odd for every s; the
+ *   - red/black blocks, Sec. 3: colour x1+x2+x3+x4 even/odd for every s; the
  *     site-diagonal blocks I_rr = I_bb carry M+ = b5(4 - M5) + 1 and
  *     M- = c5(4 - M5) - 1 (Eq. D_5d_matrix, both corners taken as -m M-, the
  *     reading that follows from Eq. MoebiusOp); the off-diagonal blocks keep
  *     the hopping part of every D_W in the tridiagonal.
  *   - I_rr^-1 by the closed-form forward elimination and back substitution of
- *     Sec. 4 on the P- half, the row/column-interchanged recursion on P+.
- *   - Schur complement D_pre = 1 - I_bb^-1 D_br I_rr^-1 D_rb (Sec. 4), solved
+ *     Sec. 3 on the P- half, the row/column-interchanged recursion on P+.
+ *   - Schur complement D_pre = 1 - I_bb^-1 D_br I_rr^-1 D_rb (Sec. 3), solved
  *     on the odd (black) sites by conjugate gradient on D_pre^dag D_pre.
  *
  * Conventions: lattice L = {X, Y, Z, T}, lexicographic site index
@@ -436,7 +436,7 @@ void or_dhop(cplx *out, const cplx *in, const cplx *U, const or_params *p, int p
 }
 
 /*
- * Closed-form solve of A_rr Psi = b along s (Sec. 4), per component; with
+ * Closed-form solve of A_rr Psi = b along s (Sec. 3), per component; with
  * r = M-/M+ ("alpha" in the paper) and kappa = m r ("M" in the paper), 0-based s:
  *   Psi_{Ls-1} = [b_{Ls-1} + kappa sum_{s=0}^{Ls-2} (-r)^s b_s] / (M+ (1 - kappa (-r)^{Ls-1}))
  *   Psi_s      = -r Psi_{s+1} + b_s / M+,  s = Ls-2 .. 0.
@@ -470,7 +470,7 @@ static void solve_arr(cplx *psi, const cplx *b, long stride, int Ls, double Mp, 
  * Eq. D_5d_matrix with M+-(s) = b5(s) (4 - M5) + 1, c5(s) (4 - M5) - 1) are
  *   P- : A_{s,s} = M+(s), A_{s,s+1} = M-(s), A_{Ls,1} = -m M-(Ls)
  *   P+ : B_{s,s} = M+(s), B_{s,s-1} = M-(s), B_{1,Ls} = -m M-(1)
- * and no longer each other's transpose; the closed form of Sec. 4 needs
+ * and no longer each other's transpose; the closed form of Sec. 3 needs
  * constant coefficients, so these are inverted by plain Gauss-Jordan
  * elimination with partial pivoting.
  */
@@ -522,7 +522,7 @@ static void invert_real(double *inv, const double *a, int n)
 }
 
 /*
- * out = I_rr^-1 in = A^-1 P- in + A^{T,-1} P+ in   (Sec. 4)
+ * out = I_rr^-1 in = A^-1 P- in + A^{T,-1} P+ in   (Sec. 3)
  * dagger: out = I_rr^{-dag} in = A^{T,-1} P- in + A^-1 P+ in
  * (A_rr is real, so I_rr^dag = A^T P- + A P+). Half fields, nsites sites.
  */
@@ -571,7 +571,7 @@ void or_mee_inv(cplx *out, const cplx *in, long nsites, const or_params *p, int 
 /* --------------------------------------------- preconditioned operator M */
 
 /*
- * out = D_pre in = in - I_bb^-1 D_br I_rr^-1 D_rb in on odd half fields (Sec. 4),
+ * out = D_pre in = in - I_bb^-1 D_br I_rr^-1 D_rb in on odd half fields (Sec. 3),
  * red = even, black = odd. dagger: the adjoint
  *   D_pre^dag = 1 - (D_rb)^dag I_rr^{-dag} (D_br)^dag I_bb^{-dag},
  * where (D_br)^dag is the even-row block of D_DW^dag and (D_rb)^dag its odd-row block.
@@ -624,7 +624,7 @@ void or_mdagm(cplx *out, const cplx *in, const cplx *U, const or_params *p)
 
 /*
  * Textbook conjugate gradient on M^dag M x = rhs (the paper names CG,
- * Sec. 3.2 and Sec. 5, without fixing its variant). When the iterated residual
+ * Sec. 2.3 and Sec. 4, without fixing its variant). When the iterated residual
  * reaches tol, the true residual |rhs - M^dag M x| / |rhs| is recomputed and
  * CG restarts from x if that is still above tol. x holds the starting guess.
  * Returns 0 on convergence, 1 if maxiter was reached, 2 on breakdown.
@@ -714,7 +714,7 @@ static void join_parity(cplx *full, const cplx *even, const cplx *odd, const or_
         }
 }
 
-/* b'_o = I_bb^-1 (b_o - D_br I_rr^-1 b_e)   (Schur decomposition, Sec. 4) */
+/* b'_o = I_bb^-1 (b_o - D_br I_rr^-1 b_e)   (Schur decomposition, Sec. 3) */
 void or_prepare(cplx *bprime, const cplx *b_full, const cplx *U, const or_params *p)
 {
     long Vh = vol4(p->L) / 2, n = 12 * Vh * p->Ls;

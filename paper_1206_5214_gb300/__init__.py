@@ -17,10 +17,11 @@ from . import build as _build
 
 __all__ = [
     "MDWF_F64", "MDWF_F32", "MDWF_F16N", "MdwfError", "lib_path", "load",
-    "mdwf_create", "mdwf_destroy", "mdwf_set_stream", "mdwf_load_gauge", "mdwf_field_bytes",
+    "mdwf_create", "mdwf_destroy", "mdwf_set_stream", "mdwf_set_s_coefficients", "mdwf_get_s_coefficients",
+    "mdwf_load_gauge", "mdwf_field_bytes",
     "mdwf_field_import", "mdwf_field_export", "mdwf_apply", "mdwf_apply_dag", "mdwf_cgne",
     "mdwf_strerror", "mdwf_force", "mdwf_apply_noalloc", "mdwf_autotune", "mdwf_set_tuning",
-    "mdwf_get_tuning", "mdwf_profile_enable", "mdwf_profile_read", "mdwf_counters", "SolveParams",
+    "mdwf_get_tuning", "mdwf_set_staging", "mdwf_get_staging", "mdwf_profile_enable", "mdwf_profile_read", "mdwf_counters", "SolveParams",
     "SolveInfo", "KernelStat",
 ]
 
@@ -83,6 +84,8 @@ def load(build_if_missing: bool = True):
                              ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_Opts)]),
         "mdwf_destroy": (ip, [vp]),
         "mdwf_set_stream": (ip, [vp, vp]),
+        "mdwf_set_s_coefficients": (ip, [vp, dp, dp]),
+        "mdwf_get_s_coefficients": (ip, [vp, dp, dp, ctypes.POINTER(ctypes.c_int)]),
         "mdwf_load_gauge": (ip, [vp, vp, ip]),
         "mdwf_field_bytes": (sz, [vp, ip, ip]),
         "mdwf_field_import": (ip, [vp, vp, vp, ip, ip, ip]),
@@ -98,6 +101,8 @@ def load(build_if_missing: bool = True):
         "mdwf_autotune": (ip, [vp, ip, ip, ctypes.POINTER(ctypes.c_int)]),
         "mdwf_set_tuning": (ip, [vp, ip, ip, ip]),
         "mdwf_get_tuning": (ip, [vp, ip, ip, ctypes.POINTER(ctypes.c_int)]),
+        "mdwf_set_staging": (ip, [vp, ip, ip]),
+        "mdwf_get_staging": (ip, [vp, ip, ctypes.POINTER(ctypes.c_int)]),
         "mdwf_strerror": (ctypes.c_char_p, [ip]),
         "mdwf_last_error": (ctypes.c_char_p, []),
     }
@@ -165,6 +170,28 @@ def mdwf_destroy(ctx) -> None:
 
 def mdwf_set_stream(ctx, stream) -> None:
     _check(load().mdwf_set_stream(ctx, _stream_handle(stream)), "mdwf_set_stream")
+
+
+def mdwf_set_s_coefficients(ctx, b5s, c5s) -> None:
+    """Per-slice b5(s), c5(s) (Ls values each, slice order s = 0..Ls-1), or both None
+    for the constant b5, c5 given at creation."""
+    if (b5s is None) != (c5s is None):
+        raise ValueError("give both b5s and c5s, or neither")
+    if b5s is None:
+        _check(load().mdwf_set_s_coefficients(ctx, None, None), "mdwf_set_s_coefficients")
+        return
+    b = (ctypes.c_double * len(b5s))(*[float(v) for v in b5s])
+    c = (ctypes.c_double * len(c5s))(*[float(v) for v in c5s])
+    _check(load().mdwf_set_s_coefficients(ctx, b, c), "mdwf_set_s_coefficients")
+
+
+def mdwf_get_s_coefficients(ctx, Ls: int):
+    """(b5s, c5s, per_slice): the Ls coefficients in force and whether they are per-slice."""
+    b = (ctypes.c_double * Ls)()
+    c = (ctypes.c_double * Ls)()
+    flag = ctypes.c_int(0)
+    _check(load().mdwf_get_s_coefficients(ctx, b, c, ctypes.byref(flag)), "mdwf_get_s_coefficients")
+    return list(b), list(c), bool(flag.value)
 
 
 def mdwf_load_gauge(ctx, U) -> None:
@@ -262,6 +289,17 @@ def mdwf_profile_read(ctx, reset: bool = False) -> list[dict]:
     _check(load().mdwf_profile_read(ctx, out, 64, ctypes.byref(n), int(bool(reset))), "mdwf_profile_read")
     return [{"name": out[i].name.decode(), "launches": out[i].launches, "ms": out[i].ms,
              "bytes": out[i].bytes, "flops": out[i].flops} for i in range(n.value)]
+
+
+def mdwf_set_staging(ctx, prec: int, staged: bool) -> None:
+    """Neighbour loads of the FP32 / FP16 hop kernels through shared memory (cp.async) or registers."""
+    _check(load().mdwf_set_staging(ctx, int(prec), int(bool(staged))), "mdwf_set_staging")
+
+
+def mdwf_get_staging(ctx, prec: int) -> bool:
+    v = ctypes.c_int(0)
+    _check(load().mdwf_get_staging(ctx, int(prec), ctypes.byref(v)), "mdwf_get_staging")
+    return bool(v.value)
 
 
 def mdwf_counters(ctx) -> tuple[int, list[int]]:

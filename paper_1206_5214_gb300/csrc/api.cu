@@ -1,7 +1,7 @@
 // C entry points of libmdwf: context, gauge upload, field conversion and the
 // red/black preconditioned Moebius operator M and M^dag.
 //
-// M = 1 - I_bb^-1 D_br I_rr^-1 D_rb (Sec. 4) is applied in the factored form
+// M = 1 - I_bb^-1 D_br I_rr^-1 D_rb (Sec. 3) is applied in the factored form
 //   D_rb = -1/2 H_eo M_phi,   I_rr = I_bb = M+ + M- C,   M_phi = b5 + c5 C,
 //   M = 1 - 1/4 A H_oe K H_eo M_phi,   A = I^-1,  K = M_phi A,
 // with C the fifth-dimension shift (P- psi_{s+1} + P+ psi_{s-1}, mass -m on
@@ -125,7 +125,9 @@ int ensure_workspace(Workspace& w, size_t bytes) {
 // ----------------------------------------------------- Ls x Ls tables (host)
 
 // Gauss-Jordan inverse with partial pivoting, n <= kMaxLs.
-static bool invert(int n, const double* a, double* inv) {
+// Gauss-Jordan inverse with partial pivoting; false when a pivot is at most
+// `tiny` in magnitude (singular to working precision at the entries' scale).
+static bool invert(int n, const double* a, double* inv, double tiny) {
     double m[kMaxLs][2 * kMaxLs];
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < 2 * n; ++j) m[i][j] = j < n ? a[i * n + j] : (j - n == i ? 1.0 : 0.0);
@@ -133,7 +135,7 @@ static bool invert(int n, const double* a, double* inv) {
         int piv = col;
         for (int r = col + 1; r < n; ++r)
             if (fabs(m[r][col]) > fabs(m[piv][col])) piv = r;
-        if (m[piv][col] == 0.0) return false;
+        if (!(fabs(m[piv][col]) > tiny)) return false;
         if (piv != col)
             for (int j = 0; j < 2 * n; ++j) { double t = m[col][j]; m[col][j] = m[piv][j]; m[piv][j] = t; }
         double d = 1.0 / m[col][col];
@@ -161,37 +163,50 @@ static void matmul(int n, const double* a, const double* b, double* c) {
 // out[t][chir][s'][s] = Mat_t,chir(s, s') for one mass, t = table_index(sop, swap);
 // chir 0 = P+, 1 = P-. The shift C is N' (psi_{s+1}, row Ls-1 takes -m psi_0)
 // on P- and N'^T on P+; the adjoint (swap) exchanges them.
-static bool build_tables(int Ls, double M5, double b5, double c5, double mf, double* out) {
+// Ls x Ls factors per chirality (Eq. D_5d_matrix, Sec. 3) with row
+// coefficients b5(s), c5(s): C = N' on P- (C_{s,s+1} = 1, C_{Ls,1} = -m) and
+// N'^T on P+; M_phi = diag(b5) + diag(c5) C, I = diag(M+) + diag(M-) C,
+// A = I^-1, K = M_phi A. swap = 1 stores the transposes of the same chirality,
+// which the adjoint chain applies (for constant coefficients these equal the
+// other chirality's matrices).
+static bool build_tables(int Ls, double M5, const double* b5s, const double* c5s, double mf, double* out) {
     const int n = Ls, nn = Ls * Ls;
-    const double Mp = b5 * (4.0 - M5) + 1.0, Mm = c5 * (4.0 - M5) - 1.0;
-    for (int chir = 0; chir < 2; ++chir)
-        for (int swap = 0; swap < 2; ++swap) {
-            const bool up = (chir == 1) != (swap == 1);
-            std::vector<double> C(nn, 0.0), Id(nn, 0.0), Mphi(nn), Mee(nn), A(nn), K(nn);
-            for (int s = 0; s < n; ++s) {
-                Id[s * n + s] = 1.0;
-                if (up) {
-                    if (s + 1 < n) C[s * n + s + 1] = 1.0;
-                    else C[s * n + 0] = -mf;
-                } else {
-                    if (s > 0) C[s * n + s - 1] = 1.0;
-                    else C[0 * n + n - 1] = -mf;
-                }
+    for (int chir = 0; chir < 2; ++chir) {
+        const bool up = chir == 1;  // P-: couples s to s+1
+        std::vector<double> C(nn, 0.0), Id(nn, 0.0), Mphi(nn), Mee(nn), A(nn), K(nn);
+        for (int s = 0; s < n; ++s) {
+            Id[s * n + s] = 1.0;
+            if (up) {
+                if (s + 1 < n) C[s * n + s + 1] = 1.0;
+                else C[s * n + 0] = -mf;
+            } else {
+                if (s > 0) C[s * n + s - 1] = 1.0;
+                else C[0 * n + n - 1] = -mf;
             }
-            for (int i = 0; i < nn; ++i) {
-                Mphi[i] = b5 * Id[i] + c5 * C[i];
+        }
+        for (int s = 0; s < n; ++s) {
+            const double Mp = b5s[s] * (4.0 - M5) + 1.0, Mm = c5s[s] * (4.0 - M5) - 1.0;
+            for (int sp = 0; sp < n; ++sp) {
+                const int i = s * n + sp;
+                Mphi[i] = b5s[s] * Id[i] + c5s[s] * C[i];
                 Mee[i] = Mp * Id[i] + Mm * C[i];
             }
-            if (!invert(n, Mee.data(), A.data())) return false;
-            matmul(n, Mphi.data(), A.data(), K.data());
-            const double* mats[5] = {Id.data(), A.data(), Mphi.data(), K.data(), C.data()};  // SOP_ID .. SOP_C
+        }
+        // the entries of I are differences of terms of size 1 + |4 - M5| max(|b5|, |c5|)
+        double scale = 1.0;
+        for (int s = 0; s < n; ++s) scale = fmax(scale, 1.0 + fabs(4.0 - M5) * fmax(fabs(b5s[s]), fabs(c5s[s])));
+        if (!invert(n, Mee.data(), A.data(), 1e-12 * scale)) return false;
+        matmul(n, Mphi.data(), A.data(), K.data());
+        const double* mats[5] = {Id.data(), A.data(), Mphi.data(), K.data(), C.data()};  // SOP_ID .. SOP_C
+        for (int swap = 0; swap < 2; ++swap)
             for (int op = SOP_ID; op <= SOP_C; ++op) {
                 double* dst = out + ((size_t)table_index(op, swap) * 2 + chir) * nn;
                 const double* M = mats[op - SOP_ID];
+                // (s, s') at [s'][s]; the transpose puts (s', s) there
                 for (int s = 0; s < n; ++s)
-                    for (int sp = 0; sp < n; ++sp) dst[sp * n + s] = M[s * n + sp];  // (s, s') at [s'][s]
+                    for (int sp = 0; sp < n; ++sp) dst[sp * n + s] = swap ? M[sp * n + s] : M[s * n + sp];
             }
-        }
+    }
     return true;
 }
 
@@ -224,9 +239,16 @@ int ensure_tables(mdwf_ctx* c, int nrhs, const double* mf_per_rhs) {
     float* h32 = reinterpret_cast<float*>(h64 + total);
     double* hm64 = reinterpret_cast<double*>(h32 + total + (total & 1));
     float* hm32 = reinterpret_cast<float*>(hm64 + 64);
-    std::vector<double> one(per_rhs);
+    std::vector<double> one(per_rhs), b5s(Ls), c5s(Ls);
+    for (int s = 0; s < Ls; ++s) {
+        b5s[s] = c->sdep ? c->b5s[s] : c->b5;
+        c5s[s] = c->sdep ? c->c5s[s] : c->c5;
+    }
     for (int r = 0; r < nrhs; ++r) {
-        if (!build_tables(Ls, c->M5, c->b5, c->c5, masses[r], one.data())) return MDWF_EINVAL;
+        if (!build_tables(Ls, c->M5, b5s.data(), c5s.data(), masses[r], one.data())) {
+            set_error_message("the Ls x Ls matrix I = M+ + M- C is singular for these coefficients");
+            return MDWF_EINVAL;
+        }
         for (int t = 0; t < kNumTables; ++t)
             memcpy(h64 + ((size_t)t * nrhs + r) * 2 * nn, one.data() + (size_t)t * 2 * nn, sizeof(double) * 2 * nn);
         hm64[r] = masses[r];
@@ -250,7 +272,7 @@ int ensure_tables(mdwf_ctx* c, int nrhs, const double* mf_per_rhs) {
 
 // ------------------------------------------------------------ operator chain
 
-int apply_op(mdwf_ctx* c, void* out, const void* in, int prec, int nrhs, int dagger) {
+int apply_op(mdwf_ctx* c, void* out, const void* in, int prec, int nrhs, int dagger, int rhs0) {
     const size_t fb = field_bytes(prec, c->g, nrhs);
     int st;
     note_apply(c, prec);
@@ -267,27 +289,34 @@ int apply_op(mdwf_ctx* c, void* out, const void* in, int prec, int nrhs, int dag
         h.out = c->tmp[0].p; h.in = in; h.x = nullptr; h.coef = 1.0; h.out_parity = 0;
         h.gather = 1; h.dagger = 0;
         set_sop(c, prec, SOP_K, 0, h);
+        offset_rhs(c, prec, rhs0, h);
         if ((st = launch_hop(c, prec, h))) return st;
         // out = psi_o - 1/4 A H_oe z_e
         h.out = out; h.in = c->tmp[0].p; h.x = in; h.coef = -0.25; h.out_parity = 1;
         h.gather = 0; h.dagger = 0;
+        h.mass = mass;
         set_sop(c, prec, SOP_A, 0, h);
+        offset_rhs(c, prec, rhs0, h);
         return launch_hop(c, prec, h);
     }
     // v_o = A^dag psi_o
     M5Launch m{};
     m.out = c->tmp[1].p; m.in = in; m.x = nullptr; m.coef = 1.0; m.nrhs = nrhs;
     set_sop(c, prec, SOP_A, 1, m);
+    offset_rhs(c, prec, rhs0, m);
     if ((st = launch_m5(c, prec, m))) return st;
     // z_e = K^dag H'_eo v_o
     h.out = c->tmp[0].p; h.in = c->tmp[1].p; h.x = nullptr; h.coef = 1.0; h.out_parity = 0;
     h.gather = 0; h.dagger = 1;
     set_sop(c, prec, SOP_K, 1, h);
+    offset_rhs(c, prec, rhs0, h);
     if ((st = launch_hop(c, prec, h))) return st;
     // out = psi_o - 1/4 M_phi^dag H'_oe z_e
     h.out = out; h.in = c->tmp[0].p; h.x = in; h.coef = -0.25; h.out_parity = 1;
     h.gather = 0; h.dagger = 1;
+    h.mass = mass;
     set_sop(c, prec, SOP_MPHI, 1, h);
+    offset_rhs(c, prec, rhs0, h);
     return launch_hop(c, prec, h);
 }
 
@@ -392,6 +421,7 @@ int mdwf_create(mdwf_ctx** out, const int dims[4], int Ls, double M5, double b5,
     {
         const double Mp = b5 * (4.0 - M5) + 1.0, Mm = c5 * (4.0 - M5) - 1.0;
         c->dense_s = (opts && opts->dense_s) || Mp == 0.0 || fabs(Mm / Mp) > 0.9;
+        c->dense_s_base = c->dense_s;
     }
     c->autotune = opts && opts->autotune;
     // the default mass tables, so that an apply needs no host round trip
@@ -418,10 +448,71 @@ int mdwf_destroy(mdwf_ctx* c) {
     cudaFree(c->tune.p);
     cudaFree(c->red_partials);
     cudaFree(c->nbr);
+    cudaFree(c->gs64); cudaFree(c->gs32);
     for (auto& r : c->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     delete c;
     return check_launch();
+}
+
+int mdwf_set_s_coefficients(mdwf_ctx* c, const double* b5s, const double* c5s) {
+    if (!c || (!b5s) != (!c5s)) return MDWF_EINVAL;
+    const int Ls = c->g.Ls;
+    int st;
+    if ((st = cuda_status(cudaSetDevice(c->device)))) return st;
+    // kernels in flight may still read the tables or the gather factors
+    if ((st = cuda_status(cudaStreamSynchronize(c->stream)))) return st;
+    if (!b5s) {
+        c->sdep = false;
+        c->dense_s = c->dense_s_base;
+        c->tab_valid = false;
+        return ensure_tables(c, 1, nullptr);
+    }
+    for (int s = 0; s < Ls; ++s)
+        if (!isfinite(b5s[s]) || !isfinite(c5s[s])) return MDWF_EINVAL;
+    if (!c->gs64 && (st = cuda_status(cudaMalloc(&c->gs64, 3 * 64 * sizeof(double))))) return st;
+    if (!c->gs32 && (st = cuda_status(cudaMalloc(&c->gs32, 3 * 64 * sizeof(float))))) return st;
+    // gather factors of row s: M_phi psi at s = gscale (gown psi_s + gfac C psi)
+    double h64[3 * 64] = {0};
+    float h32[3 * 64] = {0};
+    for (int s = 0; s < Ls; ++s) {
+        const bool fold = b5s[s] != 0.0;
+        h64[s] = fold ? 1.0 : 0.0;
+        h64[64 + s] = fold ? c5s[s] / b5s[s] : c5s[s];
+        h64[128 + s] = fold ? b5s[s] : 1.0;
+    }
+    for (int k = 0; k < 3 * 64; ++k) h32[k] = (float)h64[k];
+    const bool was_sdep = c->sdep, was_dense = c->dense_s;
+    double ob[64], oc[64];
+    memcpy(ob, c->b5s, sizeof(ob));
+    memcpy(oc, c->c5s, sizeof(oc));
+    for (int s = 0; s < Ls; ++s) { c->b5s[s] = b5s[s]; c->c5s[s] = c5s[s]; }
+    c->sdep = true;
+    c->dense_s = true;
+    c->tab_valid = false;
+    st = ensure_tables(c, 1, nullptr);
+    if (st) {  // singular I: keep the previous coefficients
+        memcpy(c->b5s, ob, sizeof(ob));
+        memcpy(c->c5s, oc, sizeof(oc));
+        c->sdep = was_sdep;
+        c->dense_s = was_dense;
+        c->tab_valid = false;
+        const int s2 = ensure_tables(c, 1, nullptr);
+        return s2 ? s2 : st;
+    }
+    // synchronous copies from pageable host memory: the factors are in place on return
+    if ((st = cuda_status(cudaMemcpy(c->gs64, h64, sizeof(h64), cudaMemcpyHostToDevice)))) return st;
+    return cuda_status(cudaMemcpy(c->gs32, h32, sizeof(h32), cudaMemcpyHostToDevice));
+}
+
+int mdwf_get_s_coefficients(const mdwf_ctx* c, double* b5s, double* c5s, int* per_slice) {
+    if (!c || !b5s || !c5s || !per_slice) return MDWF_EINVAL;
+    for (int s = 0; s < c->g.Ls; ++s) {
+        b5s[s] = c->sdep ? c->b5s[s] : c->b5;
+        c5s[s] = c->sdep ? c->c5s[s] : c->c5;
+    }
+    *per_slice = c->sdep ? 1 : 0;
+    return MDWF_OK;
 }
 
 int mdwf_set_stream(mdwf_ctx* c, void* stream) {
@@ -576,6 +667,19 @@ int mdwf_set_tuning(mdwf_ctx* c, int prec, int nrhs, int sites_per_block) {
 int mdwf_get_tuning(const mdwf_ctx* c, int prec, int nrhs, int* sites_per_block) {
     if (!c || !valid_prec(prec) || nrhs < 1 || nrhs > 64 || !sites_per_block) return MDWF_EINVAL;
     *sites_per_block = hop_sites_per_block(c, prec, nrhs);
+    return MDWF_OK;
+}
+
+int mdwf_set_staging(mdwf_ctx* c, int prec, int staged) {
+    if (!c || !valid_prec(prec) || (staged != 0 && staged != 1)) return MDWF_EINVAL;
+    if (prec == MDWF_F64 && staged) return MDWF_EINVAL;
+    c->hop_stage[prec] = staged;
+    return MDWF_OK;
+}
+
+int mdwf_get_staging(const mdwf_ctx* c, int prec, int* staged) {
+    if (!c || !valid_prec(prec) || !staged) return MDWF_EINVAL;
+    *staged = c->hop_stage[prec];
     return MDWF_OK;
 }
 

@@ -1,10 +1,10 @@
 // CGNE on M^dag M for the red/black Moebius operator, plain FP64 or mixed
 // precision with FP64 reliable updates, for a batch of right-hand sides.
 //
-// The paper solves with conjugate gradient (Sec. 3.2, Sec. 5) and measures
+// The paper solves with conjugate gradient (Sec. 2.3, Sec. 4) and measures
 // cost in Dirac applications; the variant here is CG on the normal
 // equations M^dag M x = M^dag b', with b' the red/black-preconditioned source
-// of the Schur decomposition (Sec. 4). All CG scalars live on the device
+// of the Schur decomposition (Sec. 3). All CG scalars live on the device
 // (alpha, beta, |r|^2 per right-hand side); the host only polls them every
 // few iterations. Dot products and norms accumulate in FP64 through a
 // two-pass reduction: per-block partials, then one block per right-hand side
@@ -423,8 +423,8 @@ static int cg_iteration(Solver& S, void* x, void* r, void* p, void* t, void* ap)
 }
 
 struct Fields {
-    // FP64: solution, right-hand side of the normal equations, residual, operator temporaries
-    void *xo, *src, *r, *t64, *ap64;
+    // FP64: solution, right-hand side of the normal equations, residual, operator temporary
+    void *xo, *src, *r, *t64;
     // inner iteration (w = M_phi p for the fused iteration)
     void *xs, *rs, *p, *t, *ap, *w;
 };
@@ -498,18 +498,20 @@ static int iterate(Solver& S, Fields& F, void* x, void* r) {
     return cg_iteration<PR, PP>(S, x, r, F.p, F.t, F.ap);
 }
 
-// r = src - M^dag M x in FP64 (active rhs), r_s = r in precision PS; |r|^2 -> S_AUX
+// r = src - M^dag M x in FP64 (active rhs), r_s = r in precision PS; |r|^2 -> S_AUX.
+// M^dag M x is formed in r itself (each element is read before it is
+// overwritten by the same thread), so no further FP64 field is needed; r of
+// an inactive right-hand side is left holding M^dag M x and is not used again.
 template <int PS, bool COPY>
-static int true_residual(Solver& S, void* r, void* rs, const void* src, const void* x, void* t64, void* ap64,
-                         bool masked) {
+static int true_residual(Solver& S, void* r, void* rs, const void* src, const void* x, void* t64, bool masked) {
     int st;
     if ((st = apply_op(S.c, t64, x, MDWF_F64, S.nrhs, 0))) return st;
-    if ((st = apply_op(S.c, ap64, t64, MDWF_F64, S.nrhs, 1))) return st;
+    if ((st = apply_op(S.c, r, t64, MDWF_F64, S.nrhs, 1))) return st;
     {
     LaunchScope scope(S.c, KB_BLAS * 3 + MDWF_F64, S.n5() * (3.0 * 192.0 + (COPY ? site_bytes(PS) : 0.0)), S.n5() * 48.0);
     k_residual<PS, COPY><<<S.grid(), kRedThreads, 0, S.c->stream>>>(
         make_field<MDWF_F64>(r, S.g, S.nrhs), make_field<PS>(rs ? rs : r, S.g, S.nrhs),
-        make_field<MDWF_F64>(const_cast<void*>(src), S.g, S.nrhs), make_field<MDWF_F64>(ap64, S.g, S.nrhs), S.part,
+        make_field<MDWF_F64>(const_cast<void*>(src), S.g, S.nrhs), make_field<MDWF_F64>(r, S.g, S.nrhs), S.part,
         masked ? S.sc : nullptr, S.g);
     }
     if ((st = check_launch())) return st;
@@ -541,7 +543,7 @@ static int run_mixed(Solver& S, Fields& F, const mdwf_solve_params& prm, double 
     }
     // FP32 carries ~7 digits, so it can reduce the residual 100x between FP64
     // updates; FP16 storage only ~3, so it updates after every 10x
-    const double delta = prm.delta > 0 ? prm.delta : (PP == MDWF_F32 ? 0.01 : 0.1);
+    const double delta = prm.delta > 0 ? prm.delta : (PP == MDWF_F32 ? 0.005 : 0.1);
     const int every = prm.check_every > 0 ? prm.check_every : 8;
     int it = 0;
     bool graph_ready = false;
@@ -591,7 +593,7 @@ static int run_mixed(Solver& S, Fields& F, const mdwf_solve_params& prm, double 
                 make_field<MDWF_F64>(F.xo, S.g, nrhs), make_field<MDWF_F32>(F.xs, S.g, nrhs), S.sc, S.g);
         }
         if ((st = check_launch())) return st;
-        if ((st = true_residual<MDWF_F32, true>(S, F.r, F.rs, F.src, F.xo, F.t64, F.ap64, true))) return st;
+        if ((st = true_residual<MDWF_F32, true>(S, F.r, F.rs, F.src, F.xo, F.t64, true))) return st;
         if ((st = S.pull())) return st;
         for (int r = 0; r < nrhs; ++r) {
             if (S.hsc[S_ACTIVE * kMaxRhs + r] == 0.0) continue;
@@ -618,7 +620,7 @@ static int run_plain(Solver& S, Fields& F, const mdwf_solve_params& prm, double 
     bool graph_ready = false;
     for (;;) {
         // (re)start from the true residual of the current x
-        if ((st = true_residual<MDWF_F64, false>(S, F.r, nullptr, F.src, F.xo, F.t64, F.ap64, true))) return st;
+        if ((st = true_residual<MDWF_F64, false>(S, F.r, nullptr, F.src, F.xo, F.t64, true))) return st;
         if ((st = S.pull())) return st;
         bool any = false;
         for (int r = 0; r < nrhs; ++r) {
@@ -731,6 +733,21 @@ int field_dot64(mdwf_ctx* c, const void* a, const void* b, int nrhs, double* out
     return cuda_status(cudaStreamSynchronize(c->stream));
 }
 
+static size_t up256(size_t v) { return (v + 255) / 256 * 256; }
+
+// Bytes of the solver workspace of solve_normal: FP64 r and t64, the inner
+// fields (x_s and r_s in FP32 for a mixed solve; p, t and w, or p, t and ap for
+// the unfused iteration), CG scalars and reduction partials.
+static size_t solver_bytes(const mdwf_ctx* c, int nrhs, int inner, int nb, int hb) {
+    const size_t f64 = field_bytes(MDWF_F64, c->g, nrhs), f32 = field_bytes(MDWF_F32, c->g, nrhs);
+    const size_t fpp = field_bytes(inner, c->g, nrhs);
+    const int inner_fields = c->dense_s ? 4 : 3;
+    return up256(f64) * 2 +
+           (inner == MDWF_F64 ? up256(f64) * inner_fields : up256(f32) * 2 + up256(fpp) * inner_fields) +
+           up256(sizeof(double) * S_NUM * kMaxRhs) + up256(sizeof(double) * nrhs * nb) +
+           up256(sizeof(double) * nrhs * hb);
+}
+
 // Solves M^dag M x = src for nrhs FP64 internal odd fields (x starts at zero).
 // Plain FP64 CG or mixed precision with FP64 reliable updates (prm.inner_prec).
 int solve_normal(mdwf_ctx* c, int nrhs, void* xo, const void* src, const mdwf_solve_params& prm,
@@ -766,9 +783,8 @@ int solve_normal(mdwf_ctx* c, int nrhs, void* xo, const void* src, const mdwf_so
         if ((st = tune_hop(c, MDWF_F64, nrhs, &sb))) return st;
     }
     const int hb = hop_blocks(c, inner, nrhs);
-    const size_t need = up(f64) * 3 + (inner == MDWF_F64 ? up(f64) * 4 : up(f32) * 2 + up(fpp) * 4) +
-                        up(sizeof(double) * S_NUM * kMaxRhs) + up(sizeof(double) * nrhs * nb) +
-                        up(sizeof(double) * nrhs * hb);
+    // the fused iteration (structured s-operators) needs no separate M^dag M p field
+    const size_t need = solver_bytes(c, nrhs, inner, nb, hb);
     Fields F{};
     Solver S{};
     cudaGraphExec_t gexec = nullptr;
@@ -782,12 +798,12 @@ int solve_normal(mdwf_ctx* c, int nrhs, void* xo, const void* src, const mdwf_so
         auto take = [&](size_t bytes) { void* p = w; w += up(bytes); return p; };
         F.xo = xo;
         F.src = const_cast<void*>(src);
-        F.r = take(f64); F.t64 = take(f64); F.ap64 = take(f64);
-        if (inner == MDWF_F64) {
-            F.p = take(f64); F.t = take(f64); F.ap = take(f64); F.w = take(f64);
-        } else {
-            F.xs = take(f32); F.rs = take(f32); F.p = take(fpp); F.t = take(fpp); F.ap = take(fpp); F.w = take(fpp);
-        }
+        F.r = take(f64); F.t64 = take(f64);
+        const size_t fi = inner == MDWF_F64 ? f64 : fpp;
+        if (inner != MDWF_F64) { F.xs = take(f32); F.rs = take(f32); }
+        F.p = take(fi); F.t = take(fi);
+        // unfused iteration: ap = M^dag M p; fused: w = M_phi p
+        if (c->dense_s) F.ap = take(fi); else F.w = take(fi);
         S.c = c; S.g = g; S.nrhs = nrhs; S.nb = nb;
         S.sc = (double*)take(sizeof(double) * S_NUM * kMaxRhs);
         S.part = (double*)take(sizeof(double) * nrhs * nb);
@@ -839,6 +855,45 @@ int solve_normal(mdwf_ctx* c, int nrhs, void* xo, const void* src, const mdwf_so
 
 using namespace mdwf;
 
+namespace {
+
+// Single-right-hand-side FP64 scratch of the source preparation and the
+// reconstruction; rhs r of the batch (tables and mass of rhs r).
+struct RhsScratch {
+    void *be, *bp, *xe, *t;
+    void* stage;  // one full field when the user buffers are in host memory
+};
+
+// b_r -> (b_e, b'_o) with b'_o = A b_o + 1/2 A H_oe M_phi (A b_e), A = I^-1
+// (the Schur decomposition, D_br = -1/2 H_oe M_phi); xe and t are scratch.
+int prepare_rhs(mdwf_ctx* c, const RhsScratch& w, const double* b, int where, int r) {
+    const Geom& g = c->g;
+    const size_t full1 = (size_t)g.Ls * 2 * g.Vh * 24 * sizeof(double);
+    int st;
+    const double* bdev = b + (size_t)r * full1 / sizeof(double);
+    if (where == MDWF_HOST) {
+        if ((st = cuda_status(cudaMemcpyAsync(w.stage, bdev, full1, cudaMemcpyHostToDevice, c->stream)))) return st;
+        bdev = (const double*)w.stage;
+    }
+    if ((st = launch_split_full(c, w.be, w.bp, bdev, MDWF_F64, 1))) return st;
+    M5Launch m{};
+    m.nrhs = 1; m.coef = 1.0; m.x = nullptr;
+    set_sop(c, MDWF_F64, SOP_A, 0, m);
+    offset_rhs(c, MDWF_F64, r, m);
+    m.out = w.xe; m.in = w.be;
+    if ((st = launch_m5(c, MDWF_F64, m))) return st;
+    m.out = w.t; m.in = w.bp;
+    if ((st = launch_m5(c, MDWF_F64, m))) return st;
+    HopLaunch h{};
+    h.nrhs = 1; h.b5 = c->b5; h.c5 = c->c5; h.mass = c->mass64;
+    h.out = w.bp; h.in = w.xe; h.x = w.t; h.coef = 0.5; h.out_parity = 1; h.gather = 1; h.dagger = 0;
+    set_sop(c, MDWF_F64, SOP_A, 0, h);
+    offset_rhs(c, MDWF_F64, r, h);
+    return launch_hop(c, MDWF_F64, h);
+}
+
+}  // namespace
+
 extern "C" int mdwf_cgne(mdwf_ctx* c, double* x, const double* b, int nrhs, const double* mf_per_rhs, int where,
                          const mdwf_solve_params* params, mdwf_solve_info* info) {
     auto t0 = std::chrono::steady_clock::now();
@@ -852,69 +907,84 @@ extern "C" int mdwf_cgne(mdwf_ctx* c, double* x, const double* b, int nrhs, cons
     if ((st = cuda_status(cudaSetDevice(c->device)))) return st;
     if ((st = ensure_tables(c, nrhs, mf_per_rhs))) return st;
     const Geom g = c->g;
-    const size_t f64 = field_bytes(MDWF_F64, g, nrhs);
-    const size_t full = (size_t)nrhs * g.Ls * 2 * g.Vh * 24 * sizeof(double);
+    const size_t f64 = field_bytes(MDWF_F64, g, nrhs), f1 = field_bytes(MDWF_F64, g, 1);
+    const size_t full1 = (size_t)g.Ls * 2 * g.Vh * 24 * sizeof(double);
     auto up = [](size_t v) { return (v + 255) / 256 * 256; };
-    const size_t need = up(f64) * 6 + (where == MDWF_HOST ? 2 * up(full) : 0);
-    if ((st = ensure_workspace(c->io, need))) return st;
+    // batched: x_o and M^dag b'_o; per right-hand side: two temporaries (+ host
+    // staging of one full field). b_e and b'_o of every right-hand side are kept
+    // from the preparation to the reconstruction when the device has room for
+    // them; otherwise they are formed again from b after the solve.
+    const size_t lean = up(f64) * 2 + up(f1) * 4 + (where == MDWF_HOST ? up(full1) : 0);
+    const size_t keep_need = up(f64) * 4 + up(f1) * 2 + (where == MDWF_HOST ? up(full1) : 0);
+    bool keep = true;
+    {
+        size_t free_b = 0, total_b = 0;
+        if ((st = cuda_status(cudaMemGetInfo(&free_b, &total_b)))) return st;
+        auto grow = [](size_t need_b, const Workspace& ws) { return need_b > ws.bytes ? need_b - ws.bytes : 0; };
+        const size_t extra = grow(keep_need, c->io) + grow(f64, c->tmp[0]) + grow(f64, c->tmp[1]) +
+                             grow(solver_bytes(c, nrhs, prm.inner_prec, 2 * 152, hop_blocks(c, prm.inner_prec, nrhs)),
+                                  c->solver);
+        keep = extra + (size_t(2) << 30) <= free_b;  // 2 GB left for the runtime and the caller
+    }
+    if ((st = ensure_workspace(c->io, keep ? keep_need : lean))) return st;
     if ((st = ensure_workspace(c->tmp[0], f64)) || (st = ensure_workspace(c->tmp[1], f64))) return st;
     char* w = (char*)c->io.p;
     auto take = [&](size_t bytes) { void* p = w; w += up(bytes); return p; };
-    void *be = take(f64), *bp = take(f64), *xo = take(f64), *xe = take(f64), *src = take(f64), *t = take(f64);
-    void* stage_b = where == MDWF_HOST ? take(full) : nullptr;
-    void* stage_x = where == MDWF_HOST ? take(full) : nullptr;
+    void *xo = take(f64), *src = take(f64);
+    void* be_all = keep ? take(f64) : nullptr;
+    void* bp_all = keep ? take(f64) : nullptr;
+    RhsScratch sw;
+    if (!keep) { sw.be = take(f1); sw.bp = take(f1); }
+    sw.xe = take(f1); sw.t = take(f1);
+    sw.stage = where == MDWF_HOST ? take(full1) : nullptr;
+    auto point_at = [&](int r) {
+        if (keep) { sw.be = (char*)be_all + (size_t)r * f1; sw.bp = (char*)bp_all + (size_t)r * f1; }
+    };
 
-    // b -> (b_e, b_o)
-    const double* bdev = b;
-    if (where == MDWF_HOST) {
-        if ((st = cuda_status(cudaMemcpyAsync(stage_b, b, full, cudaMemcpyHostToDevice, c->stream)))) return st;
-        bdev = (const double*)stage_b;
+    // src_r = M^dag b'_r, one right-hand side at a time
+    for (int r = 0; r < nrhs; ++r) {
+        point_at(r);
+        if ((st = prepare_rhs(c, sw, b, where, r))) return st;
+        if ((st = apply_op(c, (char*)src + (size_t)r * f1, sw.bp, MDWF_F64, 1, 1, r))) return st;
     }
-    if ((st = launch_split_full(c, be, bp, bdev, MDWF_F64, nrhs))) return st;
-    // b'_o = A b_o + 1/2 A H_oe M_phi (A b_e), A = I^-1 (D_br = -1/2 H_oe M_phi)
-    M5Launch m{};
-    m.nrhs = nrhs; m.coef = 1.0; m.x = nullptr;
-    set_sop(c, MDWF_F64, SOP_A, 0, m);
-    m.out = xe; m.in = be;
-    if ((st = launch_m5(c, MDWF_F64, m))) return st;
-    m.out = t; m.in = bp;
-    if ((st = launch_m5(c, MDWF_F64, m))) return st;
-    HopLaunch h{};
-    h.nrhs = nrhs; h.b5 = c->b5; h.c5 = c->c5; h.mass = c->mass64;
-    h.out = bp; h.in = xe; h.x = t; h.coef = 0.5; h.out_parity = 1; h.gather = 1; h.dagger = 0;
-    set_sop(c, MDWF_F64, SOP_A, 0, h);
-    if ((st = launch_hop(c, MDWF_F64, h))) return st;
-    // src = M^dag b'
-    if ((st = apply_op(c, src, bp, MDWF_F64, nrhs, 1))) return st;
 
     NormalResult res;
     if ((st = solve_normal(c, nrhs, xo, src, prm, res))) return st;
 
-    // |b' - M x| / |b'|
+    // per right-hand side: |b' - M x| / |b'| and x_e = A b_e + 1/2 A H_eo M_phi x_o
     std::vector<double> bb(nrhs), rr(nrhs);
-    if ((st = apply_op(c, t, xo, MDWF_F64, nrhs, 0))) return st;
-    {
-        // t = b' - M x
-        M5Launch d{};
-        d.nrhs = nrhs; d.out = t; d.in = t; d.x = bp; d.coef = -1.0;
-        set_sop(c, MDWF_F64, SOP_ID, 0, d);
-        if ((st = launch_m5(c, MDWF_F64, d))) return st;
+    for (int r = 0; r < nrhs; ++r) {
+        void* xo_r = (char*)xo + (size_t)r * f1;
+        point_at(r);
+        if (!keep && (st = prepare_rhs(c, sw, b, where, r))) return st;  // b_e, b'_o again
+        if ((st = apply_op(c, sw.t, xo_r, MDWF_F64, 1, 0, r))) return st;
+        {
+            M5Launch d{};  // t = b' - M x
+            d.nrhs = 1; d.out = sw.t; d.in = sw.t; d.x = sw.bp; d.coef = -1.0;
+            set_sop(c, MDWF_F64, SOP_ID, 0, d);
+            offset_rhs(c, MDWF_F64, r, d);
+            if ((st = launch_m5(c, MDWF_F64, d))) return st;
+        }
+        if ((st = field_dot64(c, sw.t, sw.t, 1, &rr[r]))) return st;
+        if ((st = field_dot64(c, sw.bp, sw.bp, 1, &bb[r]))) return st;
+        HopLaunch h{};
+        h.nrhs = 1; h.b5 = c->b5; h.c5 = c->c5; h.mass = c->mass64;
+        h.out = sw.t; h.in = xo_r; h.x = nullptr; h.coef = 0.5; h.out_parity = 0; h.gather = 1; h.dagger = 0;
+        set_sop(c, MDWF_F64, SOP_A, 0, h);
+        offset_rhs(c, MDWF_F64, r, h);
+        if ((st = launch_hop(c, MDWF_F64, h))) return st;
+        M5Launch m{};
+        m.nrhs = 1; m.out = sw.xe; m.in = sw.be; m.x = sw.t; m.coef = 1.0;
+        set_sop(c, MDWF_F64, SOP_A, 0, m);
+        offset_rhs(c, MDWF_F64, r, m);
+        if ((st = launch_m5(c, MDWF_F64, m))) return st;
+        double* x_r = x + (size_t)r * full1 / sizeof(double);
+        double* xdev = where == MDWF_HOST ? (double*)sw.stage : x_r;
+        if ((st = launch_join_full(c, xdev, sw.xe, xo_r, MDWF_F64, 1))) return st;
+        if (where == MDWF_HOST &&
+            (st = cuda_status(cudaMemcpyAsync(x_r, sw.stage, full1, cudaMemcpyDeviceToHost, c->stream))))
+            return st;
     }
-    if ((st = field_dot64(c, t, t, nrhs, rr.data()))) return st;
-    if ((st = field_dot64(c, bp, bp, nrhs, bb.data()))) return st;
-
-    // x_e = A b_e + 1/2 A H_eo M_phi x_o
-    h.out = t; h.in = xo; h.x = nullptr; h.coef = 0.5; h.out_parity = 0; h.gather = 1; h.dagger = 0;
-    set_sop(c, MDWF_F64, SOP_A, 0, h);
-    if ((st = launch_hop(c, MDWF_F64, h))) return st;
-    m.out = xe; m.in = be; m.x = t; m.coef = 1.0;
-    set_sop(c, MDWF_F64, SOP_A, 0, m);
-    if ((st = launch_m5(c, MDWF_F64, m))) return st;
-    double* xdev = where == MDWF_HOST ? (double*)stage_x : x;
-    if ((st = launch_join_full(c, xdev, xe, xo, MDWF_F64, nrhs))) return st;
-    if (where == MDWF_HOST &&
-        (st = cuda_status(cudaMemcpyAsync(x, stage_x, full, cudaMemcpyDeviceToHost, c->stream))))
-        return st;
     if ((st = cuda_status(cudaStreamSynchronize(c->stream)))) return st;
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     int ret = MDWF_OK;

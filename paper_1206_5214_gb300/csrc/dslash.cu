@@ -5,7 +5,7 @@
 // where H is the Wilson hopping sum of Eq. (D^Wilson),
 //   H w(x) = sum_mu [(1 - g_mu) U_mu(x) w(x+mu) + (1 + g_mu) U_mu(x-mu)^dag w(x-mu)]
 // (projector signs flipped for the hopping part of D_W^dag), and w is either
-// the input field or the input with the fifth-dimension gather of Sec. 5
+// the input field or the input with the fifth-dimension gather of Sec. 3
 // applied first: w_s = b5 psi_s + c5 (P+ psi_{s-1} + P- psi_{s+1}) with the
 // mass -m on the wrap-around terms (Eq. DWaction), i.e. w = M_phi psi.
 // Mat is an Ls x Ls real matrix per chirality (K = M_phi I^-1, I^-1, ...).
@@ -29,6 +29,10 @@ template <typename R> struct HopParams {
     // input gather w = gscale * (gown psi_s + gfac (P+ psi_{s-1} + P- psi_{s+1})) = M_phi psi;
     // gscale is applied once to the accumulated hop instead of per neighbour
     R gown, gfac, gscale;
+    // per-slice gather factors [gown(s)][gfac(s)][gscale(s)] (64 each) for
+    // s-dependent b5(s), c5(s), or null; gscale(s) then scales the hop of row s
+    // before the s-mixing and gscale above is 1
+    const R* gs;
     const R* mass;   // [rhs]
     const R* mat;    // dense tables [rhs][chir][s'][s] (sop == SOP_DENSE)
     const int4* nbr; // [parity][site][2] = cb index of x+mu (mu = 0..3), then of x-mu
@@ -66,18 +70,38 @@ __device__ __forceinline__ void project(const R* w, R* h) {
     }
 }
 
-template <int MU, int S, typename R>
-__device__ __forceinline__ void reconstruct_add(R* acc, const R* gin, R scale = R(1), bool scaled = false) {
-    R g[12];
+// Transport and reconstruction of one hopping term: g[a][i] = sum_j V[i][j] h[a][j]
+// with V = U (or U^dag when ADJ; U row-major complex 3x3), then the upper half
+// of (1 + S g_mu) gets g and the lower half S A_mu^dag g. It runs one output
+// colour i at a time so that only one colour of g is live; `scaled` multiplies
+// g by `scale` first (the FP16 norm of the neighbour).
+template <bool ADJ, int MU, int S, typename R>
+__device__ __forceinline__ void transport_add(R* acc, const R* U, const R* h, R scale, bool scaled) {
 #pragma unroll
-    for (int k = 0; k < 12; ++k) g[k] = scaled ? scale * gin[k] : gin[k];
+    for (int i = 0; i < 3; ++i) {
+        R g[4];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const R g0r = g[2 * c], g0i = g[2 * c + 1], g1r = g[6 + 2 * c], g1i = g[7 + 2 * c];
-        acc[2 * c] += g0r;
-        acc[2 * c + 1] += g0i;
-        acc[6 + 2 * c] += g1r;
-        acc[7 + 2 * c] += g1i;
+        for (int a = 0; a < 2; ++a) {
+            // complex multiply-accumulate as four fused multiply-adds per term
+            R sr = 0, si = 0;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const R ur = ADJ ? U[2 * (3 * j + i)] : U[2 * (3 * i + j)];
+                const R ui = ADJ ? -U[2 * (3 * j + i) + 1] : U[2 * (3 * i + j) + 1];
+                const R hr = h[6 * a + 2 * j], hi = h[6 * a + 2 * j + 1];
+                sr = fma(ur, hr, sr);
+                sr = fma(-ui, hi, sr);
+                si = fma(ur, hi, si);
+                si = fma(ui, hr, si);
+            }
+            g[2 * a] = scaled ? scale * sr : sr;
+            g[2 * a + 1] = scaled ? scale * si : si;
+        }
+        const R g0r = g[0], g0i = g[1], g1r = g[2], g1i = g[3];
+        acc[2 * i] += g0r;
+        acc[2 * i + 1] += g0i;
+        acc[6 + 2 * i] += g1r;
+        acc[7 + 2 * i] += g1i;
         R b0r, b0i, b1r, b1i;  // (A^dag g)_0, (A^dag g)_1
         if (MU == 0) {         // A^dag = i sigma_1: (i g1, i g0)
             b0r = -g1i; b0i = g1r; b1r = -g0i; b1i = g0r;
@@ -88,58 +112,37 @@ __device__ __forceinline__ void reconstruct_add(R* acc, const R* gin, R scale = 
         } else {
             b0r = g0r; b0i = g0i; b1r = g1r; b1i = g1i;
         }
-        acc[12 + 2 * c] += S * b0r;
-        acc[13 + 2 * c] += S * b0i;
-        acc[18 + 2 * c] += S * b1r;
-        acc[19 + 2 * c] += S * b1i;
+        acc[12 + 2 * i] += S * b0r;
+        acc[13 + 2 * i] += S * b0i;
+        acc[18 + 2 * i] += S * b1r;
+        acc[19 + 2 * i] += S * b1i;
     }
-}
-
-// g[a][i] = sum_j V[i][j] h[a][j], V = U or U^dag; U row-major complex 3x3
-template <bool ADJ, typename R>
-__device__ __forceinline__ void su3_mul(const R* U, const R* h, R* g) {
-#pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            R sr = 0, si = 0;
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const R ur = ADJ ? U[2 * (3 * j + i)] : U[2 * (3 * i + j)];
-                const R ui = ADJ ? -U[2 * (3 * j + i) + 1] : U[2 * (3 * i + j) + 1];
-                const R hr = h[6 * a + 2 * j], hi = h[6 * a + 2 * j + 1];
-                sr += ur * hr - ui * hi;
-                si += ur * hi + ui * hr;
-            }
-            g[6 * a + 2 * i] = sr;
-            g[6 * a + 2 * i + 1] = si;
-        }
 }
 
 // w = psi(s), or M_phi psi at s up to the factor gscale, for the neighbour column sr.
 // Returns a factor still to be applied to w (the FP16 norm of an ungathered
 // input, which is linear and is applied to the transported half spinor).
 template <int P, bool GATHER, typename R>
-__device__ __forceinline__ R load_input(const Field<P>& in, long long sr, int s, int Ls, const HopParams<R>& hp,
+__device__ __forceinline__ R load_input(const Field<P>& in, long long sr, int s, int Ls, R gown, R gfac,
                                         R mass, R* w) {
     if constexpr (P == MDWF_F16N && !GATHER) {
         return in.load_raw(sr, s, w);
     }
     in.load(sr, s, w);
     if (GATHER) {
-        if (hp.gown != R(1)) {
+        if (gown != R(1)) {
 #pragma unroll
-            for (int k = 0; k < 24; ++k) w[k] *= hp.gown;
+            for (int k = 0; k < 24; ++k) w[k] *= gown;
         }
-        if (hp.gfac != R(0)) {
+        if (gfac != R(0)) {
             R t[12];
             const int sm = s > 0 ? s - 1 : Ls - 1;
-            const R fm = s > 0 ? hp.gfac : -mass * hp.gfac;
+            const R fm = s > 0 ? gfac : -mass * gfac;
             in.load_half(sr, sm, 0, t);  // P+ psi_{s-1}
 #pragma unroll
             for (int k = 0; k < 12; ++k) w[k] += fm * t[k];
             const int sp = s < Ls - 1 ? s + 1 : 0;
-            const R fp = s < Ls - 1 ? hp.gfac : -mass * hp.gfac;
+            const R fp = s < Ls - 1 ? gfac : -mass * gfac;
             in.load_half(sr, sp, 1, t);  // P- psi_{s+1}
 #pragma unroll
             for (int k = 0; k < 12; ++k) w[12 + k] += fp * t[k];
@@ -150,26 +153,131 @@ __device__ __forceinline__ R load_input(const Field<P>& in, long long sr, int s,
 
 template <int P, int MU, bool GATHER, bool DAG, typename R>
 __device__ __forceinline__ void hop_dir(R* acc, const Field<P>& in, const Gauge<P>& U, const HopParams<R>& hp,
-                                        long long jf, long long jb, long long site, int s, long long rbase, R mass) {
+                                        long long jf, long long jb, long long site, int s, long long rbase, R mass,
+                                        R gown, R gfac) {
     const Geom& g = hp.g;
     constexpr int SF = DAG ? +1 : -1;  // forward projector 1 + SF g_mu
     constexpr bool SCALED = P == MDWF_F16N && !GATHER;
     {
-        R w[24], h[12], u[18], gg[12];
-        const R f = load_input<P, GATHER>(in, rbase + jf, s, g.Ls, hp, mass, w);
+        R w[24], h[12], u[18];
+        const R f = load_input<P, GATHER>(in, rbase + jf, s, g.Ls, gown, gfac, mass, w);
         project<MU, SF>(w, h);
         U.load(((long long)hp.out_parity * 4 + MU) * g.Vh + site, u);
-        su3_mul<false>(u, h, gg);
-        reconstruct_add<MU, SF>(acc, gg, f, SCALED);
+        transport_add<false, MU, SF>(acc, u, h, f, SCALED);
     }
     {
-        R w[24], h[12], u[18], gg[12];
-        const R f = load_input<P, GATHER>(in, rbase + jb, s, g.Ls, hp, mass, w);
+        R w[24], h[12], u[18];
+        const R f = load_input<P, GATHER>(in, rbase + jb, s, g.Ls, gown, gfac, mass, w);
         project<MU, -SF>(w, h);
         U.load(((long long)(1 - hp.out_parity) * 4 + MU) * g.Vh + jb, u);
-        su3_mul<true>(u, h, gg);
-        reconstruct_add<MU, -SF>(acc, gg, f, SCALED);
+        transport_add<true, MU, -SF>(acc, u, h, f, SCALED);
     }
+}
+
+// ------------------------------------------------ staged neighbour loads
+//
+// The staged variant (STAGE) copies each neighbour spinor of a thread into
+// shared memory with cp.async (LDGSTS) one neighbour ahead of its use, so two
+// neighbour loads per thread are in flight without holding registers; the
+// plain variant loads into registers when the spinor is needed. Buffers are
+// [2][chunk][thread] so that a warp's 16-byte accesses are contiguous.
+
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if (bytes == 16)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// bytes of the staging buffers per thread (two neighbour spinors)
+template <int P> struct StageBytes { static constexpr int value = 0; };
+template <> struct StageBytes<MDWF_F32> { static constexpr int value = 2 * 6 * 16; };
+template <> struct StageBytes<MDWF_F16N> { static constexpr int value = 2 * (6 * 8 + 4); };
+
+template <int P> struct Stager;
+template <> struct Stager<MDWF_F32> {
+    float4* buf;  // [2][6][nthr]
+    int nthr, tid;
+    __device__ __forceinline__ void issue(const Field<MDWF_F32>& in, long long sr, int s, int slot) const {
+        const float4* src = in.v + sr * 6 * in.Ls + s;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) cp_async(buf + (slot * 6 + k) * nthr + tid, src + (long long)k * in.Ls, 16);
+        cp_async_commit();
+    }
+    __device__ __forceinline__ float read(int slot, float* w) const {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float4 d = buf[(slot * 6 + k) * nthr + tid];
+            w[4 * k] = d.x; w[4 * k + 1] = d.y; w[4 * k + 2] = d.z; w[4 * k + 3] = d.w;
+        }
+        return 1.0f;
+    }
+};
+template <> struct Stager<MDWF_F16N> {
+    uint2* buf;   // [2][6][nthr]
+    float* nrm;   // [2][nthr]
+    int nthr, tid;
+    __device__ __forceinline__ void issue(const Field<MDWF_F16N>& in, long long sr, int s, int slot) const {
+        const uint2* src = in.v + sr * 6 * in.Ls + s;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) cp_async(buf + (slot * 6 + k) * nthr + tid, src + (long long)k * in.Ls, 8);
+        cp_async(nrm + slot * nthr + tid, in.norm + sr * in.Ls + s, 4);
+        cp_async_commit();
+    }
+    // values without the norm (applied to the transported half spinor); returns the norm
+    __device__ __forceinline__ float read(int slot, float* w) const {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Field<MDWF_F16N>::unpack_raw(buf[(slot * 6 + k) * nthr + tid], w + 4 * k);
+        return nrm[slot * nthr + tid];
+    }
+};
+
+// Hopping term n of the eight (MU, FWD) from staging slot n % 2: wait for its
+// copy, project it, refill the slot with neighbour `next` (< 0: none), then
+// transport and accumulate.
+template <int P, int MU, bool FWD, bool DAG, int WAITN, typename R>
+__device__ __forceinline__ void hop_term(R* acc, const Field<P>& in, const Gauge<P>& U, const HopParams<R>& hp,
+                                         const Stager<P>& st, long long site, int jb, int next, int s,
+                                         long long rbase) {
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int S = FWD ? SF : -SF;
+    constexpr int SLOT = FWD ? 0 : 1;
+    R h[12], u[18];
+    cp_async_wait<WAITN>();
+    R f;
+    {
+        R w[24];
+        f = st.read(SLOT, w);
+        project<MU, S>(w, h);
+    }
+    if (next >= 0) st.issue(in, rbase + next, s, SLOT);
+    if (FWD) U.load(((long long)hp.out_parity * 4 + MU) * hp.g.Vh + site, u);
+    else U.load(((long long)(1 - hp.out_parity) * 4 + MU) * hp.g.Vh + jb, u);
+    transport_add<!FWD, MU, S>(acc, u, h, f, P == MDWF_F16N);
+}
+
+// The eight terms with the next neighbour in flight while one is computed.
+template <int P, bool DAG, typename R>
+__device__ __forceinline__ void hop_staged(R* acc, const Field<P>& in, const Gauge<P>& U, const HopParams<R>& hp,
+                                           const Stager<P>& st, int4 f, int4 b, long long site, int s,
+                                           long long rbase) {
+    st.issue(in, rbase + f.x, s, 0);
+    st.issue(in, rbase + b.x, s, 1);
+    hop_term<P, 0, true, DAG, 1>(acc, in, U, hp, st, site, 0, f.y, s, rbase);
+    hop_term<P, 0, false, DAG, 1>(acc, in, U, hp, st, site, b.x, b.y, s, rbase);
+    hop_term<P, 1, true, DAG, 1>(acc, in, U, hp, st, site, 0, f.z, s, rbase);
+    hop_term<P, 1, false, DAG, 1>(acc, in, U, hp, st, site, b.y, b.z, s, rbase);
+    hop_term<P, 2, true, DAG, 1>(acc, in, U, hp, st, site, 0, f.w, s, rbase);
+    hop_term<P, 2, false, DAG, 1>(acc, in, U, hp, st, site, b.z, b.w, s, rbase);
+    hop_term<P, 3, true, DAG, 1>(acc, in, U, hp, st, site, 0, -1, s, rbase);
+    hop_term<P, 3, false, DAG, 0>(acc, in, U, hp, st, site, b.w, -1, s, rbase);
 }
 
 // Fused CG epilogues (structured s-operators only):
@@ -201,10 +309,15 @@ __device__ __forceinline__ double block_sum128(double v, double* red) {
     return tot;
 }
 
-template <int P, bool GATHER, bool DAG, bool XPAY, int FUSE>
-__global__ void __launch_bounds__(128, PrecTraits<P>::min_blocks - (GATHER ? 1 : 0))
+#ifndef MDWF_MINB_STAGE
+#define MDWF_MINB_STAGE 6
+#endif
+
+template <int P, bool GATHER, bool DAG, bool XPAY, int FUSE, bool STAGE>
+__global__ void __launch_bounds__(128, STAGE ? MDWF_MINB_STAGE : PrecTraits<P>::min_blocks - (GATHER ? 1 : 0))
     hop_kernel(Field<P> out, Field<P> in, Field<P> xf, Gauge<P> U, HopParams<typename PrecTraits<P>::real> hp,
                FuseArgs<P> fa) {
+    static_assert(!STAGE || (!GATHER && P != MDWF_F64), "staged loads: FP32 / FP16 operators without gather");
     typedef typename PrecTraits<P>::real R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Ls = hp.g.Ls;
@@ -224,16 +337,41 @@ __global__ void __launch_bounds__(128, PrecTraits<P>::min_blocks - (GATHER ? 1 :
     const bool active = site < hp.g.Vh;
     const long long rbase = (long long)rhs * hp.g.Vh;
     const R mass = hp.mass[rhs];
+    R gown = hp.gown, gfac = hp.gfac, gpre = R(1);
+    if (GATHER && hp.gs) {
+        gown = hp.gs[s];
+        gfac = hp.gs[64 + s];
+        gpre = hp.gs[128 + s];
+    }
     R acc[24];
 #pragma unroll
     for (int k = 0; k < 24; ++k) acc[k] = 0;
     if (active) {
         const int4* nb = hp.nbr + ((long long)hp.out_parity * hp.g.Vh + site) * 2;
         const int4 f = __ldg(nb), b = __ldg(nb + 1);
-        hop_dir<P, 0, GATHER, DAG>(acc, in, U, hp, f.x, b.x, site, s, rbase, mass);
-        hop_dir<P, 1, GATHER, DAG>(acc, in, U, hp, f.y, b.y, site, s, rbase, mass);
-        hop_dir<P, 2, GATHER, DAG>(acc, in, U, hp, f.z, b.z, site, s, rbase, mass);
-        hop_dir<P, 3, GATHER, DAG>(acc, in, U, hp, f.w, b.w, site, s, rbase, mass);
+        if constexpr (STAGE) {
+            // the staging buffers alias the rows of the epilogue (used after a barrier)
+            Stager<P> st;
+            if constexpr (P == MDWF_F32) {
+                st.buf = reinterpret_cast<float4*>(hs);
+            } else {
+                st.buf = reinterpret_cast<uint2*>(hs);
+                st.nrm = reinterpret_cast<float*>(st.buf + 2 * 6 * nthr);
+            }
+            st.nthr = nthr;
+            st.tid = tid;
+            hop_staged<P, DAG>(acc, in, U, hp, st, f, b, site, s, rbase);
+        } else {
+            hop_dir<P, 0, GATHER, DAG>(acc, in, U, hp, f.x, b.x, site, s, rbase, mass, gown, gfac);
+            hop_dir<P, 1, GATHER, DAG>(acc, in, U, hp, f.y, b.y, site, s, rbase, mass, gown, gfac);
+            hop_dir<P, 2, GATHER, DAG>(acc, in, U, hp, f.z, b.z, site, s, rbase, mass, gown, gfac);
+            hop_dir<P, 3, GATHER, DAG>(acc, in, U, hp, f.w, b.w, site, s, rbase, mass, gown, gfac);
+        }
+    }
+    if constexpr (STAGE) __syncthreads();
+    if (GATHER && hp.gs) {
+#pragma unroll
+        for (int k = 0; k < 24; ++k) acc[k] *= gpre;
     }
     const int sst = site_stride(Ls);
     R* mine = hs + (size_t)ly * sst + s * kRowStride;
@@ -328,17 +466,30 @@ int hop_blocks(const mdwf_ctx* c, int prec, int nrhs) {
     return (int)((c->g.Vh + SB - 1) / SB);
 }
 
-template <int P, bool G, bool D, bool X, int FU>
+template <int P, bool G, bool D, bool X, int FU, bool ST>
 static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<typename PrecTraits<P>::real>& hp) {
     typedef typename PrecTraits<P>::real R;
     const Geom& g = c->g;
     const int SB = hop_sites_per_block(c, P, h.nrhs);
     dim3 block(g.Ls, SB), grid((unsigned)((g.Vh + SB - 1) / SB * h.nrhs));
-    size_t smem = 4 * sizeof(double) + (size_t)((hp.sop == SOP_DENSE ? 2 * g.Ls * g.Ls : 0) + SB * site_stride(g.Ls)) * sizeof(R);
-    auto kern = hop_kernel<P, G, D, X, FU>;
+    const size_t rows = (size_t)SB * site_stride(g.Ls) * sizeof(R);
+    const size_t stage = ST ? (size_t)StageBytes<P>::value * g.Ls * SB : 0;
+    size_t smem = 4 * sizeof(double) + (size_t)(hp.sop == SOP_DENSE ? 2 * g.Ls * g.Ls : 0) * sizeof(R) +
+                  (rows > stage ? rows : stage);
+    auto kern = hop_kernel<P, G, D, X, FU, ST>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_status(e);
+    }
+    if (ST) {
+        // the staging buffers need shared memory for every resident block (once per device)
+        static unsigned long long carved = 0;
+        if (c->device < 64 && !(carved >> c->device & 1ull)) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                                 (int)cudaSharedmemCarveoutMaxShared);
+            if (e != cudaSuccess) return cuda_status(e);
+            carved |= 1ull << c->device;
+        }
     }
     Field<P> out = make_field<P>(h.out, g, h.nrhs);
     Field<P> in = make_field<P>(const_cast<void*>(h.in), g, h.nrhs);
@@ -365,6 +516,16 @@ static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<t
     return check_launch();
 }
 
+// The staged variant where it exists (FP32 and FP16 operators without the
+// input gather) and the context asks for it, else the plain one.
+template <int P, bool G, bool D, bool X, int FU>
+static int launch_hop_pick(mdwf_ctx* c, const HopLaunch& h, const HopParams<typename PrecTraits<P>::real>& hp) {
+    if constexpr (!G && P != MDWF_F64) {
+        if (c->hop_stage[P]) return launch_hop_variant<P, G, D, X, FU, true>(c, h, hp);
+    }
+    return launch_hop_variant<P, G, D, X, FU, false>(c, h, hp);
+}
+
 template <int P>
 static int launch_hop_t(mdwf_ctx* c, const HopLaunch& h) {
     typedef typename PrecTraits<P>::real R;
@@ -380,6 +541,12 @@ static int launch_hop_t(mdwf_ctx* c, const HopLaunch& h) {
         hp.gown = R(0); hp.gfac = (R)h.c5; hp.gscale = R(1);
     }
     if (!h.gather) { hp.gown = R(1); hp.gfac = R(0); hp.gscale = R(1); }
+    hp.gs = nullptr;
+    if (h.gather && c->sdep) {
+        hp.gown = R(1); hp.gfac = R(0); hp.gscale = R(1);
+        hp.gs = P == MDWF_F64 ? reinterpret_cast<const R*>(c->gs64) : reinterpret_cast<const R*>(c->gs32);
+        if (h.sop != SOP_DENSE || !hp.gs) return MDWF_EINVAL;
+    }
     hp.mass = reinterpret_cast<const R*>(h.mass);
     hp.mat = reinterpret_cast<const R*>(h.mat);
     hp.nbr = reinterpret_cast<const int4*>(c->nbr);
@@ -393,20 +560,20 @@ static int launch_hop_t(mdwf_ctx* c, const HopLaunch& h) {
     if (h.fuse != FUSE_NONE) {
         // fused CG epilogues: t = M p with v = A^dag t, or Ap = M^dag t folded into r
         if (h.sop == SOP_DENSE || !X || h.gather || !h.part || !h.sc) return MDWF_EINVAL;
-        if (h.fuse == FUSE_T && !h.dagger && h.out2) return launch_hop_variant<P, false, false, true, FUSE_T>(c, h, hp);
-        if (h.fuse == FUSE_R && h.dagger && h.rfield) return launch_hop_variant<P, false, true, true, FUSE_R>(c, h, hp);
+        if (h.fuse == FUSE_T && !h.dagger && h.out2) return launch_hop_pick<P, false, false, true, FUSE_T>(c, h, hp);
+        if (h.fuse == FUSE_R && h.dagger && h.rfield) return launch_hop_pick<P, false, true, true, FUSE_R>(c, h, hp);
         return MDWF_EINVAL;
     }
     if (h.gather) {
         if (h.dagger) return MDWF_EINVAL;
-        return X ? launch_hop_variant<P, true, false, true, FUSE_NONE>(c, h, hp)
-                 : launch_hop_variant<P, true, false, false, FUSE_NONE>(c, h, hp);
+        return X ? launch_hop_pick<P, true, false, true, FUSE_NONE>(c, h, hp)
+                 : launch_hop_pick<P, true, false, false, FUSE_NONE>(c, h, hp);
     }
     if (h.dagger)
-        return X ? launch_hop_variant<P, false, true, true, FUSE_NONE>(c, h, hp)
-                 : launch_hop_variant<P, false, true, false, FUSE_NONE>(c, h, hp);
-    return X ? launch_hop_variant<P, false, false, true, FUSE_NONE>(c, h, hp)
-             : launch_hop_variant<P, false, false, false, FUSE_NONE>(c, h, hp);
+        return X ? launch_hop_pick<P, false, true, true, FUSE_NONE>(c, h, hp)
+                 : launch_hop_pick<P, false, true, false, FUSE_NONE>(c, h, hp);
+    return X ? launch_hop_pick<P, false, false, true, FUSE_NONE>(c, h, hp)
+             : launch_hop_pick<P, false, false, false, FUSE_NONE>(c, h, hp);
 }
 
 int launch_hop(mdwf_ctx* c, int prec, const HopLaunch& h) {

@@ -155,6 +155,10 @@ extern "C" int mdwf_force(mdwf_ctx* c, double* dSdU, double* dSdb5, double* dSdc
                           const double* phi, int where, const mdwf_solve_params* params, mdwf_solve_info* info) {
     if (!c || !phi || (where != MDWF_HOST && where != MDWF_DEVICE)) return MDWF_EINVAL;
     if (!c->have_gauge) return MDWF_ENOGAUGE;
+    if (c->sdep) {
+        set_error_message("mdwf_force supports constant b5, c5 only (per-slice coefficients are set)");
+        return MDWF_EINVAL;
+    }
     mdwf_solve_params prm{};
     if (params) prm = *params;
     int st;

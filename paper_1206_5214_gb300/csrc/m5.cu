@@ -1,6 +1,6 @@
 // Site-local fifth-dimension operators: out = coef * Op in (+ x), Op one of
 // the s-operators of each chirality (I^-1 by the closed-form elimination of
-// Sec. 4, M_phi, K = M_phi I^-1, the shift C, or a dense Ls x Ls table), or
+// Sec. 3, M_phi, K = M_phi I^-1, the shift C, or a dense Ls x Ls table), or
 // their adjoints (chirality swapped). The Ls spinors of a 4d site are staged
 // in shared memory and each (site, component) column is solved by one thread.
 #include "mdwf_internal.cuh"

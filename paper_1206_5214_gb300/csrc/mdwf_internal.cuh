@@ -266,7 +266,7 @@ __device__ __forceinline__ long long cb_index(const Geom& g, int x, int y, int z
 //   SOP_C    : C psi
 //   SOP_MPHI : M_phi psi = b5 psi + c5 C psi
 //   SOP_A    : A psi = (M+ + M- C)^-1 psi by the closed-form elimination of
-//              Sec. 4: with r = M-/M+, kappa = m r,
+//              Sec. 3: with r = M-/M+, kappa = m r,
 //                Psi_{Ls-1} = [b_{Ls-1} + kappa sum_{s<Ls-1} (-r)^s b_s] / (M+ (1 - kappa (-r)^{Ls-1}))
 //                Psi_s      = b_s / M+ - r Psi_{s+1}   (s = Ls-2 .. 0)
 //   SOP_K    : K psi = M_phi A psi, fused into the back substitution
@@ -464,6 +464,14 @@ struct mdwf_ctx {
     // 1: apply every s-operator as a dense table (any coefficients); 0: the
     // closed-form recursions where they are stable (|M-/M+| <= 0.9)
     bool dense_s = false;
+    bool dense_s_base = false;  // the choice for constant coefficients
+    // per-slice coefficients b5(s), c5(s) (Sec. 2.1, Sec. 4.3); when set, every s-operator
+    // is a dense table and the gather of the hop takes per-slice factors from
+    // gs64 / gs32 = [gown(s)][gfac(s)][gscale(s)], 64 entries each
+    bool sdep = false;
+    double b5s[64] = {0}, c5s[64] = {0};
+    double* gs64 = nullptr;
+    float* gs32 = nullptr;
     // scratch fields used inside one apply: [0] even-parity z, [1] odd-parity v
     mdwf::Workspace tmp[2];
     // solver workspace (CG fields) and the fields of the entry points around it
@@ -484,6 +492,8 @@ struct mdwf_ctx {
     long long applies[3] = {0, 0, 0};
     // autotuned 4d sites per hop block, [precision][nrhs] (0 = default)
     int sb_tune[3][65] = {};
+    // 1: FP32 / FP16 hops stage neighbour spinors in shared memory (cp.async), [precision]
+    int hop_stage[3] = {0, 0, 0};
     bool autotune = false;
     // content of the CUDA graph being captured (added once per replay)
     long long cap_launches = 0;
@@ -578,8 +588,20 @@ struct M5Launch {
 };
 int launch_m5(mdwf_ctx* c, int prec, const M5Launch& m);
 
-// operator chains (api.cu)
-int apply_op(mdwf_ctx* c, void* out, const void* in, int prec, int nrhs, int dagger);
+// Points the per-rhs table and mass pointers of a launch (set by set_sop) at
+// right-hand side rhs0 of the context's current batch, for launches on a
+// slice of nrhs right-hand sides starting at rhs0.
+template <class L> inline void offset_rhs(const mdwf_ctx* c, int prec, int rhs0, L& l) {
+    if (rhs0 == 0) return;
+    const size_t es = prec == MDWF_F64 ? sizeof(double) : sizeof(float);
+    if (l.mat) l.mat = (const char*)l.mat + (size_t)rhs0 * 2 * c->g.Ls * c->g.Ls * es;
+    const void* m = l.mass ? l.mass : (prec == MDWF_F64 ? (const void*)c->mass64 : (const void*)c->mass32);
+    l.mass = (const char*)m + (size_t)rhs0 * es;
+}
+
+// operator chains (api.cu); rhs0: the fields are right-hand sides rhs0 ..
+// rhs0 + nrhs - 1 of the batch the tables were built for
+int apply_op(mdwf_ctx* c, void* out, const void* in, int prec, int nrhs, int dagger, int rhs0 = 0);
 int tune_hop(mdwf_ctx* c, int prec, int nrhs, int* chosen);
 
 // solver (cg.cu)

@@ -48,7 +48,7 @@ def pauli_gammas():
 
 
 def wall_permutation(Ls: int) -> np.ndarray:
-    """The permutation of Sec. 3.1 / Eq. (Pmatrix): P_{ss'} = delta_{ss'} P- + delta_{s',s+1 mod Ls} P+,
+    """The permutation of Sec. 2.2 / Eq. (Pmatrix): P_{ss'} = delta_{ss'} P- + delta_{s',s+1 mod Ls} P+,
     as a (4 Ls) x (4 Ls) matrix in the [s][spin] ordering (colour left out)."""
     Pp = np.diag([1, 1, 0, 0]).astype(complex)
     Pm = np.diag([0, 0, 1, 1]).astype(complex)

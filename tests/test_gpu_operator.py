@@ -211,3 +211,23 @@ def test_autotune_keeps_results_and_cache(tmp_path):
         for shape in (1, 2, 4, 8):
             mdwf.mdwf_set_tuning(c.h, F32, 1, shape)
             check(c.apply(odd, F32)[0], ref, F32)
+
+
+@pytest.mark.parametrize("prec", [F32, F16N])
+@pytest.mark.parametrize("dims,Ls", [((8, 4, 4, 4), 16), ((6, 2, 2, 4), 6)], ids=["Ls16", "ragged-Ls6"])
+def test_staged_loads_match_plain(prec, dims, Ls):
+    """Neighbour spinors staged in shared memory (cp.async) give the operator of
+    the plain loads (the same arithmetic), and both match the oracle."""
+    U, odd, p = setup(dims, Ls, 1.5, 0.5, 0.02, 0.3, 8)
+    with Ctx(dims, Ls, 1.8, 1.5, 0.5, 0.02, U) as c:
+        for dagger in (False, True):
+            ref = oracle.m(odd, U, p, dagger=dagger)
+            mdwf.mdwf_set_staging(c.h, prec, False)
+            a = c.apply(odd, prec, dagger)[0]
+            mdwf.mdwf_set_staging(c.h, prec, True)
+            assert mdwf.mdwf_get_staging(c.h, prec)
+            b = c.apply(odd, prec, dagger)[0]
+            assert np.abs(a - b).max() <= 1e-6 * np.abs(a).max()
+            check(b, ref, prec)
+        with pytest.raises(mdwf.MdwfError):
+            mdwf.mdwf_set_staging(c.h, F64, True)

@@ -205,7 +205,7 @@ def test_dw_gamma5_hermitian(orc, tiny):
 
 @pytest.mark.parametrize("b5,c5", [(1.5, 0.5), (1.0, 0.0)])
 def test_gamma5_reflection_hermiticity(orc, tiny, b5, c5):
-    """gamma5 R D_-^-1 D_DW(m) is Hermitian (Eq. Rsym and the Gamma5 relation of Sec. 3)."""
+    """gamma5 R D_-^-1 D_DW(m) is Hermitian (Eq. Rsym and the Gamma5 relation of Sec. 2.1)."""
     dims, U = tiny
     Ls, V = 4, int(np.prod(dims))
     p = orc.Params(dims, Ls, 1.8, b5, c5, 0.1)
@@ -224,7 +224,7 @@ def test_gamma5_reflection_hermiticity(orc, tiny, b5, c5):
 @pytest.mark.parametrize("b5,c5", [(1.5, 0.5), (1.0, 0.0), (1.0, 1.0)])
 def test_overlap_identity_random_links(orc, tiny, b5, c5):
     """Random links: [A^DW]_11 = D_ov(m)^-1, K^DW = identity off the first
-    column, and Det[D_DW(1)^-1 D_DW(m)] = Det[D_ov(m)] (Sec. 3.1, App. A)."""
+    column, and Det[D_DW(1)^-1 D_DW(m)] = Det[D_ov(m)] (Sec. 2.2, App. A)."""
     dims, U = tiny
     Ls, M5, m = 4, 1.8, 0.1
     V = int(np.prod(dims))
@@ -297,7 +297,7 @@ def _eo_perm(dims, Ls):
 def test_blocks_and_schur_complement(orc, tiny, b5, c5):
     """I_rr, D_rb, D_br are the red/black blocks of the dense D_DW; I_rr^-1 by
     the closed form inverts I_rr; M equals the Schur complement
-    1 - I_bb^-1 D_br I_rr^-1 D_rb computed by dense algebra (Sec. 4)."""
+    1 - I_bb^-1 D_br I_rr^-1 D_rb computed by dense algebra (Sec. 3)."""
     dims, U = tiny
     Ls = 4
     p = orc.Params(dims, Ls, 1.8, b5, c5, 0.1)

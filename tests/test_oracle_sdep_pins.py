@@ -10,9 +10,9 @@ D-^(s) = c5(s) D_W - 1 (Eq. DWaction). What fixes the oracle here:
   product T^-Ls = T_1^-1 T_2^-1 ... T_Ls^-1, the first column of
   P^dag D_DW(1)^-1 D_DW(m) P is D_ov(m) = (1+m)/2 + (1-m)/2 gamma5 (T^-Ls - 1)/(T^-Ls + 1),
   the other columns are the identity and the determinants agree; checked by
-  dense algebra with random links, for the Zolotarev-type profile of Sec. 5
+  dense algebra with random links, for the Zolotarev-type profile of Sec. 4.3
   (b5(s) - c5(s) fixed, commuting T_s) and for a generic profile;
-* Sec. 3: with a reflection-symmetric profile gamma5 R D_-^-1 D_DW is Hermitian,
+* Sec. 2.1: with a reflection-symmetric profile gamma5 R D_-^-1 D_DW is Hermitian,
   and it is not for a profile without that symmetry;
 * the red/black blocks, I_rr^-1, the Schur complement and the solve against
   dense algebra, as for constant coefficients.
@@ -24,7 +24,7 @@ import synthetic as sy
 from _pins import dense_of
 
 GENERIC = ((1.2, 1.9, 1.4, 2.3), (0.1, 0.8, 0.2, 1.0))          # b5(s) - c5(s) varies, no symmetry
-ZOLO = ((1.1, 1.6, 2.4, 1.3), (0.1, 0.6, 1.4, 0.3))             # b5(s) - c5(s) = 1 (Sec. 5)
+ZOLO = ((1.1, 1.6, 2.4, 1.3), (0.1, 0.6, 1.4, 0.3))             # b5(s) - c5(s) = 1 (Sec. 4.3)
 SYMM = ((1.3, 2.0, 2.0, 1.3), (0.2, 1.1, 1.1, 0.2))             # b5(s) = b5(Ls+1-s), c5 likewise
 
 
@@ -81,7 +81,7 @@ def _eo_index(dims, Ls):
 
 def test_constant_arrays_equal_constant_operator(orc, tiny):
     """b5(s) = b5, c5(s) = c5 for all s: the general Ls x Ls elimination and the
-    closed form of Sec. 4 give the same I_rr^-1 and the same M, M^dag."""
+    closed form of Sec. 3 give the same I_rr^-1 and the same M, M^dag."""
     dims, U = tiny
     Ls = 6
     p0 = orc.Params(dims, Ls, 1.8, 1.5, 0.5, 0.07)
@@ -124,7 +124,7 @@ def test_transfer_matrix_overlap_identity(orc, tiny, prof):
 
 
 def test_zolotarev_type_profile_order_free(orc, tiny):
-    """With b5(s) - c5(s) fixed the T_s commute (Sec. 5): permuting the slices
+    """With b5(s) - c5(s) fixed the T_s commute (Sec. 4.3): permuting the slices
     leaves the first column of K^DW unchanged."""
     dims, U = tiny
     V = int(np.prod(dims))
