@@ -35,6 +35,10 @@ DIMS = (16, 16, 16, 32)
 LS, M5, B5, C5, MF, EPS = 16, 1.8, 1.5, 0.5, 0.01, 0.2
 GAUGE_SEED, SOURCE_SEED = 1002, 2002
 FLOPS_PER_SITE = 3120.0      # per odd 5d site and M (or M^dag) application
+# DRAM bytes (read + write) per launch of a kernel in this workload's solve, from one
+# ncu capture of the kernels as they are now (profiles/hop_kernels_cgne_iteration_*);
+# a kernel that changes drops out of this table until it is captured again.
+NCU_TRAFFIC = {"hop_xpay_f32": 252.558336e6 + 176.487424e6}
 METRIC = "Moebius Dslash GFLOP/s in CGNE to 1e-10 (mixed FP32/FP64)"
 N5 = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2 * LS
 
@@ -336,7 +340,8 @@ def main() -> None:
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     achieved = top["bytes"] / top["launches"] / (top["ms"] / top["launches"] * 1e-3) / 1e9
     roofline = {"kernel": top["name"], "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "peak_source": peak_src, "traffic": None,
+                "frac": achieved / hbm_peak, "peak_source": peak_src,
+                "traffic": NCU_TRAFFIC.get(top["name"]),
                 "launches": top["launches"], "avg_us": 1e3 * top["ms"] / top["launches"],
                 "share_of_solve_kernel_time": top["ms"] / total_ms,
                 "algorithmic_bytes_per_launch": top["bytes"] / top["launches"]}

@@ -183,7 +183,7 @@ typedef struct {
     int maxiter;          /* CG iteration cap; 0 = 20000 */
     int inner_prec;       /* MDWF_F64: plain FP64 CG; MDWF_F32 / MDWF_F16N: mixed precision
                              with FP64 reliable updates of x and the true residual */
-    double delta;         /* reliable-update threshold on |r| / max |r|; 0 = 0.01 (FP32 inner), 0.1 (FP16N) */
+    double delta;         /* reliable-update threshold on |r| / max |r|; 0 = 0.005 (FP32 inner), 0.1 (FP16N) */
     int check_every;      /* iterations between host convergence polls; 0 = 8 */
     int use_graph;        /* 1: replay the CG iteration as a captured CUDA graph */
 } mdwf_solve_params;
@@ -208,6 +208,49 @@ typedef struct {
  */
 int mdwf_cgne(mdwf_ctx *ctx, double *x, const double *b, int nrhs, const double *mf_per_rhs,
               int where, const mdwf_solve_params *params, mdwf_solve_info *info);
+
+/*
+ * out = D_DW(m) in (dagger = 1: D_DW(m)^dag), the full unpreconditioned
+ * operator of Eq. MoebiusOp on nrhs full 5d fields (user full format,
+ * complex128, host or device as where says; in != out). FP64. mf_per_rhs:
+ * NULL or nrhs masses (host). Synchronises the stream for host buffers.
+ */
+int mdwf_apply_full(mdwf_ctx *ctx, double *out, const double *in, int nrhs, const double *mf_per_rhs,
+                    int where, int dagger);
+
+/*
+ * The effective 4d overlap operator of Sec. 2.2 on nrhs 4d fields psi (user
+ * 4d format [rhs][t][z][y][x][spin][colour], complex128, host or device):
+ *   out = D_ov(m) psi = [P^dag D_DW(1)^-1 D_DW(m) P psi~]_{s=1},  psi~_s = psi delta_{s,1},
+ * P the wall permutation of Sec. 2.2 ((P x)_s = P- x_s + P+ x_{s+1}). The
+ * inverse is a Pauli-Villars solve (mdwf_cgne at mass 1 for every right-hand
+ * side, params and info as there). out != psi. Synchronises the stream.
+ * Returns the solve's status (MDWF_ENOCONV still writes out).
+ */
+int mdwf_overlap_apply(mdwf_ctx *ctx, double *out, const double *psi, int nrhs, const double *mf_per_rhs,
+                       int where, const mdwf_solve_params *params, mdwf_solve_info *info);
+
+/*
+ * Bulk domain-wall solution from a 4d overlap solution (Sec. 2.3): given
+ * psi = D_ov(m)^-1 b, writes the 5d Psi = P^dag D_DW(m)^-1 D_DW(1) P B of the
+ * wall source B_s = b delta_{s,1} as Psi_1 = psi, Psi_s = -Omega_s (s > 1),
+ * Omega = P^dag D_DW(1)^-1 D_DW(m) P psi~ (one Pauli-Villars solve).
+ * Psi: full 5d user format; psi: 4d user format; both host or both device.
+ * Synchronises the stream; returns the solve's status.
+ */
+int mdwf_pv_reconstruct(mdwf_ctx *ctx, double *Psi, const double *psi, int nrhs, const double *mf_per_rhs,
+                        int where, const mdwf_solve_params *params, mdwf_solve_info *info);
+
+/*
+ * The chiral-symmetry violation of the effective overlap operator,
+ * out = Delta_Ls psi = (1 - eps_Ls^2) psi / 4 (Eq. Delta_Ls), with
+ * eps_Ls psi = gamma5 (2 D_ov(m) psi - (1 + m) psi) / (1 - m) from two
+ * applications of mdwf_overlap_apply (two Pauli-Villars solves). 4d user
+ * format, host or device; out != psi; every mass must differ from 1.
+ * info receives the second solve's statistics. Synchronises the stream.
+ */
+int mdwf_gw_violation(mdwf_ctx *ctx, double *out, const double *psi, int nrhs, const double *mf_per_rhs,
+                      int where, const mdwf_solve_params *params, mdwf_solve_info *info);
 
 /*
  * Derivatives of the action S = phi^dag (M^dag M)^-1 phi with M the operator

@@ -20,6 +20,7 @@ __all__ = [
     "mdwf_create", "mdwf_destroy", "mdwf_set_stream", "mdwf_set_s_coefficients", "mdwf_get_s_coefficients",
     "mdwf_load_gauge", "mdwf_field_bytes",
     "mdwf_field_import", "mdwf_field_export", "mdwf_apply", "mdwf_apply_dag", "mdwf_cgne",
+    "mdwf_apply_full", "mdwf_overlap_apply", "mdwf_pv_reconstruct", "mdwf_gw_violation",
     "mdwf_strerror", "mdwf_force", "mdwf_apply_noalloc", "mdwf_autotune", "mdwf_set_tuning",
     "mdwf_get_tuning", "mdwf_set_staging", "mdwf_get_staging", "mdwf_profile_enable", "mdwf_profile_read", "mdwf_counters", "SolveParams",
     "SolveInfo", "KernelStat",
@@ -94,6 +95,10 @@ def load(build_if_missing: bool = True):
         "mdwf_apply_dag": (ip, [vp, vp, vp, ip, ip, dp]),
         "mdwf_cgne": (ip, [vp, vp, vp, ip, dp, ip, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]),
         "mdwf_apply_noalloc": (ip, [vp, vp, vp, ip, ip, dp, ip]),
+        "mdwf_apply_full": (ip, [vp, vp, vp, ip, dp, ip, ip]),
+        "mdwf_overlap_apply": (ip, [vp, vp, vp, ip, dp, ip, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]),
+        "mdwf_pv_reconstruct": (ip, [vp, vp, vp, ip, dp, ip, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]),
+        "mdwf_gw_violation": (ip, [vp, vp, vp, ip, dp, ip, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]),
         "mdwf_force": (ip, [vp, vp, dp, dp, dp, vp, ip, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]),
         "mdwf_profile_enable": (ip, [vp, ip]),
         "mdwf_profile_read": (ip, [vp, ctypes.POINTER(KernelStat), ip, ctypes.POINTER(ctypes.c_int), ip]),
@@ -245,6 +250,50 @@ def mdwf_cgne(ctx, x, b, nrhs: int = 1, mf_per_rhs=None, tol: float = 1e-10, max
     if raise_on_error and st not in (0,):
         raise MdwfError(st, "mdwf_cgne")
     return st, list(infos)
+
+
+def mdwf_apply_full(ctx, out, inp, nrhs: int = 1, mf_per_rhs=None, dagger: bool = False) -> None:
+    """out = D_DW(m) in (or its adjoint) on full 5d fields (complex128, user order), FP64."""
+    po, wo = _ptr_where(out)
+    pi, wi = _ptr_where(inp)
+    if wo != wi:
+        raise ValueError("out and in must both be host or both be device buffers")
+    _check(load().mdwf_apply_full(ctx, po, pi, int(nrhs), _masses(mf_per_rhs), wi, int(bool(dagger))),
+           "mdwf_apply_full")
+
+
+def _pv_call(fn, name, ctx, out, psi, nrhs, mf_per_rhs, tol, maxiter, raise_on_error):
+    po, wo = _ptr_where(out)
+    pp, wp = _ptr_where(psi)
+    if wo != wp:
+        raise ValueError("both buffers must be host or both device")
+    prm = SolveParams(float(tol), int(maxiter), MDWF_F64, 0.0, 8, 1)
+    infos = (SolveInfo * int(nrhs))()
+    st = fn(ctx, po, pp, int(nrhs), _masses(mf_per_rhs), wp, ctypes.byref(prm), infos)
+    if raise_on_error and st != 0:
+        raise MdwfError(st, name)
+    return st, list(infos)
+
+
+def mdwf_overlap_apply(ctx, out4, psi4, nrhs: int = 1, mf_per_rhs=None, tol: float = 1e-12, maxiter: int = 20000,
+                       raise_on_error: bool = True):
+    """out4 = D_ov(m) psi4 through a Pauli-Villars solve; returns (status, [SolveInfo])."""
+    return _pv_call(load().mdwf_overlap_apply, "mdwf_overlap_apply", ctx, out4, psi4, nrhs, mf_per_rhs, tol,
+                    maxiter, raise_on_error)
+
+
+def mdwf_pv_reconstruct(ctx, Psi5, psi4, nrhs: int = 1, mf_per_rhs=None, tol: float = 1e-12, maxiter: int = 20000,
+                        raise_on_error: bool = True):
+    """5d Psi (Sec. 2.3) from the 4d overlap solution psi4; returns (status, [SolveInfo])."""
+    return _pv_call(load().mdwf_pv_reconstruct, "mdwf_pv_reconstruct", ctx, Psi5, psi4, nrhs, mf_per_rhs, tol,
+                    maxiter, raise_on_error)
+
+
+def mdwf_gw_violation(ctx, out4, psi4, nrhs: int = 1, mf_per_rhs=None, tol: float = 1e-12, maxiter: int = 20000,
+                      raise_on_error: bool = True):
+    """out4 = Delta_Ls psi4 = (1 - eps^2) psi4 / 4 through two overlap applications."""
+    return _pv_call(load().mdwf_gw_violation, "mdwf_gw_violation", ctx, out4, psi4, nrhs, mf_per_rhs, tol, maxiter,
+                    raise_on_error)
 
 
 def mdwf_apply_noalloc(ctx, out, inp, prec: int, nrhs: int = 1, mf_per_rhs=None, dagger: bool = False) -> None:

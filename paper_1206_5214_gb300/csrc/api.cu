@@ -161,14 +161,13 @@ static void matmul(int n, const double* a, const double* b, double* c) {
 }
 
 // out[t][chir][s'][s] = Mat_t,chir(s, s') for one mass, t = table_index(sop, swap);
-// chir 0 = P+, 1 = P-. The shift C is N' (psi_{s+1}, row Ls-1 takes -m psi_0)
-// on P- and N'^T on P+; the adjoint (swap) exchanges them.
+// chir 0 = P+, 1 = P-.
 // Ls x Ls factors per chirality (Eq. D_5d_matrix, Sec. 3) with row
 // coefficients b5(s), c5(s): C = N' on P- (C_{s,s+1} = 1, C_{Ls,1} = -m) and
 // N'^T on P+; M_phi = diag(b5) + diag(c5) C, I = diag(M+) + diag(M-) C,
-// A = I^-1, K = M_phi A. swap = 1 stores the transposes of the same chirality,
-// which the adjoint chain applies (for constant coefficients these equal the
-// other chirality's matrices).
+// A = I^-1, K = M_phi A, and I itself for the full operator. swap = 1 stores
+// the transposes of the same chirality, which the adjoint chain applies (for
+// constant coefficients these equal the other chirality's matrices).
 static bool build_tables(int Ls, double M5, const double* b5s, const double* c5s, double mf, double* out) {
     const int n = Ls, nn = Ls * Ls;
     for (int chir = 0; chir < 2; ++chir) {
@@ -197,9 +196,9 @@ static bool build_tables(int Ls, double M5, const double* b5s, const double* c5s
         for (int s = 0; s < n; ++s) scale = fmax(scale, 1.0 + fabs(4.0 - M5) * fmax(fabs(b5s[s]), fabs(c5s[s])));
         if (!invert(n, Mee.data(), A.data(), 1e-12 * scale)) return false;
         matmul(n, Mphi.data(), A.data(), K.data());
-        const double* mats[5] = {Id.data(), A.data(), Mphi.data(), K.data(), C.data()};  // SOP_ID .. SOP_C
+        const double* mats[6] = {Id.data(), A.data(), Mphi.data(), K.data(), C.data(), Mee.data()};  // SOP_ID .. SOP_MEE
         for (int swap = 0; swap < 2; ++swap)
-            for (int op = SOP_ID; op <= SOP_C; ++op) {
+            for (int op = SOP_ID; op <= SOP_MEE; ++op) {
                 double* dst = out + ((size_t)table_index(op, swap) * 2 + chir) * nn;
                 const double* M = mats[op - SOP_ID];
                 // (s, s') at [s'][s]; the transpose puts (s', s) there
@@ -367,8 +366,13 @@ int tune_hop(mdwf_ctx* c, int prec, int nrhs, int* chosen) {
     c->sb_tune[prec][nrhs] = best_sb;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    // the scratch fields are needed only while tuning: give the memory back
+    const int st2 = cuda_status(cudaStreamSynchronize(c->stream));
+    cudaFree(c->tune.p);
+    c->tune.p = nullptr;
+    c->tune.bytes = 0;
     if (chosen) *chosen = best_sb;
-    return st;
+    return st ? st : st2;
 }
 
 }  // namespace mdwf
@@ -439,6 +443,7 @@ int mdwf_destroy(mdwf_ctx* c) {
     if (!c) return MDWF_OK;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    cudaGetLastError();  // an earlier call's failure was reported by that call
     for (int k = 0; k < 2; ++k) cudaFree(c->gauge[k]);
     cudaFree(c->tab64); cudaFree(c->tab32); cudaFree(c->mass64); cudaFree(c->mass32);
     cudaFreeHost(c->tab_host);
@@ -446,6 +451,9 @@ int mdwf_destroy(mdwf_ctx* c) {
     cudaFree(c->solver.p);
     cudaFree(c->io.p);
     cudaFree(c->tune.p);
+    cudaFree(c->aux.p);
+    cudaFree(c->ov.p);
+    cudaFree(c->gw.p);
     cudaFree(c->red_partials);
     cudaFree(c->nbr);
     cudaFree(c->gs64); cudaFree(c->gs32);

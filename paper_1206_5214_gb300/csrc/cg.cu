@@ -26,7 +26,6 @@
 namespace mdwf {
 
 enum { S_RR = 0, S_PAP, S_ALPHA, S_BETA, S_SRC2, S_ACTIVE, S_STATUS, S_AUX, S_ITERS, S_NUM };
-constexpr int kMaxRhs = 64;
 constexpr int kRedThreads = 256;
 #define SC(k, r) sc[(k) * kMaxRhs + (r)]
 
@@ -921,9 +920,15 @@ extern "C" int mdwf_cgne(mdwf_ctx* c, double* x, const double* b, int nrhs, cons
         size_t free_b = 0, total_b = 0;
         if ((st = cuda_status(cudaMemGetInfo(&free_b, &total_b)))) return st;
         auto grow = [](size_t need_b, const Workspace& ws) { return need_b > ws.bytes ? need_b - ws.bytes : 0; };
-        const size_t extra = grow(keep_need, c->io) + grow(f64, c->tmp[0]) + grow(f64, c->tmp[1]) +
-                             grow(solver_bytes(c, nrhs, prm.inner_prec, 2 * 152, hop_blocks(c, prm.inner_prec, nrhs)),
-                                  c->solver);
+        size_t extra = grow(keep_need, c->io) + grow(f64, c->tmp[0]) + grow(f64, c->tmp[1]);
+        // the solver workspace, or the autotuner's two scratch fields before it (freed after tuning)
+        size_t later = grow(solver_bytes(c, nrhs, prm.inner_prec, 2 * 152, hop_blocks(c, prm.inner_prec, nrhs)),
+                            c->solver);
+        if (c->autotune) {
+            const size_t tune_f = 2 * up(field_bytes(MDWF_F64, g, nrhs));
+            if (tune_f > later) later = tune_f;
+        }
+        extra += later;
         keep = extra + (size_t(2) << 30) <= free_b;  // 2 GB left for the runtime and the caller
     }
     if ((st = ensure_workspace(c->io, keep ? keep_need : lean))) return st;

@@ -37,6 +37,7 @@
 namespace mdwf {
 
 constexpr int kMaxLs = 32;
+constexpr int kMaxRhs = 64;  // right-hand sides per call
 
 struct Geom {
     int X, Y, Z, T, Ls;
@@ -270,8 +271,9 @@ __device__ __forceinline__ long long cb_index(const Geom& g, int x, int y, int z
 //                Psi_{Ls-1} = [b_{Ls-1} + kappa sum_{s<Ls-1} (-r)^s b_s] / (M+ (1 - kappa (-r)^{Ls-1}))
 //                Psi_s      = b_s / M+ - r Psi_{s+1}   (s = Ls-2 .. 0)
 //   SOP_K    : K psi = M_phi A psi, fused into the back substitution
+//   SOP_MEE  : I psi = M+ psi + M- C psi (the site-diagonal block of Eq. D_5d_matrix)
 //   SOP_DENSE: a dense Ls x Ls table (any coefficients)
-enum SOp { SOP_DENSE = 0, SOP_ID = 1, SOP_A = 2, SOP_MPHI = 3, SOP_K = 4, SOP_C = 5 };
+enum SOp { SOP_DENSE = 0, SOP_ID = 1, SOP_A = 2, SOP_MPHI = 3, SOP_K = 4, SOP_C = 5, SOP_MEE = 6 };
 
 template <typename R> struct SCoef {
     R b5, c5, Mp, Mm;
@@ -329,8 +331,9 @@ __device__ __forceinline__ void column_op(R* base, int stride, int Ls, int op, b
             o.y = sc.b5 * li - m * sc.c5 * pi;
             *at(Ls - 1) = o;
         }
-    } else if (op == SOP_MPHI || op == SOP_C) {
-        const R w0 = op == SOP_MPHI ? sc.b5 : R(0), w1 = op == SOP_MPHI ? sc.c5 : R(1);
+    } else if (op == SOP_MPHI || op == SOP_C || op == SOP_MEE) {
+        const R w0 = op == SOP_MPHI ? sc.b5 : op == SOP_MEE ? sc.Mp : R(0);
+        const R w1 = op == SOP_MPHI ? sc.c5 : op == SOP_MEE ? sc.Mm : R(1);
         const C f0 = *at(0);
         C cur = f0;
         for (int s = 0; s < Ls - 1; ++s) {
@@ -410,7 +413,7 @@ __device__ __forceinline__ void block_columns(R* hs, int SB, int Ls, int op, boo
 // table[t][rhs][chir][s'][s] holds element (s, s') (transposed, so that the
 // Ls threads of a column read consecutive words); chir 0 is the P+ half
 // (spins 0, 1), chir 1 the P- half; t = table_index(sop, swap).
-constexpr int kNumTables = 10;
+constexpr int kNumTables = 12;
 inline int table_index(int sop, int swap) { return (sop - 1) * 2 + (swap ? 1 : 0); }
 
 // ---------------------------------------------------------------- context
@@ -478,6 +481,9 @@ struct mdwf_ctx {
     mdwf::Workspace solver;
     mdwf::Workspace io;
     mdwf::Workspace tune;  // scratch fields of the autotuner
+    mdwf::Workspace aux;   // even/odd halves of the full operator
+    mdwf::Workspace ov;    // full 5d fields of the Pauli-Villars constructions
+    mdwf::Workspace gw;    // 4d fields of the chiral-violation operator
     // reduction scratch: per-rhs block partials and scalars
     double* red_partials = nullptr;
     size_t red_partials_len = 0;

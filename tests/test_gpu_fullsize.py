@@ -86,6 +86,7 @@ def test_cgne_24x24x24x64_Ls12_point_sources_mixed_f32(c3_links):
         st, info = mdwf.mdwf_cgne(h, x, b, nrhs=12, tol=1e-10, inner_prec=F32)
     finally:
         mdwf.mdwf_destroy(h)
+    print("point sources", [i.as_dict() for i in info[:2]])
     assert st == 0
     assert all(i.true_res <= 1e-10 for i in info)
     for r in (0, 11):  # spin 0 colour 0 on s = Ls - 1, and spin 3 colour 2 on s = 0
@@ -128,6 +129,8 @@ def test_cgne_32x32x32x64_Ls16_eight_masses_mixed_f16n(c5_links):
                                   maxiter=40000)
     finally:
         mdwf.mdwf_destroy(h)
+    for r, i in enumerate(info):
+        print("mf", C5_MASSES[r], i.as_dict())
     assert st == 0, [i.as_dict() for i in info]
     assert all(i.true_res <= 1e-10 for i in info)
     for r in (0, 7):
