@@ -273,6 +273,21 @@ int mdwf_force(mdwf_ctx *ctx, double *dSdU, double *dSdb5, double *dSdc5, double
                int where, const mdwf_solve_params *params, mdwf_solve_info *info);
 
 /*
+ * The action with the pseudofermion on the wall (Sec. 2.4) and its link force:
+ *   S = phi^dag P^dag D_DW(m)^-1 D_DW(1) D_DW(1)^dag D_DW(m)^-dag P phi,
+ * phi a 4d field on s = 1 (user 4d format, host or device), P the wall
+ * permutation of Sec. 2.2. Two inversions: an adjoint solve
+ * chi = D_DW(m)^-dag P phi (red/black, CG on M^dag M) and a solve
+ * psi = D_DW(m)^-1 D_DW(1) D_DW(1)^dag chi (mdwf_cgne); S = |D_DW(1)^dag chi|^2.
+ * dSdU (NULL: action only) has the gauge layout and the convention of
+ * mdwf_force (dS/dRe U + i dS/dIm U). One right-hand side; mf != 1; per-slice
+ * coefficients are allowed. info receives the second solve's statistics.
+ * Synchronises the stream; returns the worst solve status.
+ */
+int mdwf_force4d(mdwf_ctx *ctx, double *dSdU, double *S, const double *phi, int where,
+                 const mdwf_solve_params *params, mdwf_solve_info *info);
+
+/*
  * Per-kernel timing. While enabled, every kernel the context launches outside
  * a CUDA-graph capture is bracketed by two CUDA events on the launch stream
  * (solves then run without graphs). mdwf_profile_read synchronises the

@@ -119,6 +119,7 @@ def _load():
             "or_prepare": (None, [vp, vp, vp, P]),
             "or_reconstruct": (None, [vp, vp, vp, vp, P]),
             "or_solve": (ctypes.c_int, [vp, vp, vp, P, ctypes.c_double, ctypes.c_int, ip, dp]),
+            "or_solve_dag": (ctypes.c_int, [vp, vp, vp, P, ctypes.c_double, ctypes.c_int, ip, dp]),
             "or_dm_dparam": (None, [vp, vp, vp, P, ctypes.c_int]),
             "or_force": (ctypes.c_int, [vp, dp, dp, dp, vp, vp, P, ctypes.c_double, ctypes.c_int, ip]),
             "or_set_threads": (None, [ctypes.c_int]),
@@ -257,6 +258,17 @@ def dm_dparam(X: np.ndarray, U: np.ndarray, p: Params, which: str) -> np.ndarray
     out = np.empty_like(X)
     _load().or_dm_dparam(_ptr(out), _ptr(X), _ptr(U), ctypes.byref(p.c()), {"b5": 0, "c5": 1}[which])
     return out
+
+
+def solve_dag(b: np.ndarray, U: np.ndarray, p: Params, tol: float = 1e-12, maxiter: int = 20000):
+    """x = D_DW(m)^-dag b on a full 5d field by CG on D D^dag (no red/black split).
+    Returns (x, status, iters, |D^dag x - b| / |b|)."""
+    b, U = _c(b), _c(U)
+    x = np.empty_like(b)
+    it, rel = ctypes.c_int(0), ctypes.c_double(0)
+    st = _load().or_solve_dag(_ptr(x), _ptr(b), _ptr(U), ctypes.byref(p.c()), float(tol), int(maxiter),
+                              ctypes.byref(it), ctypes.byref(rel))
+    return x, int(st), int(it.value), float(rel.value)
 
 
 def force(phi: np.ndarray, U: np.ndarray, p: Params, tol: float = 1e-12, maxiter: int = 20000):

@@ -20,7 +20,7 @@ __all__ = [
     "mdwf_create", "mdwf_destroy", "mdwf_set_stream", "mdwf_set_s_coefficients", "mdwf_get_s_coefficients",
     "mdwf_load_gauge", "mdwf_field_bytes",
     "mdwf_field_import", "mdwf_field_export", "mdwf_apply", "mdwf_apply_dag", "mdwf_cgne",
-    "mdwf_apply_full", "mdwf_overlap_apply", "mdwf_pv_reconstruct", "mdwf_gw_violation",
+    "mdwf_apply_full", "mdwf_overlap_apply", "mdwf_pv_reconstruct", "mdwf_gw_violation", "mdwf_force4d",
     "mdwf_strerror", "mdwf_force", "mdwf_apply_noalloc", "mdwf_autotune", "mdwf_set_tuning",
     "mdwf_get_tuning", "mdwf_set_staging", "mdwf_get_staging", "mdwf_profile_enable", "mdwf_profile_read", "mdwf_counters", "SolveParams",
     "SolveInfo", "KernelStat",
@@ -99,6 +99,7 @@ def load(build_if_missing: bool = True):
         "mdwf_overlap_apply": (ip, [vp, vp, vp, ip, dp, ip, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]),
         "mdwf_pv_reconstruct": (ip, [vp, vp, vp, ip, dp, ip, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]),
         "mdwf_gw_violation": (ip, [vp, vp, vp, ip, dp, ip, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]),
+        "mdwf_force4d": (ip, [vp, vp, dp, vp, ip, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]),
         "mdwf_force": (ip, [vp, vp, dp, dp, dp, vp, ip, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveInfo)]),
         "mdwf_profile_enable": (ip, [vp, ip]),
         "mdwf_profile_read": (ip, [vp, ctypes.POINTER(KernelStat), ip, ctypes.POINTER(ctypes.c_int), ip]),
@@ -325,6 +326,24 @@ def mdwf_force(ctx, dSdU, phi, tol: float = 1e-12, maxiter: int = 40000, inner_p
     if raise_on_error and st != 0:
         raise MdwfError(st, "mdwf_force")
     return S.value, db5.value, dc5.value, st, info
+
+
+def mdwf_force4d(ctx, dSdU, phi4, tol: float = 1e-12, maxiter: int = 40000, raise_on_error: bool = True):
+    """S = |D(1)^dag D(m)^-dag P phi|^2 for a 4d wall pseudofermion and dS/dU (into dSdU, or
+    None for S only). Returns (S, status, SolveInfo)."""
+    pp, wp = _ptr_where(phi4)
+    pg = None
+    if dSdU is not None:
+        pg, wg = _ptr_where(dSdU)
+        if wg != wp:
+            raise ValueError("dSdU and phi must both be host or both be device buffers")
+    prm = SolveParams(float(tol), int(maxiter), MDWF_F64, 0.0, 8, 1)
+    info = SolveInfo()
+    S = ctypes.c_double(0)
+    st = load().mdwf_force4d(ctx, pg, ctypes.byref(S), pp, wp, ctypes.byref(prm), ctypes.byref(info))
+    if raise_on_error and st != 0:
+        raise MdwfError(st, "mdwf_force4d")
+    return S.value, st, info
 
 
 def mdwf_profile_enable(ctx, enable: bool = True) -> None:

@@ -454,6 +454,7 @@ int mdwf_destroy(mdwf_ctx* c) {
     cudaFree(c->aux.p);
     cudaFree(c->ov.p);
     cudaFree(c->gw.p);
+    cudaFree(c->h4.p);
     cudaFree(c->red_partials);
     cudaFree(c->nbr);
     cudaFree(c->gs64); cudaFree(c->gs32);

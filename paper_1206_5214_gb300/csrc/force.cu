@@ -121,9 +121,10 @@ __global__ void __launch_bounds__(128) force_kernel(double2* dSdU, Field<MDWF_F6
     }
 }
 
-// out = sum of the per-parity force launches; both parities cover all links
-static int launch_force(mdwf_ctx* c, double* dSdU, const void* A_odd, const void* B_even, const void* C_even,
-                        const void* D_odd) {
+// dSdU = coef [Re(A^dag dH_oe B) + Re(C^dag dH_eo D)] per link, written (not
+// accumulated) by one launch per parity of x; both parities cover all links.
+int launch_force(mdwf_ctx* c, double* dSdU, const void* A_odd, const void* B_even, const void* C_even,
+                 const void* D_odd, double coef) {
     // even x: forward (gamma_x, delta_{x+mu}), backward (alpha_{x+mu}, beta_x)
     // odd x : forward (alpha_x, beta_{x+mu}), backward (gamma_{x+mu}, delta_x)
     const Geom& g = c->g;
@@ -136,13 +137,13 @@ static int launch_force(mdwf_ctx* c, double* dSdU, const void* A_odd, const void
     {
         LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, n5 * 192.0 * 10.0 + g.Vh * 4 * 144.0, n5 * 4 * 200.0);
         force_kernel<<<grid, block, smem, c->stream>>>((double2*)dSdU, F(C_even), F(D_odd), F(A_odd), F(B_even),
-                                                       (const int4*)c->nbr, g, 0, 0.5);
+                                                       (const int4*)c->nbr, g, 0, coef);
     }
     if ((st = check_launch())) return st;
     {
         LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, n5 * 192.0 * 10.0 + g.Vh * 4 * 144.0, n5 * 4 * 200.0);
         force_kernel<<<grid, block, smem, c->stream>>>((double2*)dSdU, F(A_odd), F(B_even), F(C_even), F(D_odd),
-                                                       (const int4*)c->nbr, g, 1, 0.5);
+                                                       (const int4*)c->nbr, g, 1, coef);
     }
     return check_launch();
 }
@@ -226,7 +227,7 @@ extern "C" int mdwf_force(mdwf_ctx* c, double* dSdU, double* dSdb5, double* dSdc
 
     if (dSdU) {
         double* gdev = where == MDWF_HOST ? stage_g : dSdU;
-        if ((st = launch_force(c, gdev, al, be, ga, de))) return st;
+        if ((st = launch_force(c, gdev, al, be, ga, de, 0.5))) return st;
         if (where == MDWF_HOST &&
             (st = cuda_status(cudaMemcpyAsync(dSdU, stage_g, gb, cudaMemcpyDeviceToHost, c->stream))))
             return st;

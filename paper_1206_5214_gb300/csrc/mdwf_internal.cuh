@@ -484,6 +484,7 @@ struct mdwf_ctx {
     mdwf::Workspace aux;   // even/odd halves of the full operator
     mdwf::Workspace ov;    // full 5d fields of the Pauli-Villars constructions
     mdwf::Workspace gw;    // 4d fields of the chiral-violation operator
+    mdwf::Workspace h4;    // fields of the 4d-HMC force
     // reduction scratch: per-rhs block partials and scalars
     double* red_partials = nullptr;
     size_t red_partials_len = 0;
@@ -604,6 +605,12 @@ template <class L> inline void offset_rhs(const mdwf_ctx* c, int prec, int rhs0,
     const void* m = l.mass ? l.mass : (prec == MDWF_F64 ? (const void*)c->mass64 : (const void*)c->mass32);
     l.mass = (const char*)m + (size_t)rhs0 * es;
 }
+
+// full-field operators and the force's outer products (overlap.cu, force.cu)
+int apply_full_dev(mdwf_ctx* c, double* out, const double* in, int nrhs, int dagger);
+int launch_embed_wall(mdwf_ctx* c, double* out5, const double* in4, int nrhs);
+int launch_force(mdwf_ctx* c, double* dSdU, const void* A_odd, const void* B_even, const void* C_even,
+                 const void* D_odd, double coef);
 
 // operator chains (api.cu); rhs0: the fields are right-hand sides rhs0 ..
 // rhs0 + nrhs - 1 of the batch the tables were built for

@@ -87,7 +87,7 @@ static dim3 grid_of(long long n) {
 // out = D_DW(m) in (dagger: D_DW(m)^dag) on device full fields, FP64:
 //   (D in)_e = I in_e - 1/2 H_eo M_phi in_o,   (D in)_o = I in_o - 1/2 H_oe M_phi in_e
 //   (D^dag in)_e = I^dag in_e - 1/2 M_phi^dag H'_eo in_o, and likewise for o.
-static int apply_full_dev(mdwf_ctx* c, double* out, const double* in, int nrhs, int dagger) {
+int apply_full_dev(mdwf_ctx* c, double* out, const double* in, int nrhs, int dagger) {
     const Geom& g = c->g;
     const size_t f64 = field_bytes(MDWF_F64, g, nrhs);
     auto up = [](size_t v) { return (v + 255) / 256 * 256; };
@@ -117,6 +117,13 @@ static int apply_full_dev(mdwf_ctx* c, double* out, const double* in, int nrhs, 
         if ((st = launch_hop(c, MDWF_F64, h))) return st;
     }
     return launch_join_full(c, out, oe, oo, MDWF_F64, nrhs);
+}
+
+int launch_embed_wall(mdwf_ctx* c, double* out5, const double* in4, int nrhs) {
+    const long long V = 2 * c->g.Vh;
+    k_embed_wall<<<grid_of((long long)nrhs * c->g.Ls * V * 12), 256, 0, c->stream>>>(
+        (double2*)out5, (const double2*)in4, V, c->g.Ls, nrhs);
+    return check_launch();
 }
 
 static size_t full5_bytes(const Geom& g, int nrhs) { return (size_t)nrhs * g.Ls * 2 * g.Vh * 24 * sizeof(double); }

@@ -393,3 +393,20 @@ def test_force_finite_differences(orc):
     Md = dense_of(lambda v: orc.m(v, U, p), int(np.prod(hshape)), hshape)
     Sd = np.real(np.vdot(phi.reshape(-1), np.linalg.solve(Md.conj().T @ Md, phi.reshape(-1))))
     assert S == pytest.approx(Sd, rel=1e-11)
+
+
+def test_adjoint_solve_inverts_the_adjoint(orc, tiny):
+    """solve_dag(b) x satisfies D^dag x = b, equals the dense (D^dag)^-1 b and, for the
+    adjoint pairing, <D^-dag b, c> = <b, D^-1 c> with the red/black solve."""
+    dims, U = tiny
+    Ls = 4
+    p = orc.Params(dims, Ls, 1.8, 1.5, 0.5, 0.05)
+    b = sy.gaussian_field(dims, Ls, 2061)
+    c = sy.gaussian_field(dims, Ls, 2062)
+    x, st, it, rel = orc.solve_dag(b, U, p, tol=1e-13)
+    assert st == 0 and rel < 1e-11
+    D = _dense_ddw(orc, U, p)
+    xd = np.linalg.solve(D.conj().T, b.reshape(-1)).reshape(b.shape)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-10
+    y, st2, _, _ = orc.solve(c, U, p, tol=1e-13)
+    assert abs(np.vdot(x, c) - np.vdot(b, y)) < 1e-10 * abs(np.vdot(b, y))
