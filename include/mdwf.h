@@ -116,6 +116,17 @@ int mdwf_set_stream(mdwf_ctx *ctx, void *stream);
  */
 int mdwf_set_s_coefficients(mdwf_ctx *ctx, const double *b5s, const double *c5s);
 
+/*
+ * Chemical potential mu on the time links (Sec. 6.6): the forward time hop of
+ * D_W carries e^{+mu} and the backward one e^{-mu} ((1 -+ g_4) U_{+-4} ->
+ * e^{+-mu} (1 -+ g_4) U_{+-4}); D_W is then no longer gamma5-Hermitian and
+ * every operator, solve and construction of this library uses D_W(mu) (the
+ * adjoints D_W(mu)^dag). 0 turns it off. mdwf_force and mdwf_force4d return
+ * MDWF_EINVAL while it is set. Errors: MDWF_EINVAL for a non-finite or
+ * |mu| > 10 value.
+ */
+int mdwf_set_chemical_potential(mdwf_ctx *ctx, double mu);
+
 /* Writes the Ls coefficients in force to b5s, c5s (host, Ls values each) and
  * sets *per_slice to 1 when they are per-slice, 0 when constant. */
 int mdwf_get_s_coefficients(const mdwf_ctx *ctx, double *b5s, double *c5s, int *per_slice);

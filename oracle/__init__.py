@@ -45,7 +45,8 @@ def build(force: bool = False) -> str:
 class _Params(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int * 4), ("Ls", ctypes.c_int), ("M5", ctypes.c_double),
                 ("b5", ctypes.c_double), ("c5", ctypes.c_double), ("mf", ctypes.c_double),
-                ("b5s", ctypes.POINTER(ctypes.c_double)), ("c5s", ctypes.POINTER(ctypes.c_double))]
+                ("b5s", ctypes.POINTER(ctypes.c_double)), ("c5s", ctypes.POINTER(ctypes.c_double)),
+                ("mu", ctypes.c_double)]
 
 
 @dataclass(frozen=True)
@@ -54,8 +55,9 @@ class Params:
 
     ``b5s`` / ``c5s`` (tuples of Ls values, or None) replace the constant b5 / c5
     by per-slice coefficients b5(s), c5(s): row s of Eq. (MoebiusOp) then uses
-    D+ = b5(s) D_W + 1 and D- = c5(s) D_W - 1. The force supports constant
-    coefficients only.
+    D+ = b5(s) D_W + 1 and D- = c5(s) D_W - 1. ``mu`` is a chemical potential
+    on the time links (Sec. 6.6). The force supports constant coefficients and
+    mu = 0 only.
     """
     dims: tuple
     Ls: int
@@ -65,12 +67,14 @@ class Params:
     mf: float
     b5s: tuple | None = None
     c5s: tuple | None = None
+    mu: float = 0.0
 
     def c(self) -> _Params:
         p = _Params()
         for k in range(4):
             p.L[k] = int(self.dims[k])
         p.Ls, p.M5, p.b5, p.c5, p.mf = int(self.Ls), float(self.M5), float(self.b5), float(self.c5), float(self.mf)
+        p.mu = float(self.mu)
         keep = []
         for name in ("b5s", "c5s"):
             vals = getattr(self, name)
@@ -85,7 +89,7 @@ class Params:
 
     def with_(self, **kw) -> "Params":
         d = dict(dims=self.dims, Ls=self.Ls, M5=self.M5, b5=self.b5, c5=self.c5, mf=self.mf,
-                 b5s=self.b5s, c5s=self.c5s)
+                 b5s=self.b5s, c5s=self.c5s, mu=self.mu)
         d.update(kw)
         return Params(**d)
 
@@ -108,7 +112,8 @@ def _load():
         dp = ctypes.POINTER(ctypes.c_double)
         sig = {
             "or_gammas": (None, [vp]),
-            "or_dw": (None, [vp, vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_int]),
+            "or_dw": (None, [vp, vp, vp, ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_double,
+                             ctypes.c_int]),
             "or_ddw": (None, [vp, vp, vp, P, ctypes.c_int]),
             "or_mee": (None, [vp, vp, P, ctypes.c_int]),
             "or_dhop": (None, [vp, vp, vp, P, ctypes.c_int, ctypes.c_int]),
@@ -156,12 +161,12 @@ def gammas() -> tuple[np.ndarray, np.ndarray]:
     return out[:64].reshape(4, 4, 4), out[64:].reshape(4, 4)
 
 
-def dw(psi4: np.ndarray, U: np.ndarray, dims, M5: float, dagger: bool = False) -> np.ndarray:
+def dw(psi4: np.ndarray, U: np.ndarray, dims, M5: float, dagger: bool = False, mu: float = 0.0) -> np.ndarray:
     """D_W (Eq. D^Wilson, diagonal 4 - M5) on a 4d field of shape (T, Z, Y, X, 4, 3)."""
     psi4, U = _c(psi4), _c(U)
     out = np.empty_like(psi4)
     L = (ctypes.c_int * 4)(*[int(d) for d in dims])
-    _load().or_dw(_ptr(out), _ptr(psi4), _ptr(U), L, float(M5), int(dagger))
+    _load().or_dw(_ptr(out), _ptr(psi4), _ptr(U), L, float(M5), float(mu), int(dagger))
     return out
 
 
@@ -277,8 +282,8 @@ def force(phi: np.ndarray, U: np.ndarray, p: Params, tol: float = 1e-12, maxiter
     dS/dU has the gauge field's shape; a variation dU changes S by
     Re sum(conj(dSdU) * dU). Returns (S, dSdU, dSdb5, dSdc5, status, iters).
     """
-    if p.s_dependent:
-        raise ValueError("the oracle force supports constant b5, c5 only")
+    if p.s_dependent or p.mu != 0.0:
+        raise ValueError("the oracle force supports constant b5, c5 and mu = 0 only")
     phi, U = _c(phi), _c(U)
     G = np.zeros_like(U)
     S, db5, dc5 = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)

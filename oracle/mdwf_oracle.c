@@ -55,6 +55,7 @@ typedef struct {
     double mf;    /* quark mass m of the walls */
     const double *b5s;  /* b5(s), s = 0..Ls-1, or NULL for the constant b5 */
     const double *c5s;  /* c5(s), or NULL for the constant c5 */
+    double mu;          /* chemical potential on the time links (Sec. 6.6); 0 for none */
 } or_params;
 
 static double b5_of(const or_params *p, int s) { return p->b5s ? p->b5s[s] : p->b5; }
@@ -208,8 +209,14 @@ static void one_pm_gamma(cplx out[4][4], int mu, double sgn)
  * D_W = (4 - M5) - H/2. The input field f is a full field (half == 0) or
  * the half field of the parity opposite to x (half == 1).
  */
+/*
+ * The hopping sum at site i with a chemical potential chem on the time links
+ * ((1 -+ g_4) U_4 -> e^{+-chem} (1 -+ g_4) U_4 for the forward / backward
+ * hop, Sec. 6.6). The adjoint (dagger) has the projectors flipped and, the
+ * matrix being transposed, the factor of each direction exchanged.
+ */
 static void hop_site(cplx out[12], const cplx *f, int half, const cplx *U,
-                     const int L[4], long i, int dagger)
+                     const int L[4], long i, int dagger, double chem)
 {
     for (int k = 0; k < 12; ++k) out[k] = 0;
     double sf = dagger ? +1.0 : -1.0;
@@ -220,22 +227,27 @@ static void hop_site(cplx out[12], const cplx *f, int half, const cplx *U,
         one_pm_gamma(Sb, mu, -sf);
         const cplx *ff = f + 12 * (half ? fw / 2 : fw);
         const cplx *fb = f + 12 * (half ? bw / 2 : bw);
-        acc_spin_colour(out, 1.0, Sf, U + 9 * (4 * i + mu), 0, ff);
-        acc_spin_colour(out, 1.0, Sb, U + 9 * (4 * bw + mu), 1, fb);
+        double wf = 1.0, wb = 1.0;
+        if (mu == 3 && chem != 0.0) {
+            wf = exp(dagger ? -chem : chem);
+            wb = exp(dagger ? chem : -chem);
+        }
+        acc_spin_colour(out, wf, Sf, U + 9 * (4 * i + mu), 0, ff);
+        acc_spin_colour(out, wb, Sb, U + 9 * (4 * bw + mu), 1, fb);
     }
 }
 
 /* ------------------------------------------------------------- Wilson D_W */
 
 /* out = D_W in (dagger: D_W^dag) on full 4d fields. Eq. (D^Wilson). */
-void or_dw(cplx *out, const cplx *in, const cplx *U, const int L[4], double M5, int dagger)
+void or_dw(cplx *out, const cplx *in, const cplx *U, const int L[4], double M5, double chem, int dagger)
 {
     init_gammas();
     long V = vol4(L);
 #pragma omp parallel for schedule(static)
     for (long i = 0; i < V; ++i) {
         cplx h[12];
-        hop_site(h, in, 0, U, L, i, dagger);
+        hop_site(h, in, 0, U, L, i, dagger, chem);
         for (int k = 0; k < 12; ++k) out[12 * i + k] = (4.0 - M5) * in[12 * i + k] - 0.5 * h[k];
     }
 }
@@ -243,11 +255,11 @@ void or_dw(cplx *out, const cplx *in, const cplx *U, const int L[4], double M5, 
 /* ------------------------------------------------ 5d operator (full lattice) */
 
 /* out = c_w D_W in + c_1 in on a full 4d field (D+ : c_w = b5, c_1 = +1; D- : c5, -1) */
-static void dw_affine(cplx *out, const cplx *in, const cplx *U, const int L[4], double M5,
+static void dw_affine(cplx *out, const cplx *in, const cplx *U, const int L[4], double M5, double chem,
                       int dagger, double c_w, double c_1)
 {
     long V = vol4(L);
-    or_dw(out, in, U, L, M5, dagger);
+    or_dw(out, in, U, L, M5, chem, dagger);
     for (long k = 0; k < 12 * V; ++k) out[k] = c_w * out[k] + c_1 * in[k];
 }
 
@@ -276,22 +288,22 @@ void or_ddw(cplx *out, const cplx *in, const cplx *U, const or_params *p, int da
     cplx *t = malloc(sizeof(cplx) * n), *u = malloc(sizeof(cplx) * n);
     for (int s = 0; s < Ls; ++s) {
         cplx *o = out + s * n;
-        dw_affine(o, in + s * n, U, p->L, p->M5, dagger, b5_of(p, s), 1.0);   /* D+ psi_s */
+        dw_affine(o, in + s * n, U, p->L, p->M5, p->mu, dagger, b5_of(p, s), 1.0);   /* D+ psi_s */
         int sp = (s + 1) % Ls, sm = (s - 1 + Ls) % Ls;
         double wp = (s == Ls - 1) ? -p->mf : 1.0;   /* coefficient of the s+1 block */
         double wm = (s == 0) ? -p->mf : 1.0;        /* coefficient of the s-1 block */
         if (!dagger) {
             proj_field(t, PM, in + sp * n, V);
-            dw_affine(u, t, U, p->L, p->M5, 0, c5_of(p, s), -1.0);
+            dw_affine(u, t, U, p->L, p->M5, p->mu, 0, c5_of(p, s), -1.0);
             for (long k = 0; k < n; ++k) o[k] += wp * u[k];
             proj_field(t, PP, in + sm * n, V);
-            dw_affine(u, t, U, p->L, p->M5, 0, c5_of(p, s), -1.0);
+            dw_affine(u, t, U, p->L, p->M5, p->mu, 0, c5_of(p, s), -1.0);
             for (long k = 0; k < n; ++k) o[k] += wm * u[k];
         } else {
-            dw_affine(t, in + sp * n, U, p->L, p->M5, 1, c5_of(p, sp), -1.0);
+            dw_affine(t, in + sp * n, U, p->L, p->M5, p->mu, 1, c5_of(p, sp), -1.0);
             proj_field(u, PP, t, V);
             for (long k = 0; k < n; ++k) o[k] += wp * u[k];
-            dw_affine(t, in + sm * n, U, p->L, p->M5, 1, c5_of(p, sm), -1.0);
+            dw_affine(t, in + sm * n, U, p->L, p->M5, p->mu, 1, c5_of(p, sm), -1.0);
             proj_field(u, PM, t, V);
             for (long k = 0; k < n; ++k) o[k] += wm * u[k];
         }
@@ -308,14 +320,14 @@ void or_ddw(cplx *out, const cplx *in, const cplx *U, const or_params *p, int da
  * This is the off-site-diagonal part of D_W (dagger: of D_W^dag).
  */
 static void hop_half(cplx *out, const cplx *in, const cplx *U, const int L[4], int po,
-                     int dagger, double coef, int accumulate)
+                     int dagger, double coef, int accumulate, double chem)
 {
     long Vh = vol4(L) / 2;
 #pragma omp parallel for schedule(static)
     for (long j = 0; j < Vh; ++j) {
         long i = half_to_lex(L, j, po);
         cplx h[12];
-        hop_site(h, in, 1, U, L, i, dagger);
+        hop_site(h, in, 1, U, L, i, dagger, chem);
         for (int k = 0; k < 12; ++k) {
             cplx v = -0.5 * coef * h[k];
             out[12 * j + k] = accumulate ? out[12 * j + k] + v : v;
@@ -352,17 +364,17 @@ static void rb_block(cplx *out, const cplx *in, const cplx *U, const or_params *
         double wp = (dagger ? co[sp] : co[s]) * ((s == Ls - 1) ? -p->mf : 1.0);
         double wm = (dagger ? co[sm] : co[s]) * ((s == 0) ? -p->mf : 1.0);
         if (hop) {
-            hop_half(o, in + s * n, U, p->L, po, dagger, cd[s], 0);
+            hop_half(o, in + s * n, U, p->L, po, dagger, cd[s], 0, p->mu);
             if (!dagger) {
                 proj_field(t, PM, in + sp * n, Vh);
-                hop_half(o, t, U, p->L, po, 0, wp, 1);
+                hop_half(o, t, U, p->L, po, 0, wp, 1, p->mu);
                 proj_field(t, PP, in + sm * n, Vh);
-                hop_half(o, t, U, p->L, po, 0, wm, 1);
+                hop_half(o, t, U, p->L, po, 0, wm, 1, p->mu);
             } else {
-                hop_half(t, in + sp * n, U, p->L, po, 1, wp, 0);
+                hop_half(t, in + sp * n, U, p->L, po, 1, wp, 0, p->mu);
                 proj_field(u, PP, t, Vh);
                 for (long k = 0; k < n; ++k) o[k] += u[k];
-                hop_half(t, in + sm * n, U, p->L, po, 1, wm, 0);
+                hop_half(t, in + sm * n, U, p->L, po, 1, wm, 0, p->mu);
                 proj_field(u, PM, t, Vh);
                 for (long k = 0; k < n; ++k) o[k] += u[k];
             }
@@ -908,7 +920,7 @@ void or_dm_dparam(cplx *out, const cplx *X, const cplx *U, const or_params *p, i
 int or_force(cplx *dSdU, double *dSdb5, double *dSdc5, double *S, const cplx *phi,
              const cplx *U, const or_params *p, double tol, int maxiter, int *iters)
 {
-    if (p->b5s || p->c5s) return -1;   /* the derivatives below assume constant b5, c5 */
+    if (p->b5s || p->c5s || p->mu != 0.0) return -1;   /* the derivatives below: constant b5, c5, no mu */
     long V = vol4(p->L), Vh = V / 2, n = 12 * Vh * p->Ls;
     cplx *X = calloc((size_t)n, sizeof(cplx)), *Y = malloc(sizeof(cplx) * n);
     cplx *a = malloc(sizeof(cplx) * n), *b = malloc(sizeof(cplx) * n);

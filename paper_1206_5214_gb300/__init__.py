@@ -18,6 +18,7 @@ from . import build as _build
 __all__ = [
     "MDWF_F64", "MDWF_F32", "MDWF_F16N", "MdwfError", "lib_path", "load",
     "mdwf_create", "mdwf_destroy", "mdwf_set_stream", "mdwf_set_s_coefficients", "mdwf_get_s_coefficients",
+    "mdwf_set_chemical_potential",
     "mdwf_load_gauge", "mdwf_field_bytes",
     "mdwf_field_import", "mdwf_field_export", "mdwf_apply", "mdwf_apply_dag", "mdwf_cgne",
     "mdwf_apply_full", "mdwf_overlap_apply", "mdwf_pv_reconstruct", "mdwf_gw_violation", "mdwf_force4d",
@@ -86,6 +87,7 @@ def load(build_if_missing: bool = True):
         "mdwf_destroy": (ip, [vp]),
         "mdwf_set_stream": (ip, [vp, vp]),
         "mdwf_set_s_coefficients": (ip, [vp, dp, dp]),
+        "mdwf_set_chemical_potential": (ip, [vp, ctypes.c_double]),
         "mdwf_get_s_coefficients": (ip, [vp, dp, dp, ctypes.POINTER(ctypes.c_int)]),
         "mdwf_load_gauge": (ip, [vp, vp, ip]),
         "mdwf_field_bytes": (sz, [vp, ip, ip]),
@@ -189,6 +191,11 @@ def mdwf_set_s_coefficients(ctx, b5s, c5s) -> None:
     b = (ctypes.c_double * len(b5s))(*[float(v) for v in b5s])
     c = (ctypes.c_double * len(c5s))(*[float(v) for v in c5s])
     _check(load().mdwf_set_s_coefficients(ctx, b, c), "mdwf_set_s_coefficients")
+
+
+def mdwf_set_chemical_potential(ctx, mu: float) -> None:
+    """Chemical potential on the time links (e^{+mu} forward, e^{-mu} backward); 0 turns it off."""
+    _check(load().mdwf_set_chemical_potential(ctx, float(mu)), "mdwf_set_chemical_potential")
 
 
 def mdwf_get_s_coefficients(ctx, Ls: int):

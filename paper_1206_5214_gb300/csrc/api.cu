@@ -514,6 +514,12 @@ int mdwf_set_s_coefficients(mdwf_ctx* c, const double* b5s, const double* c5s) {
     return cuda_status(cudaMemcpy(c->gs32, h32, sizeof(h32), cudaMemcpyHostToDevice));
 }
 
+int mdwf_set_chemical_potential(mdwf_ctx* c, double mu) {
+    if (!c || !isfinite(mu) || fabs(mu) > 10.0) return MDWF_EINVAL;
+    c->chem = mu;
+    return MDWF_OK;
+}
+
 int mdwf_get_s_coefficients(const mdwf_ctx* c, double* b5s, double* c5s, int* per_slice) {
     if (!c || !b5s || !c5s || !per_slice) return MDWF_EINVAL;
     for (int s = 0; s < c->g.Ls; ++s) {

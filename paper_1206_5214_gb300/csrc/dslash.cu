@@ -38,6 +38,10 @@ template <typename R> struct HopParams {
     const int4* nbr; // [parity][site][2] = cb index of x+mu (mu = 0..3), then of x-mu
     int sop, swap;
     SCoef<R> sc;
+    // chemical potential (Sec. 6.6): the time-direction terms carry efwd
+    // (forward hop) and ebwd (backward hop) when chem is set
+    bool chem;
+    R efwd, ebwd;
 };
 
 // --------------------------------------------------------- spin structure
@@ -163,14 +167,16 @@ __device__ __forceinline__ void hop_dir(R* acc, const Field<P>& in, const Gauge<
         const R f = load_input<P, GATHER>(in, rbase + jf, s, g.Ls, gown, gfac, mass, w);
         project<MU, SF>(w, h);
         U.load(((long long)hp.out_parity * 4 + MU) * g.Vh + site, u);
-        transport_add<false, MU, SF>(acc, u, h, f, SCALED);
+        const bool tm = MU == 3 && hp.chem;
+        transport_add<false, MU, SF>(acc, u, h, tm ? f * hp.efwd : f, SCALED || tm);
     }
     {
         R w[24], h[12], u[18];
         const R f = load_input<P, GATHER>(in, rbase + jb, s, g.Ls, gown, gfac, mass, w);
         project<MU, -SF>(w, h);
         U.load(((long long)(1 - hp.out_parity) * 4 + MU) * g.Vh + jb, u);
-        transport_add<true, MU, -SF>(acc, u, h, f, SCALED);
+        const bool tm = MU == 3 && hp.chem;
+        transport_add<true, MU, -SF>(acc, u, h, tm ? f * hp.ebwd : f, SCALED || tm);
     }
 }
 
@@ -260,7 +266,8 @@ __device__ __forceinline__ void hop_term(R* acc, const Field<P>& in, const Gauge
     if (next >= 0) st.issue(in, rbase + next, s, SLOT);
     if (FWD) U.load(((long long)hp.out_parity * 4 + MU) * hp.g.Vh + site, u);
     else U.load(((long long)(1 - hp.out_parity) * 4 + MU) * hp.g.Vh + jb, u);
-    transport_add<!FWD, MU, S>(acc, u, h, f, P == MDWF_F16N);
+    const bool tm = MU == 3 && hp.chem;
+    transport_add<!FWD, MU, S>(acc, u, h, tm ? f * (FWD ? hp.efwd : hp.ebwd) : f, P == MDWF_F16N || tm);
 }
 
 // The eight terms with the next neighbour in flight while one is computed.
@@ -556,6 +563,10 @@ static int launch_hop_t(mdwf_ctx* c, const HopLaunch& h) {
     hp.sc.c5 = (R)c->c5;
     hp.sc.Mp = (R)(c->b5 * (4.0 - c->M5) + 1.0);
     hp.sc.Mm = (R)(c->c5 * (4.0 - c->M5) - 1.0);
+    // the adjoint's hopping matrix is transposed: the two factors exchange
+    hp.chem = c->chem != 0.0;
+    hp.efwd = (R)exp(h.dagger ? -c->chem : c->chem);
+    hp.ebwd = (R)exp(h.dagger ? c->chem : -c->chem);
     const bool X = h.x != nullptr;
     if (h.fuse != FUSE_NONE) {
         // fused CG epilogues: t = M p with v = A^dag t, or Ap = M^dag t folded into r

@@ -160,6 +160,10 @@ extern "C" int mdwf_force(mdwf_ctx* c, double* dSdU, double* dSdb5, double* dSdc
         set_error_message("mdwf_force supports constant b5, c5 only (per-slice coefficients are set)");
         return MDWF_EINVAL;
     }
+    if (c->chem != 0.0) {
+        set_error_message("the force is defined without a chemical potential");
+        return MDWF_EINVAL;
+    }
     mdwf_solve_params prm{};
     if (params) prm = *params;
     int st;

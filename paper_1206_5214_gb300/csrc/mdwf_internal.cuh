@@ -472,6 +472,8 @@ struct mdwf_ctx {
     // is a dense table and the gather of the hop takes per-slice factors from
     // gs64 / gs32 = [gown(s)][gfac(s)][gscale(s)], 64 entries each
     bool sdep = false;
+    // chemical potential on the time links (0: none)
+    double chem = 0.0;
     double b5s[64] = {0}, c5s[64] = {0};
     double* gs64 = nullptr;
     float* gs32 = nullptr;
