@@ -386,6 +386,33 @@ def main() -> None:
                         "kernels": {s["name"]: round(1e3 * s["ms"] / s["launches"], 2) for s in st}}
         del fi, fo
 
+    # ---------------- batching: M on 12 right-hand sides in one launch against 1 (FP32)
+    batched = None
+    if not args.no_extras:
+        per_rhs = {}
+        for nr in (1, 12):
+            nbytes = mdwf.mdwf_field_bytes(h, mdwf.MDWF_F32, nr)
+            fi = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            fo = torch.empty_like(fi)
+            mdwf.mdwf_field_import(h, fi, src_odd.unsqueeze(0).expand(nr, *src_odd.shape).contiguous(),
+                                   mdwf.MDWF_F32, nr)
+            for _ in range(3):
+                mdwf.mdwf_apply(h, fo, fi, mdwf.MDWF_F32, nr)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 10
+            flush.zero_()
+            e0.record()
+            for _ in range(reps):
+                mdwf.mdwf_apply(h, fo, fi, mdwf.MDWF_F32, nr)
+            e1.record()
+            torch.cuda.synchronize()
+            per_rhs[nr] = e0.elapsed_time(e1) / reps / nr
+            del fi, fo
+        batched = {"prec": "f32", "nrhs": 12, "ms_per_M_per_rhs": per_rhs[12], "ms_per_M_nrhs1": per_rhs[1],
+                   "GFLOPs": FLOPS_PER_SITE * n5 / (per_rhs[12] * 1e-3) / 1e9,
+                   "speedup_per_rhs": per_rhs[1] / per_rhs[12]}
+
     # ---------------- time to solution: mixed (both inner precisions) and plain FP64
     cg = {"mixed_" + args.inner: {"ms": ms / args.steps, "iters": infos[-1].iters,
                                   "reliable_updates": infos[-1].reliable_updates,
@@ -417,7 +444,7 @@ def main() -> None:
             "gpu_launches": launches1 - launches0,
             "applies_per_step": applies / args.steps,
             "roofline": roofline, "clocks": clocks.summary(), "e2e": e2e, "cpu_baseline": cpu,
-            "cgne": cg, "dslash": dslash, "kernels": kernels,
+            "cgne": cg, "dslash": dslash, "batched_apply": batched, "kernels": kernels,
             "profiled_solve": {"iters": prof_info.iters, "true_res": prof_info.true_res}}
     print(json.dumps(line), flush=True)
     if dist:
