@@ -197,6 +197,8 @@ typedef struct {
     double delta;         /* reliable-update threshold on |r| / max |r|; 0 = 0.005 (FP32 inner), 0.1 (FP16N) */
     int check_every;      /* iterations between host convergence polls; 0 = 8 */
     int use_graph;        /* 1: replay the CG iteration as a captured CUDA graph */
+    int guess;            /* 1: x holds an initial guess on entry and the CG starts from its odd
+                             part (a restart or warm start); 0: the CG starts from zero */
 } mdwf_solve_params;
 
 typedef struct {

@@ -50,7 +50,8 @@ class _Opts(ctypes.Structure):
 
 class SolveParams(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("inner_prec", ctypes.c_int),
-                ("delta", ctypes.c_double), ("check_every", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("delta", ctypes.c_double), ("check_every", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("guess", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -246,13 +247,15 @@ def mdwf_apply_dag(ctx, out, inp, prec: int, nrhs: int = 1, mf_per_rhs=None) -> 
 
 def mdwf_cgne(ctx, x, b, nrhs: int = 1, mf_per_rhs=None, tol: float = 1e-10, maxiter: int = 20000,
               inner_prec: int = MDWF_F64, delta: float = 0.0, check_every: int = 8, use_graph: bool = True,
-              raise_on_error: bool = True):
-    """Solve D_DW(m) x = b (full 5d fields, complex128, user order). Returns (status, [SolveInfo per rhs])."""
+              raise_on_error: bool = True, guess: bool = False):
+    """Solve D_DW(m) x = b (full 5d fields, complex128, user order). Returns (status, [SolveInfo per rhs]).
+    guess=True starts the CG from the odd part of the x passed in."""
     px, wx = _ptr_where(x)
     pb, wb = _ptr_where(b)
     if wx != wb:
         raise ValueError("x and b must both be host or both be device buffers")
-    prm = SolveParams(float(tol), int(maxiter), int(inner_prec), float(delta), int(check_every), int(bool(use_graph)))
+    prm = SolveParams(float(tol), int(maxiter), int(inner_prec), float(delta), int(check_every), int(bool(use_graph)),
+                      int(bool(guess)))
     infos = (SolveInfo * int(nrhs))()
     st = load().mdwf_cgne(ctx, px, pb, int(nrhs), _masses(mf_per_rhs), wb, ctypes.byref(prm), infos)
     if raise_on_error and st not in (0,):

@@ -537,6 +537,7 @@ int mdwf_set_stream(mdwf_ctx* c, void* stream) {
 }
 
 int mdwf_load_gauge(mdwf_ctx* c, const double* U, int where) {
+    NvtxRange nvtx_range("mdwf_load_gauge");
     if (!c || !U || (where != MDWF_HOST && where != MDWF_DEVICE)) return MDWF_EINVAL;
     int st;
     if ((st = cuda_status(cudaSetDevice(c->device)))) return st;
@@ -609,6 +610,7 @@ int mdwf_field_export(mdwf_ctx* c, double* dst, const void* src, int prec, int n
 }
 
 static int apply_entry(mdwf_ctx* c, void* out, const void* in, int prec, int nrhs, const double* mf, int dagger) {
+    NvtxRange nvtx_range("mdwf_apply");
     if (!c || !out || !in || !valid_prec(prec) || nrhs < 1 || nrhs > 64 || out == in) return MDWF_EINVAL;
     if (!c->have_gauge) return MDWF_ENOGAUGE;
     int st;
@@ -661,6 +663,7 @@ int mdwf_profile_read(mdwf_ctx* c, mdwf_kernel_stat* out, int max, int* n_out, i
 }
 
 int mdwf_autotune(mdwf_ctx* c, int prec, int nrhs, int* sites_per_block) {
+    NvtxRange nvtx_range("mdwf_autotune");
     if (!c || !valid_prec(prec) || nrhs < 1 || nrhs > 64) return MDWF_EINVAL;
     if (!c->have_gauge) return MDWF_ENOGAUGE;
     int st;

@@ -528,17 +528,30 @@ static int run_mixed(Solver& S, Fields& F, const mdwf_solve_params& prm, double 
     mdwf_ctx* c = S.c;
     const int nrhs = S.nrhs;
     int st;
-    // r = src (x = 0), r_s = r, x_s = 0, p = r_s
-    if ((st = S.copy<MDWF_F64, MDWF_F64>(F.r, F.src, false))) return st;
-    if ((st = S.copy<MDWF_F32, MDWF_F64>(F.rs, F.src, false))) return st;
+    // r = src - M^dag M x (x = 0: r = src), r_s = r, x_s = 0, p = r_s
     if ((st = cuda_status(cudaMemsetAsync(F.xs, 0, field_bytes(MDWF_F32, S.g, nrhs), c->stream)))) return st;
-    if ((st = S.copy<PP, MDWF_F64>(F.p, F.src, false))) return st;
+    if (prm.guess) {
+        if ((st = true_residual<MDWF_F32, true>(S, F.r, F.rs, F.src, F.xo, F.t64, true))) return st;
+        if ((st = S.pull())) return st;
+        for (int r = 0; r < nrhs; ++r) {
+            if (S.hsc[S_ACTIVE * kMaxRhs + r] == 0.0) continue;
+            const double rr = S.hsc[S_AUX * kMaxRhs + r];
+            S.hsc[S_RR * kMaxRhs + r] = rr;
+            if (rr <= tol * tol * S.hsc[S_SRC2 * kMaxRhs + r]) S.hsc[S_ACTIVE * kMaxRhs + r] = 0.0;
+        }
+        if ((st = S.push())) return st;
+        if ((st = S.copy<PP, MDWF_F64>(F.p, F.r, false))) return st;
+    } else {
+        if ((st = S.copy<MDWF_F64, MDWF_F64>(F.r, F.src, false))) return st;
+        if ((st = S.copy<MDWF_F32, MDWF_F64>(F.rs, F.src, false))) return st;
+        if ((st = S.copy<PP, MDWF_F64>(F.p, F.src, false))) return st;
+        if ((st = S.norm<MDWF_F64>(F.src, false, S_RR))) return st;
+    }
     if ((st = init_w<PP>(S, F.w, F.p))) return st;
-    if ((st = S.norm<MDWF_F64>(F.src, false, S_RR))) return st;
     if ((st = S.pull())) return st;
     for (int r = 0; r < nrhs; ++r) {
         maxr[r] = sqrt(S.hsc[S_RR * kMaxRhs + r]);
-        last_true[r] = S.hsc[S_RR * kMaxRhs + r];  // x = 0: r = src
+        last_true[r] = S.hsc[S_RR * kMaxRhs + r];
     }
     // FP32 carries ~7 digits, so it can reduce the residual 100x between FP64
     // updates; FP16 storage only ~3, so it updates after every 10x
@@ -586,6 +599,7 @@ static int run_mixed(Solver& S, Fields& F, const mdwf_solve_params& prm, double 
         if (!any_active) break;
         if (!need_update) continue;
         // reliable update: x += x_s, x_s = 0, r = src - M^dag M x (FP64), r_s = r
+        NvtxRange nvtx_update("reliable update");
         {
             LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, S.n5() * (2.0 * 192.0 + 2.0 * 96.0), S.n5() * 24.0);
             k_accum_zero<MDWF_F64, MDWF_F32><<<S.grid(), kRedThreads, 0, c->stream>>>(
@@ -814,11 +828,18 @@ int solve_normal(mdwf_ctx* c, int nrhs, void* xo, const void* src, const mdwf_so
         for (int r = 0; r < nrhs; ++r) hsc[S_ACTIVE * kMaxRhs + r] = 1.0;
         if ((st = S.push())) { ret = st; break; }
         if ((st = S.norm<MDWF_F64>(F.src, false, S_SRC2))) { ret = st; break; }
-        if ((st = cuda_status(cudaMemsetAsync(F.xo, 0, f64, c->stream)))) { ret = st; break; }
+        if (!prm.guess && (st = cuda_status(cudaMemsetAsync(F.xo, 0, f64, c->stream)))) { ret = st; break; }
         // zero right-hand sides are solved by x = 0
         if ((st = S.pull())) { ret = st; break; }
         for (int r = 0; r < nrhs; ++r)
-            if (S.hsc[S_SRC2 * kMaxRhs + r] == 0.0) S.hsc[S_ACTIVE * kMaxRhs + r] = 0.0;
+            if (S.hsc[S_SRC2 * kMaxRhs + r] == 0.0) {
+                S.hsc[S_ACTIVE * kMaxRhs + r] = 0.0;
+                if (prm.guess) {  // whatever the guess, the solution is zero
+                    const size_t f1 = field_bytes(MDWF_F64, g, 1);
+                    if ((st = cuda_status(cudaMemsetAsync((char*)F.xo + r * f1, 0, f1, c->stream)))) break;
+                }
+            }
+        if (st) { ret = st; break; }
         if ((st = S.push())) { ret = st; break; }
 
         std::vector<double> last_true(nrhs, 0.0);
@@ -895,6 +916,7 @@ int prepare_rhs(mdwf_ctx* c, const RhsScratch& w, const double* b, int where, in
 
 extern "C" int mdwf_cgne(mdwf_ctx* c, double* x, const double* b, int nrhs, const double* mf_per_rhs, int where,
                          const mdwf_solve_params* params, mdwf_solve_info* info) {
+    NvtxRange nvtx_range("mdwf_cgne");
     auto t0 = std::chrono::steady_clock::now();
     if (!c || !x || !b || nrhs < 1 || nrhs > kMaxRhs || (where != MDWF_HOST && where != MDWF_DEVICE))
         return MDWF_EINVAL;
@@ -952,6 +974,17 @@ extern "C" int mdwf_cgne(mdwf_ctx* c, double* x, const double* b, int nrhs, cons
         if ((st = prepare_rhs(c, sw, b, where, r))) return st;
         if ((st = apply_op(c, (char*)src + (size_t)r * f1, sw.bp, MDWF_F64, 1, 1, r))) return st;
     }
+    // an initial guess: the odd part of x
+    if (prm.guess)
+        for (int r = 0; r < nrhs; ++r) {
+            const double* x_r = x + (size_t)r * full1 / sizeof(double);
+            if (where == MDWF_HOST) {
+                if ((st = cuda_status(cudaMemcpyAsync(sw.stage, x_r, full1, cudaMemcpyHostToDevice, c->stream))))
+                    return st;
+                x_r = (const double*)sw.stage;
+            }
+            if ((st = launch_split_full(c, sw.xe, (char*)xo + (size_t)r * f1, x_r, MDWF_F64, 1))) return st;
+        }
 
     NormalResult res;
     if ((st = solve_normal(c, nrhs, xo, src, prm, res))) return st;

@@ -154,6 +154,7 @@ using namespace mdwf;
 
 extern "C" int mdwf_force(mdwf_ctx* c, double* dSdU, double* dSdb5, double* dSdc5, double* S_out,
                           const double* phi, int where, const mdwf_solve_params* params, mdwf_solve_info* info) {
+    NvtxRange nvtx_range("mdwf_force");
     if (!c || !phi || (where != MDWF_HOST && where != MDWF_DEVICE)) return MDWF_EINVAL;
     if (!c->have_gauge) return MDWF_ENOGAUGE;
     if (c->sdep) {
@@ -166,6 +167,7 @@ extern "C" int mdwf_force(mdwf_ctx* c, double* dSdU, double* dSdb5, double* dSdc
     }
     mdwf_solve_params prm{};
     if (params) prm = *params;
+    prm.guess = 0;  // the solves here start from zero
     int st;
     if ((st = cuda_status(cudaSetDevice(c->device)))) return st;
     if ((st = ensure_tables(c, 1, nullptr))) return st;

@@ -61,6 +61,7 @@ using namespace mdwf;
 
 extern "C" int mdwf_force4d(mdwf_ctx* c, double* dSdU, double* S_out, const double* phi, int where,
                             const mdwf_solve_params* params, mdwf_solve_info* info) {
+    NvtxRange nvtx_range("mdwf_force4d");
     if (!c || !phi || !S_out || (where != MDWF_HOST && where != MDWF_DEVICE)) return MDWF_EINVAL;
     if (!c->have_gauge) return MDWF_ENOGAUGE;
     if (c->mf == 1.0) return MDWF_EINVAL;
@@ -70,6 +71,7 @@ extern "C" int mdwf_force4d(mdwf_ctx* c, double* dSdU, double* S_out, const doub
     }
     mdwf_solve_params prm{};
     if (params) prm = *params;
+    prm.guess = 0;  // the solves here start from zero
     int st;
     if ((st = cuda_status(cudaSetDevice(c->device)))) return st;
     const Geom& g = c->g;

@@ -23,6 +23,8 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mdwf.h"
 
 // Blocks per SM the hop kernels are compiled for (register budget per thread:
@@ -35,6 +37,15 @@
 #endif
 
 namespace mdwf {
+
+// An NVTX range around one library call, so that timeline profilers show the
+// entry points (header-only NVTX: no cost without an attached tool).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 constexpr int kMaxLs = 32;
 constexpr int kMaxRhs = 64;  // right-hand sides per call

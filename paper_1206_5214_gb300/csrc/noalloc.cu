@@ -63,6 +63,7 @@ using namespace mdwf;
 
 extern "C" int mdwf_apply_noalloc(mdwf_ctx* c, void* out, const void* in, int prec, int nrhs,
                                   const double* mf_per_rhs, int dagger) {
+    NvtxRange nvtx_range("mdwf_apply_noalloc");
     if (!c || !out || !in || out == in || nrhs < 1 || nrhs > 64) return MDWF_EINVAL;
     if (prec != MDWF_F64 && prec != MDWF_F32 && prec != MDWF_F16N) return MDWF_EINVAL;
     if (!c->have_gauge) return MDWF_ENOGAUGE;

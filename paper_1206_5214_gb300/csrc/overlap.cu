@@ -147,8 +147,11 @@ static int pv_stage(mdwf_ctx* c, const double* psi4_dev, int nrhs, const double*
     if ((st = ensure_tables(c, nrhs, mf_per_rhs))) return st;
     if ((st = apply_full_dev(c, y, a, nrhs, 0))) return st;  // y = D(m) P psi~
     std::vector<double> ones(nrhs, 1.0);
+    mdwf_solve_params pv{};
+    if (prm) pv = *prm;
+    pv.guess = 0;  // a holds P psi~, not a guess
     // x = D(1)^-1 y (the Pauli-Villars solve), into a
-    st = mdwf_cgne(c, a, y, nrhs, ones.data(), MDWF_DEVICE, prm, info);
+    st = mdwf_cgne(c, a, y, nrhs, ones.data(), MDWF_DEVICE, &pv, info);
     *x_out = a;  // also after MDWF_ENOCONV: the last iterate is in a
     return st;
 }
@@ -159,6 +162,7 @@ using namespace mdwf;
 
 extern "C" int mdwf_apply_full(mdwf_ctx* c, double* out, const double* in, int nrhs, const double* mf_per_rhs,
                                int where, int dagger) {
+    NvtxRange nvtx_range("mdwf_apply_full");
     if (!c || !out || !in || out == in || nrhs < 1 || nrhs > kMaxRhs || (where != MDWF_HOST && where != MDWF_DEVICE) ||
         (dagger != 0 && dagger != 1))
         return MDWF_EINVAL;
@@ -181,6 +185,7 @@ extern "C" int mdwf_apply_full(mdwf_ctx* c, double* out, const double* in, int n
 // Shared driver of the two Pauli-Villars constructions.
 static int pv_entry(mdwf_ctx* c, double* out, const double* psi4, int nrhs, const double* mf_per_rhs, int where,
                     const mdwf_solve_params* params, mdwf_solve_info* info, int mode) {
+    NvtxRange nvtx_range("mdwf_pv");
     if (!c || !out || !psi4 || nrhs < 1 || nrhs > kMaxRhs || (where != MDWF_HOST && where != MDWF_DEVICE))
         return MDWF_EINVAL;
     if (!c->have_gauge) return MDWF_ENOGAUGE;
@@ -234,6 +239,7 @@ extern "C" int mdwf_pv_reconstruct(mdwf_ctx* c, double* Psi5, const double* psi4
 // applications of D_ov(m) (m != 1 for every right-hand side).
 extern "C" int mdwf_gw_violation(mdwf_ctx* c, double* out4, const double* psi4, int nrhs, const double* mf_per_rhs,
                                  int where, const mdwf_solve_params* params, mdwf_solve_info* info) {
+    NvtxRange nvtx_range("mdwf_gw_violation");
     if (!c || !out4 || !psi4 || out4 == psi4 || nrhs < 1 || nrhs > kMaxRhs ||
         (where != MDWF_HOST && where != MDWF_DEVICE))
         return MDWF_EINVAL;

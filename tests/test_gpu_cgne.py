@@ -146,3 +146,59 @@ def test_cgne_full_16x16x16x32(inner):
     assert st == 0, info[0].as_dict()
     assert info[0].true_res <= 1e-10
     assert oracle_residual(x[0] if x.ndim == 8 else x, b, U, p) <= 1.05e-10
+
+
+@pytest.mark.parametrize("inner", [F64, F32], ids=["f64", "mixed-f32"])
+def test_cgne_warm_start(inner):
+    """guess=True starts the CG from the odd part of the x passed in (restart /
+    resume): the converged solution needs no iteration, a perturbed one fewer
+    than a cold start, and both still solve the system (oracle residual)."""
+    dims, Ls = (4, 4, 4, 4), 8
+    U = sy.gauge_field(dims, 0.3, 1091)
+    b = sy.gaussian_field(dims, Ls, 2091)
+    p = oracle.Params(dims, Ls, 1.8, 1.5, 0.5, 0.01)
+    h = mdwf.mdwf_create(dims, Ls, 1.8, 1.5, 0.5, 0.01)
+    try:
+        mdwf.mdwf_load_gauge(h, torch.from_numpy(U).cuda())
+        bb = torch.from_numpy(b).cuda()
+        x = torch.zeros_like(bb)
+        st, cold = mdwf.mdwf_cgne(h, x, bb, tol=1e-10, inner_prec=inner)
+        assert st == 0
+        st, again = mdwf.mdwf_cgne(h, x, bb, tol=1e-10, inner_prec=inner, guess=True)
+        assert st == 0 and again[0].iters == 0
+        rng = np.random.default_rng(4)
+        noise = torch.from_numpy(rng.standard_normal(b.shape) + 0j).cuda()
+        x2 = x + 1e-4 * noise * torch.linalg.vector_norm(x) / torch.linalg.vector_norm(noise)
+        st, warm = mdwf.mdwf_cgne(h, x2, bb, tol=1e-10, inner_prec=inner, guess=True)
+        assert st == 0 and 0 < warm[0].iters < cold[0].iters
+        # a zero source gives x = 0 whatever the guess
+        z = torch.zeros_like(bb)
+        xz = x.clone()
+        st, _ = mdwf.mdwf_cgne(h, xz, z, tol=1e-10, inner_prec=inner, guess=True)
+        assert st == 0 and int(torch.count_nonzero(xz)) == 0
+        xs = x2.cpu().numpy()
+    finally:
+        mdwf.mdwf_destroy(h)
+    assert oracle_residual(xs, b, U, p) <= 1.05e-10
+
+
+@pytest.mark.parametrize("inner", [F64, F32], ids=["f64", "mixed-f32"])
+def test_cgne_nan_source_is_reported_per_rhs(inner):
+    """Failure detection on the host side of a solve: a NaN planted in one source
+    of a batch ends that right-hand side with MDWF_EBREAKDOWN while the other
+    converges; the call returns normally."""
+    dims, Ls = (4, 4, 2, 4), 6
+    U = sy.gauge_field(dims, 0.3, 1093)
+    b = sy.gaussian_field(dims, Ls, 2093, nrhs=2)
+    b[1, 2, 0, 1, 0, 1, 3, 2] = np.nan
+    h = mdwf.mdwf_create(dims, Ls, 1.8, 1.5, 0.5, 0.02)
+    try:
+        mdwf.mdwf_load_gauge(h, torch.from_numpy(U).cuda())
+        bb = torch.from_numpy(b).cuda()
+        x = torch.zeros_like(bb)
+        st, info = mdwf.mdwf_cgne(h, x, bb, nrhs=2, tol=1e-10, inner_prec=inner, raise_on_error=False)
+    finally:
+        mdwf.mdwf_destroy(h)
+    assert st == 5
+    assert info[0].status == 0 and info[0].true_res <= 1e-10
+    assert info[1].status == 5

@@ -116,6 +116,6 @@ def test_autograd_backward_matches_force():
     S.backward()
     p = oracle.Params(dims, Ls, 1.8, 1.5, 0.5, 0.05)
     S0, G0, db0, dc0, _, _ = oracle.force(phi_np, U.detach().cpu().numpy(), p, tol=1e-14)
-    assert float(S) == pytest.approx(S0, rel=1e-10)
+    assert float(S.detach()) == pytest.approx(S0, rel=1e-10)
     assert np.abs(U.grad.cpu().numpy() - G0).max() <= 1e-8 * np.abs(G0).max()
     assert b5c5.grad.cpu().numpy() == pytest.approx([db0, dc0], rel=1e-8)
