@@ -231,3 +231,13 @@ def test_staged_loads_match_plain(prec, dims, Ls):
             check(b, ref, prec)
         with pytest.raises(mdwf.MdwfError):
             mdwf.mdwf_set_staging(c.h, F64, True)
+
+
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_apply_parity_Ls32(prec):
+    """The largest Ls (32): one s-column fills a warp; M and M^dag against the oracle."""
+    dims, Ls = (4, 4, 2, 2), 32
+    U, odd, p = setup(dims, Ls, 1.5, 0.5, 0.01, 0.3, 9)
+    with Ctx(dims, Ls, 1.8, 1.5, 0.5, 0.01, U) as c:
+        for d in (False, True):
+            check(c.apply(odd, prec, d)[0], oracle.m(odd, U, p, dagger=d), prec)
