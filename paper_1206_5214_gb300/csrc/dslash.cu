@@ -16,6 +16,8 @@
 // from HBM once per hop and reused across all Ls slices. Spinor chunks of
 // consecutive s are contiguous, so every vector load of a warp is coalesced.
 // The s-mixing matrix is applied after the hop through shared memory.
+#include <atomic>
+
 #include "mdwf_internal.cuh"
 
 namespace mdwf {
@@ -490,12 +492,14 @@ static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<t
     }
     if (ST) {
         // the staging buffers need shared memory for every resident block (once per device)
-        static unsigned long long carved = 0;
-        if (c->device < 64 && !(carved >> c->device & 1ull)) {
+        // (contexts on other host threads may launch at the same time: the mask is atomic, and
+        // setting the attribute twice is harmless)
+        static std::atomic<unsigned long long> carved{0};
+        if (c->device < 64 && !(carved.load() >> c->device & 1ull)) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                                  (int)cudaSharedmemCarveoutMaxShared);
             if (e != cudaSuccess) return cuda_status(e);
-            carved |= 1ull << c->device;
+            carved.fetch_or(1ull << c->device);
         }
     }
     Field<P> out = make_field<P>(h.out, g, h.nrhs);
