@@ -55,7 +55,8 @@ __global__ void __launch_bounds__(256) m5_kernel(Field<P> out, Field<P> in, Fiel
             for (int k = 12; k < 24; ++k) res[k] += mm * h[k];
         }
     } else {
-        block_columns(cs, blockDim.y, Ls, sop, swap != 0, sc, mass[rhs], tid, nthr);
+        // the shared-memory walk: register-held columns measured slower in this 256-thread kernel
+        block_columns(cs, blockDim.y, Ls, sop, swap != 0, sc, mass[rhs], tid, nthr, false);
         __syncthreads();
         if (!active) return;
         row_load(mine, res);

@@ -362,6 +362,75 @@ __device__ __forceinline__ void column_op(R* base, int stride, int Ls, int op, b
     }
 }
 
+// column_op with the column held in registers (Ls known at compile time): all
+// Ls elements are loaded at once, the recursion runs on registers, and all are
+// stored back; the arithmetic is that of column_op.
+template <int LS, typename R>
+__device__ __forceinline__ void column_op_reg(R* base, int stride, int op, bool up, const SCoef<R>& sc, R m) {
+    typedef typename CPair<R>::T C;
+    C v[LS];
+#pragma unroll
+    for (int s = 0; s < LS; ++s) v[s] = *reinterpret_cast<const C*>(base + (up ? s : LS - 1 - s) * stride);
+    if (op == SOP_A || op == SOP_K) {
+        const R r = sc.Mm / sc.Mp, kappa = m * r, inv = R(1) / sc.Mp;
+        R ar = v[LS - 1].x, ai = v[LS - 1].y, pw = kappa;
+#pragma unroll
+        for (int s = 0; s < LS - 1; ++s) {
+            ar += pw * v[s].x;
+            ai += pw * v[s].y;
+            pw *= -r;
+        }
+        const R den = sc.Mp * (R(1) - pw);
+        R pr = ar / den, pi = ai / den;  // Psi_{Ls-1}
+        const R lr = pr, li = pi;
+        if (op == SOP_A) {
+            v[LS - 1].x = pr; v[LS - 1].y = pi;
+#pragma unroll
+            for (int s = LS - 2; s >= 0; --s) {
+                pr = v[s].x * inv - r * pr;
+                pi = v[s].y * inv - r * pi;
+                v[s].x = pr; v[s].y = pi;
+            }
+        } else {
+#pragma unroll
+            for (int s = LS - 2; s >= 0; --s) {
+                const R nr = v[s].x * inv - r * pr, ni = v[s].y * inv - r * pi;  // Psi_s
+                v[s].x = sc.b5 * nr + sc.c5 * pr;                               // (M_phi Psi)_s
+                v[s].y = sc.b5 * ni + sc.c5 * pi;
+                pr = nr;
+                pi = ni;
+            }
+            v[LS - 1].x = sc.b5 * lr - m * sc.c5 * pr;
+            v[LS - 1].y = sc.b5 * li - m * sc.c5 * pi;
+        }
+    } else if (op == SOP_MPHI || op == SOP_C || op == SOP_MEE) {
+        const R w0 = op == SOP_MPHI ? sc.b5 : op == SOP_MEE ? sc.Mp : R(0);
+        const R w1 = op == SOP_MPHI ? sc.c5 : op == SOP_MEE ? sc.Mm : R(1);
+        const C f0 = v[0];
+#pragma unroll
+        for (int s = 0; s < LS - 1; ++s) {
+            v[s].x = w0 * v[s].x + w1 * v[s + 1].x;
+            v[s].y = w0 * v[s].y + w1 * v[s + 1].y;
+        }
+        v[LS - 1].x = w0 * v[LS - 1].x - m * w1 * f0.x;
+        v[LS - 1].y = w0 * v[LS - 1].y - m * w1 * f0.y;
+    } else {
+        return;
+    }
+#pragma unroll
+    for (int s = 0; s < LS; ++s) *reinterpret_cast<C*>(base + (up ? s : LS - 1 - s) * stride) = v[s];
+}
+
+template <typename R>
+__device__ __forceinline__ void column_op_any(R* base, int stride, int Ls, int op, bool up, const SCoef<R>& sc, R m) {
+    switch (Ls) {
+        case 8: column_op_reg<8>(base, stride, op, up, sc, m); return;
+        case 12: column_op_reg<12>(base, stride, op, up, sc, m); return;
+        case 16: column_op_reg<16>(base, stride, op, up, sc, m); return;
+        default: column_op(base, stride, Ls, op, up, sc, m); return;
+    }
+}
+
 // 24 reals of one (site, s) row in shared memory, as 16-byte vector accesses.
 __device__ __forceinline__ void row_store(float* row, const float* v) {
 #pragma unroll
@@ -406,7 +475,7 @@ __host__ __device__ inline int site_stride(int Ls) {
 // Dense tables are applied by the caller instead.
 template <typename R>
 __device__ __forceinline__ void block_columns(R* hs, int SB, int Ls, int op, bool swap, const SCoef<R>& sc,
-                                              R m, int tid, int nthr) {
+                                              R m, int tid, int nthr, bool in_registers = true) {
     const int ss = site_stride(Ls);
     const int per = SB * 6, half = (per + 31) / 32 * 32;
     for (int t = tid; t < 2 * half; t += nthr) {
@@ -414,7 +483,8 @@ __device__ __forceinline__ void block_columns(R* hs, int SB, int Ls, int op, boo
         if (r >= per) continue;
         const int ly = r / 6, j = chir * 6 + (r - 6 * (r / 6));
         const bool up = (chir == 1) != swap;  // P- uses N' unless the adjoint swaps
-        column_op(hs + (size_t)ly * ss + 2 * j, kRowStride, Ls, op, up, sc, m);
+        if (in_registers) column_op_any(hs + (size_t)ly * ss + 2 * j, kRowStride, Ls, op, up, sc, m);
+        else column_op(hs + (size_t)ly * ss + 2 * j, kRowStride, Ls, op, up, sc, m);
     }
 }
 
