@@ -72,11 +72,25 @@ __global__ void __launch_bounds__(kRedThreads) k_norm(Field<PA> a, double* part,
 
 enum { FIN_STORE = 0, FIN_ALPHA = 1, FIN_BETA = 2 };
 
-__global__ void k_finalize(const double* part, int nb, double* sc, int mode, int slot) {
+// One block of kFinThreads per right-hand side sums the nb partials in a
+// fixed order (four independent running sums per thread, so that the loads
+// of a thread are in flight together), then updates the CG scalars.
+constexpr int kFinThreads = 1024;
+
+__global__ void __launch_bounds__(kFinThreads) k_finalize(const double* part, int nb, double* sc, int mode, int slot) {
     const int rhs = blockIdx.x;
-    double v = 0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) v += part[rhs * nb + i];
-    v = block_sum(v);
+    const double* pp = part + (size_t)rhs * nb;
+    const int bd = blockDim.x;
+    double v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+    int i = threadIdx.x;
+    for (; i + 3 * bd < nb; i += 4 * bd) {
+        v0 += pp[i];
+        v1 += pp[i + bd];
+        v2 += pp[i + 2 * bd];
+        v3 += pp[i + 3 * bd];
+    }
+    for (; i < nb; i += bd) v0 += pp[i];
+    double v = block_sum((v0 + v1) + (v2 + v3));
     if (threadIdx.x != 0) return;
     const bool active = SC(S_ACTIVE, rhs) != 0.0;
     if (mode == FIN_STORE) {
@@ -348,12 +362,12 @@ struct Solver {
     double n5() const { return (double)g.Vh * g.Ls * nrhs; }
     int fin(int mode, int slot = 0) {
         LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, 8.0 * nrhs * nb, 0.0);
-        k_finalize<<<nrhs, kRedThreads, 0, c->stream>>>(part, nb, sc, mode, slot);
+        k_finalize<<<nrhs, kFinThreads, 0, c->stream>>>(part, nb, sc, mode, slot);
         return check_launch();
     }
     int fin_hop(int mode) {
         LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, 8.0 * nrhs * hb, 0.0);
-        k_finalize<<<nrhs, kRedThreads, 0, c->stream>>>(hpart, hb, sc, mode, 0);
+        k_finalize<<<nrhs, kFinThreads, 0, c->stream>>>(hpart, hb, sc, mode, 0);
         return check_launch();
     }
     template <int P>
