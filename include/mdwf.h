@@ -346,14 +346,35 @@ int mdwf_get_tuning(const mdwf_ctx *ctx, int prec, int nrhs, int *sites_per_bloc
 
 /*
  * Load strategy of the FP32 and FP16+norm hopping kernels (no counterpart in
- * the paper; a GPU implementation choice): staged = 1 copies every neighbour
- * spinor into shared memory with asynchronous copies one neighbour ahead of
- * its use; 0 loads it into registers when needed. Results are identical up to
- * nothing (the same arithmetic in the same order). prec MDWF_F64 accepts 0
- * only. mdwf_get_staging reads the setting.
+ * the paper; a GPU implementation choice). staged = 0 (default) loads every
+ * neighbour spinor into registers when it is needed; 1 copies it into shared
+ * memory with per-thread asynchronous copies one neighbour ahead of its use;
+ * 2 has the copy engine (bulk copies, TMA) move whole neighbour s-columns of
+ * the block's sites into shared memory, two hopping terms ahead, behind
+ * mbarriers. Results are identical (the same arithmetic in the same order).
+ * prec MDWF_F64 accepts 0 only; staged = 2 with MDWF_F16N needs Ls % 4 == 0
+ * (MDWF_EINVAL otherwise). The waits of mode 2 are bounded: one that gives up
+ * marks the context, and the next mdwf_cgne or mdwf_device_status returns
+ * MDWF_ETIMEOUT. mdwf_get_staging reads the setting.
  */
 int mdwf_set_staging(mdwf_ctx *ctx, int prec, int staged);
 int mdwf_get_staging(const mdwf_ctx *ctx, int prec, int *staged);
+
+/*
+ * Waits for the work enqueued on the context's stream and reports whether a
+ * bounded device-side wait gave up since the last report: MDWF_ETIMEOUT if
+ * one did (the mark is cleared), MDWF_ECUDA on a CUDA error, else MDWF_OK.
+ */
+int mdwf_device_status(mdwf_ctx *ctx);
+
+/*
+ * Self-test of the bounded device-side wait: one thread waits on an mbarrier
+ * that expects two arrivals, of which `arrivals` (0, 1 or 2) are made. With
+ * fewer than two the wait gives up after its limit (well under a second)
+ * and the call returns MDWF_ETIMEOUT; with two it returns MDWF_OK. The
+ * context stays usable either way.
+ */
+int mdwf_selftest_wait(mdwf_ctx *ctx, int arrivals);
 
 /* Human-readable name of a status code (static string). */
 const char *mdwf_strerror(int status);

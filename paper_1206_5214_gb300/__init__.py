@@ -23,12 +23,14 @@ __all__ = [
     "mdwf_field_import", "mdwf_field_export", "mdwf_apply", "mdwf_apply_dag", "mdwf_cgne",
     "mdwf_apply_full", "mdwf_overlap_apply", "mdwf_pv_reconstruct", "mdwf_gw_violation", "mdwf_force4d",
     "mdwf_strerror", "mdwf_force", "mdwf_apply_noalloc", "mdwf_autotune", "mdwf_set_tuning",
-    "mdwf_get_tuning", "mdwf_set_staging", "mdwf_get_staging", "mdwf_profile_enable", "mdwf_profile_read", "mdwf_counters", "SolveParams",
-    "SolveInfo", "KernelStat",
+    "mdwf_get_tuning", "mdwf_set_staging", "mdwf_get_staging", "mdwf_device_status", "mdwf_selftest_wait",
+    "mdwf_profile_enable", "mdwf_profile_read", "mdwf_counters", "SolveParams", "SolveInfo", "KernelStat",
+    "MDWF_OK", "MDWF_ETIMEOUT", "STAGE_REGISTERS", "STAGE_CP_ASYNC", "STAGE_BULK",
 ]
 
 MDWF_F64, MDWF_F32, MDWF_F16N = 0, 1, 2
 MDWF_HOST, MDWF_DEVICE = 0, 1
+MDWF_OK, MDWF_ETIMEOUT = 0, 6
 _lib = None
 
 
@@ -112,6 +114,8 @@ def load(build_if_missing: bool = True):
         "mdwf_get_tuning": (ip, [vp, ip, ip, ctypes.POINTER(ctypes.c_int)]),
         "mdwf_set_staging": (ip, [vp, ip, ip]),
         "mdwf_get_staging": (ip, [vp, ip, ctypes.POINTER(ctypes.c_int)]),
+        "mdwf_device_status": (ip, [vp]),
+        "mdwf_selftest_wait": (ip, [vp, ip]),
         "mdwf_strerror": (ctypes.c_char_p, [ip]),
         "mdwf_last_error": (ctypes.c_char_p, []),
     }
@@ -369,15 +373,36 @@ def mdwf_profile_read(ctx, reset: bool = False) -> list[dict]:
              "bytes": out[i].bytes, "flops": out[i].flops} for i in range(n.value)]
 
 
-def mdwf_set_staging(ctx, prec: int, staged: bool) -> None:
-    """Neighbour loads of the FP32 / FP16 hop kernels through shared memory (cp.async) or registers."""
-    _check(load().mdwf_set_staging(ctx, int(prec), int(bool(staged))), "mdwf_set_staging")
+STAGE_REGISTERS, STAGE_CP_ASYNC, STAGE_BULK = 0, 1, 2
 
 
-def mdwf_get_staging(ctx, prec: int) -> bool:
+def mdwf_set_staging(ctx, prec: int, staged: int) -> None:
+    """Neighbour loads of the FP32 / FP16 hop kernels: 0 into registers, 1 through shared
+    memory with per-thread cp.async, 2 whole neighbour columns by bulk copies (TMA)."""
+    _check(load().mdwf_set_staging(ctx, int(prec), int(staged)), "mdwf_set_staging")
+
+
+def mdwf_get_staging(ctx, prec: int) -> int:
     v = ctypes.c_int(0)
     _check(load().mdwf_get_staging(ctx, int(prec), ctypes.byref(v)), "mdwf_get_staging")
-    return bool(v.value)
+    return v.value
+
+
+def mdwf_device_status(ctx) -> int:
+    """Synchronise the context's stream; MDWF_ETIMEOUT if a bounded device wait gave up since
+    the last report (the mark is cleared), else MDWF_OK (a CUDA error raises)."""
+    st = load().mdwf_device_status(ctx)
+    if st not in (MDWF_OK, MDWF_ETIMEOUT):
+        _check(st, "mdwf_device_status")
+    return st
+
+
+def mdwf_selftest_wait(ctx, arrivals: int) -> int:
+    """Bounded-wait self-test: MDWF_ETIMEOUT unless both expected arrivals are made."""
+    st = load().mdwf_selftest_wait(ctx, int(arrivals))
+    if st not in (MDWF_OK, MDWF_ETIMEOUT):
+        _check(st, "mdwf_selftest_wait")
+    return st
 
 
 def mdwf_counters(ctx) -> tuple[int, list[int]]:

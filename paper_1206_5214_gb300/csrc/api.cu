@@ -381,6 +381,22 @@ using namespace mdwf;
 
 // ------------------------------------------------------------------- C ABI
 
+namespace mdwf {
+
+int device_wait_status(mdwf_ctx* c) {
+    int flag = 0;
+    int st;
+    if ((st = cuda_status(cudaMemcpyAsync(&flag, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream))) ||
+        (st = cuda_status(cudaStreamSynchronize(c->stream))))
+        return st;
+    if (!flag) return MDWF_OK;
+    if ((st = cuda_status(cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream)))) return st;
+    set_error_message("a bounded device-side wait gave up");
+    return MDWF_ETIMEOUT;
+}
+
+}  // namespace mdwf
+
 extern "C" {
 
 const char* mdwf_strerror(int status) {
@@ -431,6 +447,8 @@ int mdwf_create(mdwf_ctx** out, const int dims[4], int Ls, double M5, double b5,
     // the default mass tables, so that an apply needs no host round trip
     if ((st = ensure_tables(c, 1, nullptr)) ||
         (st = cuda_status(cudaMalloc(&c->nbr, sizeof(int) * 16 * (size_t)c->g.Vh))) ||
+        (st = cuda_status(cudaMalloc(&c->dev_err, sizeof(int)))) ||
+        (st = cuda_status(cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream))) ||
         (st = launch_build_neighbours(c)) || (st = cuda_status(cudaStreamSynchronize(c->stream)))) {
         mdwf_destroy(c);
         return st;
@@ -457,6 +475,7 @@ int mdwf_destroy(mdwf_ctx* c) {
     cudaFree(c->h4.p);
     cudaFree(c->red_partials);
     cudaFree(c->nbr);
+    cudaFree(c->dev_err);
     cudaFree(c->gs64); cudaFree(c->gs32);
     for (auto& r : c->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
@@ -689,8 +708,10 @@ int mdwf_get_tuning(const mdwf_ctx* c, int prec, int nrhs, int* sites_per_block)
 }
 
 int mdwf_set_staging(mdwf_ctx* c, int prec, int staged) {
-    if (!c || !valid_prec(prec) || (staged != 0 && staged != 1)) return MDWF_EINVAL;
+    if (!c || !valid_prec(prec) || staged < 0 || staged > 2) return MDWF_EINVAL;
     if (prec == MDWF_F64 && staged) return MDWF_EINVAL;
+    // bulk copies of the FP16 norms need 16-byte columns (4 Ls bytes)
+    if (prec == MDWF_F16N && staged == 2 && c->g.Ls % 4 != 0) return MDWF_EINVAL;
     c->hop_stage[prec] = staged;
     return MDWF_OK;
 }
@@ -699,6 +720,13 @@ int mdwf_get_staging(const mdwf_ctx* c, int prec, int* staged) {
     if (!c || !valid_prec(prec) || !staged) return MDWF_EINVAL;
     *staged = c->hop_stage[prec];
     return MDWF_OK;
+}
+
+int mdwf_device_status(mdwf_ctx* c) {
+    if (!c) return MDWF_EINVAL;
+    int st;
+    if ((st = cuda_status(cudaSetDevice(c->device)))) return st;
+    return device_wait_status(c);
 }
 
 int mdwf_counters(const mdwf_ctx* c, long long* launches, long long applies[3]) {

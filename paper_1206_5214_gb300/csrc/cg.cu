@@ -1038,6 +1038,7 @@ extern "C" int mdwf_cgne(mdwf_ctx* c, double* x, const double* b, int nrhs, cons
             return st;
     }
     if ((st = cuda_status(cudaStreamSynchronize(c->stream)))) return st;
+    if ((st = device_wait_status(c))) return st;
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     int ret = MDWF_OK;
     for (int r = 0; r < nrhs; ++r) {

@@ -44,6 +44,7 @@ template <typename R> struct HopParams {
     // (forward hop) and ebwd (backward hop) when chem is set
     bool chem;
     R efwd, ebwd;
+    int* err;        // device error word (bounded waits of the bulk variant)
 };
 
 // --------------------------------------------------------- spin structure
@@ -289,6 +290,188 @@ __device__ __forceinline__ void hop_staged(R* acc, const Field<P>& in, const Gau
     hop_term<P, 3, false, DAG, 0>(acc, in, U, hp, st, site, b.w, -1, s, rbase);
 }
 
+// ------------------------------------------ bulk copies of neighbour columns
+//
+// The bulk variant (STAGE == 2) lets the copy engine (TMA, cp.async.bulk)
+// fetch whole neighbour columns: in the [site][chunk][s] layout the Ls
+// spinors of a 4d site are one contiguous run of 96 Ls bytes (FP32), so one
+// instruction of the row's s = 0 thread moves a column into shared memory
+// while the threads compute the previous hopping term; the threads spend no
+// load instructions on the global copy. Two buffers [2][SB][column] alternate
+// over the eight terms, each with an mbarrier that counts the bytes of the
+// SB copies of its term. Every wait is bounded: after kWaitLimit polls it sets
+// the device error word and gives up (the results are then not valid; the
+// host reports MDWF_ETIMEOUT).
+
+constexpr int kWaitLimit = 1 << 20;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// non-blocking test of the phase with parity `parity`
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// bounded wait; false when the limit was reached
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+    for (int it = 0; it < kWaitLimit; ++it) {
+        if (mbar_test(bar, parity)) return true;
+        if (it >= 64) __nanosleep(64);
+    }
+    return false;
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// global -> shared, completing `bytes` on the mbarrier (16-byte aligned, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+template <int P> struct BulkBytes { static constexpr int value = 0; };  // per slice of a column
+template <> struct BulkBytes<MDWF_F32> { static constexpr int value = 96; };
+template <> struct BulkBytes<MDWF_F16N> { static constexpr int value = 52; };
+
+template <int P> struct Bulk;
+template <> struct Bulk<MDWF_F32> {
+    float4* buf;  // [2][SB][6 Ls]
+    int Ls, SB;
+    __device__ __forceinline__ void issue(const Field<MDWF_F32>& in, long long sr, int slot, int ly,
+                                          unsigned long long* bar) const {
+        const unsigned bytes = 96u * (unsigned)Ls;
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_g2s(buf + ((size_t)slot * SB + ly) * 6 * Ls, in.v + sr * 6 * Ls, bytes, bar);
+    }
+    __device__ __forceinline__ float read(int slot, int ly, int s, float* w) const {
+        const float4* p = buf + ((size_t)slot * SB + ly) * 6 * Ls + s;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float4 d = p[k * Ls];
+            w[4 * k] = d.x; w[4 * k + 1] = d.y; w[4 * k + 2] = d.z; w[4 * k + 3] = d.w;
+        }
+        return 1.0f;
+    }
+};
+template <> struct Bulk<MDWF_F16N> {
+    uint2* buf;  // [2][SB][6 Ls]
+    float* nrm;  // [2][SB][Ls]
+    int Ls, SB;
+    __device__ __forceinline__ void issue(const Field<MDWF_F16N>& in, long long sr, int slot, int ly,
+                                          unsigned long long* bar) const {
+        mbar_arrive_expect_tx(bar, 52u * (unsigned)Ls);
+        bulk_g2s(buf + ((size_t)slot * SB + ly) * 6 * Ls, in.v + sr * 6 * Ls, 48u * (unsigned)Ls, bar);
+        bulk_g2s(nrm + ((size_t)slot * SB + ly) * Ls, in.norm + sr * Ls, 4u * (unsigned)Ls, bar);
+    }
+    // values without the norm (applied to the transported half spinor); returns the norm
+    __device__ __forceinline__ float read(int slot, int ly, int s, float* w) const {
+        const uint2* p = buf + ((size_t)slot * SB + ly) * 6 * Ls + s;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Field<MDWF_F16N>::unpack_raw(p[k * Ls], w + 4 * k);
+        return nrm[((size_t)slot * SB + ly) * Ls + s];
+    }
+};
+
+// Hopping term T (0..7 = mu 0 forward, mu 0 backward, mu 1 forward, ...) from
+// buffer T % 2: wait for its columns, project, release the buffer to the copy
+// of term T + 2 (neighbour `next`), then transport and accumulate. Every
+// thread of the block takes part in the waits and barriers.
+template <int P, int T, bool DAG, typename R>
+__device__ __forceinline__ void bulk_term(R* acc, const Field<P>& in, const Gauge<P>& U, const HopParams<R>& hp,
+                                          const Bulk<P>& bk, unsigned long long* bars, bool& ok, bool active,
+                                          long long site, int jb, int next, int s, int ly, long long rbase) {
+    constexpr int MU = T / 2, SLOT = T % 2;
+    constexpr bool FWD = SLOT == 0;
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int S = FWD ? SF : -SF;
+    if (ok && !mbar_wait(bars + SLOT, (T / 2) & 1)) {
+        ok = false;
+        atomicOr(hp.err, 1);
+    }
+    R h[12], f = R(1);
+    if (active) {
+        R w[24];
+        f = bk.read(SLOT, ly, s, w);
+        project<MU, S>(w, h);
+    }
+    if (T + 2 < 8) {
+        __syncthreads();  // every thread is done with this buffer
+        if (s == 0) {
+            if (active && ok) {
+                fence_proxy_async();
+                bk.issue(in, rbase + next, SLOT, ly, bars + SLOT);
+            } else {
+                mbar_arrive(bars + SLOT);
+            }
+        }
+    }
+    if (active) {
+        R u[18];
+        if (FWD) U.load(((long long)hp.out_parity * 4 + MU) * hp.g.Vh + site, u);
+        else U.load(((long long)(1 - hp.out_parity) * 4 + MU) * hp.g.Vh + jb, u);
+        const bool tm = MU == 3 && hp.chem;
+        transport_add<!FWD, MU, S>(acc, u, h, tm ? f * (FWD ? hp.efwd : hp.ebwd) : f, P == MDWF_F16N || tm);
+    }
+}
+
+// The eight terms, two neighbour columns in flight per site row. bars[0..1]
+// are initialised here with one arrival per site row of the block.
+template <int P, bool DAG, typename R>
+__device__ __forceinline__ void hop_bulk(R* acc, const Field<P>& in, const Gauge<P>& U, const HopParams<R>& hp,
+                                         const Bulk<P>& bk, unsigned long long* bars, bool active, long long site,
+                                         int s, int ly, int tid, long long rbase) {
+    int4 f = make_int4(0, 0, 0, 0), b = f;
+    if (active) {
+        const int4* nb = hp.nbr + ((long long)hp.out_parity * hp.g.Vh + site) * 2;
+        f = __ldg(nb);
+        b = __ldg(nb + 1);
+    }
+    if (tid == 0) {
+        mbar_init(bars, (unsigned)bk.SB);
+        mbar_init(bars + 1, (unsigned)bk.SB);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    bool ok = true;
+    if (s == 0) {
+        if (active) {
+            bk.issue(in, rbase + f.x, 0, ly, bars);
+            bk.issue(in, rbase + b.x, 1, ly, bars + 1);
+        } else {
+            mbar_arrive(bars);
+            mbar_arrive(bars + 1);
+        }
+    }
+    bulk_term<P, 0, DAG>(acc, in, U, hp, bk, bars, ok, active, site, 0, f.y, s, ly, rbase);
+    bulk_term<P, 1, DAG>(acc, in, U, hp, bk, bars, ok, active, site, b.x, b.y, s, ly, rbase);
+    bulk_term<P, 2, DAG>(acc, in, U, hp, bk, bars, ok, active, site, 0, f.z, s, ly, rbase);
+    bulk_term<P, 3, DAG>(acc, in, U, hp, bk, bars, ok, active, site, b.y, b.z, s, ly, rbase);
+    bulk_term<P, 4, DAG>(acc, in, U, hp, bk, bars, ok, active, site, 0, f.w, s, ly, rbase);
+    bulk_term<P, 5, DAG>(acc, in, U, hp, bk, bars, ok, active, site, b.z, b.w, s, ly, rbase);
+    bulk_term<P, 6, DAG>(acc, in, U, hp, bk, bars, ok, active, site, 0, -1, s, ly, rbase);
+    bulk_term<P, 7, DAG>(acc, in, U, hp, bk, bars, ok, active, site, b.w, -1, s, ly, rbase);
+}
+
 // Fused CG epilogues (structured s-operators only):
 //   FUSE_T : after out = t = M p is formed, also write v = A^dag t (the first
 //            factor of M^dag) to out2 and the block's partial |t|^2 to part
@@ -318,12 +501,18 @@ __device__ __forceinline__ double block_sum128(double v, double* red) {
     return tot;
 }
 
+// shared memory of a hop block: [4 doubles: block reduction][2 mbarriers] then
+// the dense tables and the rows / staging buffers
+constexpr int kHopHeader = 4 * sizeof(double) + 2 * sizeof(unsigned long long);
+
 #ifndef MDWF_MINB_STAGE
 #define MDWF_MINB_STAGE 6
 #endif
 
-template <int P, bool GATHER, bool DAG, bool XPAY, int FUSE, bool STAGE>
-__global__ void __launch_bounds__(128, STAGE ? MDWF_MINB_STAGE : PrecTraits<P>::min_blocks - (GATHER ? 1 : 0))
+// STAGE: 0 neighbour spinors loaded into registers, 1 staged per thread with
+// cp.async, 2 whole neighbour columns copied by the copy engine (bulk).
+template <int P, bool GATHER, bool DAG, bool XPAY, int FUSE, int STAGE>
+__global__ void __launch_bounds__(128, STAGE == 1 ? MDWF_MINB_STAGE : PrecTraits<P>::min_blocks - (GATHER ? 1 : 0))
     hop_kernel(Field<P> out, Field<P> in, Field<P> xf, Gauge<P> U, HopParams<typename PrecTraits<P>::real> hp,
                FuseArgs<P> fa) {
     static_assert(!STAGE || (!GATHER && P != MDWF_F64), "staged loads: FP32 / FP16 operators without gather");
@@ -332,7 +521,8 @@ __global__ void __launch_bounds__(128, STAGE ? MDWF_MINB_STAGE : PrecTraits<P>::
     const int Ls = hp.g.Ls;
     const bool dense = hp.sop == SOP_DENSE;
     double* red = reinterpret_cast<double*>(smem_raw);          // [4] block reduction
-    R* mat = reinterpret_cast<R*>(smem_raw + 4 * sizeof(double)); // [chir][s'][s] (dense only)
+    unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem_raw + 4 * sizeof(double));  // [2]
+    R* mat = reinterpret_cast<R*>(smem_raw + kHopHeader);       // [chir][s'][s] (dense only)
     R* hs = mat + (dense ? 2 * Ls * Ls : 0);                      // [SB][site_stride], rows of kRowStride
     const int s = threadIdx.x, ly = threadIdx.y;
     const int rhs = blockIdx.x % hp.nrhs;
@@ -355,10 +545,22 @@ __global__ void __launch_bounds__(128, STAGE ? MDWF_MINB_STAGE : PrecTraits<P>::
     R acc[24];
 #pragma unroll
     for (int k = 0; k < 24; ++k) acc[k] = 0;
-    if (active) {
+    if constexpr (STAGE == 2) {
+        // the buffers alias the rows of the epilogue (used after a barrier)
+        Bulk<P> bk;
+        bk.Ls = Ls;
+        bk.SB = blockDim.y;
+        if constexpr (P == MDWF_F32) {
+            bk.buf = reinterpret_cast<float4*>(hs);
+        } else {
+            bk.buf = reinterpret_cast<uint2*>(hs);
+            bk.nrm = reinterpret_cast<float*>(bk.buf + (size_t)2 * blockDim.y * 6 * Ls);
+        }
+        hop_bulk<P, DAG>(acc, in, U, hp, bk, bars, active, site, s, ly, tid, rbase);
+    } else if (active) {
         const int4* nb = hp.nbr + ((long long)hp.out_parity * hp.g.Vh + site) * 2;
         const int4 f = __ldg(nb), b = __ldg(nb + 1);
-        if constexpr (STAGE) {
+        if constexpr (STAGE == 1) {
             // the staging buffers alias the rows of the epilogue (used after a barrier)
             Stager<P> st;
             if constexpr (P == MDWF_F32) {
@@ -377,7 +579,7 @@ __global__ void __launch_bounds__(128, STAGE ? MDWF_MINB_STAGE : PrecTraits<P>::
             hop_dir<P, 3, GATHER, DAG>(acc, in, U, hp, f.w, b.w, site, s, rbase, mass, gown, gfac);
         }
     }
-    if constexpr (STAGE) __syncthreads();
+    if constexpr (STAGE != 0) __syncthreads();
     if (GATHER && hp.gs) {
 #pragma unroll
         for (int k = 0; k < 24; ++k) acc[k] *= gpre;
@@ -475,22 +677,23 @@ int hop_blocks(const mdwf_ctx* c, int prec, int nrhs) {
     return (int)((c->g.Vh + SB - 1) / SB);
 }
 
-template <int P, bool G, bool D, bool X, int FU, bool ST>
+template <int P, bool G, bool D, bool X, int FU, int ST>
 static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<typename PrecTraits<P>::real>& hp) {
     typedef typename PrecTraits<P>::real R;
     const Geom& g = c->g;
     const int SB = hop_sites_per_block(c, P, h.nrhs);
     dim3 block(g.Ls, SB), grid((unsigned)((g.Vh + SB - 1) / SB * h.nrhs));
     const size_t rows = (size_t)SB * site_stride(g.Ls) * sizeof(R);
-    const size_t stage = ST ? (size_t)StageBytes<P>::value * g.Ls * SB : 0;
-    size_t smem = 4 * sizeof(double) + (size_t)(hp.sop == SOP_DENSE ? 2 * g.Ls * g.Ls : 0) * sizeof(R) +
+    const size_t stage = ST == 1 ? (size_t)StageBytes<P>::value * g.Ls * SB
+                         : ST == 2 ? (size_t)2 * BulkBytes<P>::value * g.Ls * SB : 0;
+    size_t smem = kHopHeader + (size_t)(hp.sop == SOP_DENSE ? 2 * g.Ls * g.Ls : 0) * sizeof(R) +
                   (rows > stage ? rows : stage);
     auto kern = hop_kernel<P, G, D, X, FU, ST>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_status(e);
     }
-    if (ST) {
+    if (ST != 0) {
         // the staging buffers need shared memory for every resident block (once per device)
         // (contexts on other host threads may launch at the same time: the mask is atomic, and
         // setting the attribute twice is harmless)
@@ -532,9 +735,10 @@ static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<t
 template <int P, bool G, bool D, bool X, int FU>
 static int launch_hop_pick(mdwf_ctx* c, const HopLaunch& h, const HopParams<typename PrecTraits<P>::real>& hp) {
     if constexpr (!G && P != MDWF_F64) {
-        if (c->hop_stage[P]) return launch_hop_variant<P, G, D, X, FU, true>(c, h, hp);
+        if (c->hop_stage[P] == 1) return launch_hop_variant<P, G, D, X, FU, 1>(c, h, hp);
+        if (c->hop_stage[P] == 2) return launch_hop_variant<P, G, D, X, FU, 2>(c, h, hp);
     }
-    return launch_hop_variant<P, G, D, X, FU, false>(c, h, hp);
+    return launch_hop_variant<P, G, D, X, FU, 0>(c, h, hp);
 }
 
 template <int P>
@@ -571,6 +775,7 @@ static int launch_hop_t(mdwf_ctx* c, const HopLaunch& h) {
     hp.chem = c->chem != 0.0;
     hp.efwd = (R)exp(h.dagger ? -c->chem : c->chem);
     hp.ebwd = (R)exp(h.dagger ? c->chem : -c->chem);
+    hp.err = c->dev_err;
     const bool X = h.x != nullptr;
     if (h.fuse != FUSE_NONE) {
         // fused CG epilogues: t = M p with v = A^dag t, or Ap = M^dag t folded into r
@@ -591,6 +796,17 @@ static int launch_hop_t(mdwf_ctx* c, const HopLaunch& h) {
              : launch_hop_pick<P, false, false, false, FUSE_NONE>(c, h, hp);
 }
 
+// One thread waits, bounded, on an mbarrier that expects two arrivals of
+// which `arrivals` are made; a wait that gives up sets the error word.
+__global__ void k_wait_selftest(int* err, int arrivals) {
+    __shared__ unsigned long long bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 2);
+    mbar_init_fence();
+    for (int k = 0; k < arrivals; ++k) mbar_arrive(&bar);
+    if (!mbar_wait(&bar, 0)) atomicOr(err, 1);
+}
+
 int launch_hop(mdwf_ctx* c, int prec, const HopLaunch& h) {
     switch (prec) {
         case MDWF_F64: return launch_hop_t<MDWF_F64>(c, h);
@@ -601,3 +817,14 @@ int launch_hop(mdwf_ctx* c, int prec, const HopLaunch& h) {
 }
 
 }  // namespace mdwf
+
+using namespace mdwf;
+
+extern "C" int mdwf_selftest_wait(mdwf_ctx* c, int arrivals) {
+    if (!c || arrivals < 0 || arrivals > 2) return MDWF_EINVAL;
+    int st;
+    if ((st = cuda_status(cudaSetDevice(c->device)))) return st;
+    k_wait_selftest<<<1, 32, 0, c->stream>>>(c->dev_err, arrivals);
+    if ((st = check_launch())) return st;
+    return device_wait_status(c);
+}

@@ -582,8 +582,11 @@ struct mdwf_ctx {
     long long applies[3] = {0, 0, 0};
     // autotuned 4d sites per hop block, [precision][nrhs] (0 = default)
     int sb_tune[3][65] = {};
-    // 1: FP32 / FP16 hops stage neighbour spinors in shared memory (cp.async), [precision]
+    // load strategy of the FP32 / FP16 hops, [precision]: 0 registers, 1 cp.async
+    // per thread, 2 bulk copies of whole neighbour columns (TMA)
     int hop_stage[3] = {0, 0, 0};
+    // device word set by a bounded device-side wait that gave up (0 = none)
+    int* dev_err = nullptr;
     bool autotune = false;
     // content of the CUDA graph being captured (added once per replay)
     long long cap_launches = 0;
@@ -614,6 +617,8 @@ void replay_graph_counts(mdwf_ctx* c, long long replays);
 void set_error_message(const char* msg);
 int cuda_status(cudaError_t e);
 int check_launch();
+// MDWF_ETIMEOUT if a bounded device-side wait gave up since the last call (synchronises)
+int device_wait_status(mdwf_ctx* c);
 int ensure_workspace(Workspace& w, size_t bytes);
 int ensure_tables(mdwf_ctx* c, int nrhs, const double* mf_per_rhs);
 

@@ -213,24 +213,53 @@ def test_autotune_keeps_results_and_cache(tmp_path):
             check(c.apply(odd, F32)[0], ref, F32)
 
 
+@pytest.mark.parametrize("mode", [mdwf.STAGE_CP_ASYNC, mdwf.STAGE_BULK], ids=["cp.async", "bulk"])
 @pytest.mark.parametrize("prec", [F32, F16N])
-@pytest.mark.parametrize("dims,Ls", [((8, 4, 4, 4), 16), ((6, 2, 2, 4), 6)], ids=["Ls16", "ragged-Ls6"])
-def test_staged_loads_match_plain(prec, dims, Ls):
-    """Neighbour spinors staged in shared memory (cp.async) give the operator of
-    the plain loads (the same arithmetic), and both match the oracle."""
+@pytest.mark.parametrize("dims,Ls", [((8, 4, 4, 4), 16), ((6, 2, 2, 4), 6), ((6, 4, 2, 2), 12), ((4, 2, 2, 6), 32)],
+                         ids=["Ls16", "ragged-Ls6", "ragged-Ls12", "Ls32"])
+def test_staged_loads_match_plain(mode, prec, dims, Ls):
+    """Neighbour spinors staged in shared memory (per-thread cp.async, or whole
+    columns by bulk copies) give the operator of the plain loads (the same
+    arithmetic), and all match the oracle. Vh is not a multiple of the sites per
+    block in the ragged cases, so the last block has idle site rows; at Ls = 12
+    a site row straddles two warps."""
     U, odd, p = setup(dims, Ls, 1.5, 0.5, 0.02, 0.3, 8)
     with Ctx(dims, Ls, 1.8, 1.5, 0.5, 0.02, U) as c:
+        if prec == F16N and mode == mdwf.STAGE_BULK and Ls % 4:
+            with pytest.raises(mdwf.MdwfError):
+                mdwf.mdwf_set_staging(c.h, prec, mode)
+            return
         for dagger in (False, True):
             ref = oracle.m(odd, U, p, dagger=dagger)
-            mdwf.mdwf_set_staging(c.h, prec, False)
+            mdwf.mdwf_set_staging(c.h, prec, mdwf.STAGE_REGISTERS)
             a = c.apply(odd, prec, dagger)[0]
-            mdwf.mdwf_set_staging(c.h, prec, True)
-            assert mdwf.mdwf_get_staging(c.h, prec)
+            mdwf.mdwf_set_staging(c.h, prec, mode)
+            assert mdwf.mdwf_get_staging(c.h, prec) == mode
             b = c.apply(odd, prec, dagger)[0]
             assert np.abs(a - b).max() <= 1e-6 * np.abs(a).max()
             check(b, ref, prec)
+        assert mdwf.mdwf_device_status(c.h) == mdwf.MDWF_OK
         with pytest.raises(mdwf.MdwfError):
-            mdwf.mdwf_set_staging(c.h, F64, True)
+            mdwf.mdwf_set_staging(c.h, F64, mode)
+        with pytest.raises(mdwf.MdwfError):
+            mdwf.mdwf_set_staging(c.h, prec, 3)
+
+
+@pytest.mark.parametrize("arrivals", [0, 1, 2])
+def test_bounded_device_wait(arrivals):
+    """A device-side wait on an mbarrier that never completes (fewer arrivals
+    than expected) gives up within its limit and is reported as MDWF_ETIMEOUT;
+    the mark is cleared by the report and the context stays usable."""
+    import time
+    dims, Ls = (4, 4, 2, 2), 8
+    U, odd, p = setup(dims, Ls, 1.5, 0.5, 0.02, 0.3, 10)
+    with Ctx(dims, Ls, 1.8, 1.5, 0.5, 0.02, U) as c:
+        t0 = time.perf_counter()
+        st = mdwf.mdwf_selftest_wait(c.h, arrivals)
+        assert time.perf_counter() - t0 < 10.0
+        assert st == (mdwf.MDWF_OK if arrivals == 2 else mdwf.MDWF_ETIMEOUT)
+        assert mdwf.mdwf_device_status(c.h) == mdwf.MDWF_OK
+        check(c.apply(odd, F32)[0], oracle.m(odd, U, p), F32)
 
 
 @pytest.mark.parametrize("prec", [F64, F32])
