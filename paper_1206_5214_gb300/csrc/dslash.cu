@@ -1,667 +1,13 @@
-// Fused hopping kernel of the red/black Moebius operator.
-//
-// One launch computes, for every site x of parity `out_parity` and every s,
-//   out(x, s) = coef * sum_s' Mat_chi(s, s') [H w](x, s') (+ x_add(x, s))
-// where H is the Wilson hopping sum of Eq. (D^Wilson),
-//   H w(x) = sum_mu [(1 - g_mu) U_mu(x) w(x+mu) + (1 + g_mu) U_mu(x-mu)^dag w(x-mu)]
-// (projector signs flipped for the hopping part of D_W^dag), and w is either
-// the input field or the input with the fifth-dimension gather of Sec. 3
-// applied first: w_s = b5 psi_s + c5 (P+ psi_{s-1} + P- psi_{s+1}) with the
-// mass -m on the wrap-around terms (Eq. DWaction), i.e. w = M_phi psi.
-// Mat is an Ls x Ls real matrix per chirality (K = M_phi I^-1, I^-1, ...).
-//
-// Thread mapping: a block is Ls x SB threads: threadIdx.x = s, threadIdx.y =
-// one of SB 4d sites, blockIdx.y = right-hand side. The Ls threads of a
-// column load the same link (one L1 line, broadcast), so each link is read
-// from HBM once per hop and reused across all Ls slices. Spinor chunks of
-// consecutive s are contiguous, so every vector load of a warp is coalesced.
-// The s-mixing matrix is applied after the hop through shared memory.
-#include <atomic>
-
+// Hop launch dispatch over the operator precisions (the kernels are in
+// hop_kernel.cuh, instantiated in dslash_f64.cu, dslash_f32.cu and
+// dslash_f16n.cu), the block shapes of the hop kernels, and the self-test of
+// the bounded device-side wait.
 #include "mdwf_internal.cuh"
+#include "mbarrier.cuh"
 
 namespace mdwf {
 
-template <typename R> struct HopParams {
-    Geom g;
-    int nrhs;        // blocks are (site block, rhs) with rhs fastest: blocks that run
-                     // together share sites, so their links come from L2
-    int out_parity;
-    R coef;
-    // input gather w = gscale * (gown psi_s + gfac (P+ psi_{s-1} + P- psi_{s+1})) = M_phi psi;
-    // gscale is applied once to the accumulated hop instead of per neighbour
-    R gown, gfac, gscale;
-    // per-slice gather factors [gown(s)][gfac(s)][gscale(s)] (64 each) for
-    // s-dependent b5(s), c5(s), or null; gscale(s) then scales the hop of row s
-    // before the s-mixing and gscale above is 1
-    const R* gs;
-    const R* mass;   // [rhs]
-    const R* mat;    // dense tables [rhs][chir][s'][s] (sop == SOP_DENSE)
-    const int4* nbr; // [parity][site][2] = cb index of x+mu (mu = 0..3), then of x-mu
-    int sop, swap;
-    SCoef<R> sc;
-    // chemical potential (Sec. 6.6): the time-direction terms carry efwd
-    // (forward hop) and ebwd (backward hop) when chem is set
-    bool chem;
-    R efwd, ebwd;
-    int* err;        // device error word (bounded waits of the bulk variant)
-};
-
-// --------------------------------------------------------- spin structure
-//
-// Chiral basis g_mu = [[0, A_mu], [A_mu^dag, 0]], A_k = -i sigma_k, A_4 = 1.
-// (1 + S g_mu) psi, psi = (u, l) by chirality halves, has upper half
-// h = u + S A l and lower half S A^dag h, so only h (2 spins x 3 colours) is
-// transported: project -> multiply by the link -> reconstruct.
-
-template <int MU, int S, typename R>
-__device__ __forceinline__ void project(const R* w, R* h) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const R u0r = w[2 * c], u0i = w[2 * c + 1], u1r = w[6 + 2 * c], u1i = w[7 + 2 * c];
-        const R l0r = w[12 + 2 * c], l0i = w[13 + 2 * c], l1r = w[18 + 2 * c], l1i = w[19 + 2 * c];
-        R a0r, a0i, a1r, a1i;  // (A l)_0, (A l)_1
-        if (MU == 0) {         // A = -i sigma_1: (A l)_0 = -i l1, (A l)_1 = -i l0
-            a0r = l1i; a0i = -l1r; a1r = l0i; a1i = -l0r;
-        } else if (MU == 1) {  // A = -i sigma_2: (A l)_0 = -l1, (A l)_1 = l0
-            a0r = -l1r; a0i = -l1i; a1r = l0r; a1i = l0i;
-        } else if (MU == 2) {  // A = -i sigma_3: (A l)_0 = -i l0, (A l)_1 = i l1
-            a0r = l0i; a0i = -l0r; a1r = -l1i; a1i = l1r;
-        } else {               // A = 1
-            a0r = l0r; a0i = l0i; a1r = l1r; a1i = l1i;
-        }
-        h[2 * c] = u0r + S * a0r;
-        h[2 * c + 1] = u0i + S * a0i;
-        h[6 + 2 * c] = u1r + S * a1r;
-        h[7 + 2 * c] = u1i + S * a1i;
-    }
-}
-
-// Transport and reconstruction of one hopping term: g[a][i] = sum_j V[i][j] h[a][j]
-// with V = U (or U^dag when ADJ; U row-major complex 3x3), then the upper half
-// of (1 + S g_mu) gets g and the lower half S A_mu^dag g. It runs one output
-// colour i at a time so that only one colour of g is live; `scaled` multiplies
-// g by `scale` first (the FP16 norm of the neighbour).
-template <bool ADJ, int MU, int S, typename R>
-__device__ __forceinline__ void transport_add(R* acc, const R* U, const R* h, R scale, bool scaled) {
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        R g[4];
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-            // complex multiply-accumulate as four fused multiply-adds per term
-            R sr = 0, si = 0;
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const R ur = ADJ ? U[2 * (3 * j + i)] : U[2 * (3 * i + j)];
-                const R ui = ADJ ? -U[2 * (3 * j + i) + 1] : U[2 * (3 * i + j) + 1];
-                const R hr = h[6 * a + 2 * j], hi = h[6 * a + 2 * j + 1];
-                sr = fma(ur, hr, sr);
-                sr = fma(-ui, hi, sr);
-                si = fma(ur, hi, si);
-                si = fma(ui, hr, si);
-            }
-            g[2 * a] = scaled ? scale * sr : sr;
-            g[2 * a + 1] = scaled ? scale * si : si;
-        }
-        const R g0r = g[0], g0i = g[1], g1r = g[2], g1i = g[3];
-        acc[2 * i] += g0r;
-        acc[2 * i + 1] += g0i;
-        acc[6 + 2 * i] += g1r;
-        acc[7 + 2 * i] += g1i;
-        R b0r, b0i, b1r, b1i;  // (A^dag g)_0, (A^dag g)_1
-        if (MU == 0) {         // A^dag = i sigma_1: (i g1, i g0)
-            b0r = -g1i; b0i = g1r; b1r = -g0i; b1i = g0r;
-        } else if (MU == 1) {  // A^dag = i sigma_2: (g1, -g0)
-            b0r = g1r; b0i = g1i; b1r = -g0r; b1i = -g0i;
-        } else if (MU == 2) {  // A^dag = i sigma_3: (i g0, -i g1)
-            b0r = -g0i; b0i = g0r; b1r = g1i; b1i = -g1r;
-        } else {
-            b0r = g0r; b0i = g0i; b1r = g1r; b1i = g1i;
-        }
-        acc[12 + 2 * i] += S * b0r;
-        acc[13 + 2 * i] += S * b0i;
-        acc[18 + 2 * i] += S * b1r;
-        acc[19 + 2 * i] += S * b1i;
-    }
-}
-
-// w = psi(s), or M_phi psi at s up to the factor gscale, for the neighbour column sr.
-// Returns a factor still to be applied to w (the FP16 norm of an ungathered
-// input, which is linear and is applied to the transported half spinor).
-template <int P, bool GATHER, typename R>
-__device__ __forceinline__ R load_input(const Field<P>& in, long long sr, int s, int Ls, R gown, R gfac,
-                                        R mass, R* w) {
-    if constexpr (P == MDWF_F16N && !GATHER) {
-        return in.load_raw(sr, s, w);
-    }
-    in.load(sr, s, w);
-    if (GATHER) {
-        if (gown != R(1)) {
-#pragma unroll
-            for (int k = 0; k < 24; ++k) w[k] *= gown;
-        }
-        if (gfac != R(0)) {
-            R t[12];
-            const int sm = s > 0 ? s - 1 : Ls - 1;
-            const R fm = s > 0 ? gfac : -mass * gfac;
-            in.load_half(sr, sm, 0, t);  // P+ psi_{s-1}
-#pragma unroll
-            for (int k = 0; k < 12; ++k) w[k] += fm * t[k];
-            const int sp = s < Ls - 1 ? s + 1 : 0;
-            const R fp = s < Ls - 1 ? gfac : -mass * gfac;
-            in.load_half(sr, sp, 1, t);  // P- psi_{s+1}
-#pragma unroll
-            for (int k = 0; k < 12; ++k) w[12 + k] += fp * t[k];
-        }
-    }
-    return R(1);
-}
-
-template <int P, int MU, bool GATHER, bool DAG, typename R>
-__device__ __forceinline__ void hop_dir(R* acc, const Field<P>& in, const Gauge<P>& U, const HopParams<R>& hp,
-                                        long long jf, long long jb, long long site, int s, long long rbase, R mass,
-                                        R gown, R gfac) {
-    const Geom& g = hp.g;
-    constexpr int SF = DAG ? +1 : -1;  // forward projector 1 + SF g_mu
-    constexpr bool SCALED = P == MDWF_F16N && !GATHER;
-    {
-        R w[24], h[12], u[18];
-        const R f = load_input<P, GATHER>(in, rbase + jf, s, g.Ls, gown, gfac, mass, w);
-        project<MU, SF>(w, h);
-        U.load(((long long)hp.out_parity * 4 + MU) * g.Vh + site, u);
-        const bool tm = MU == 3 && hp.chem;
-        transport_add<false, MU, SF>(acc, u, h, tm ? f * hp.efwd : f, SCALED || tm);
-    }
-    {
-        R w[24], h[12], u[18];
-        const R f = load_input<P, GATHER>(in, rbase + jb, s, g.Ls, gown, gfac, mass, w);
-        project<MU, -SF>(w, h);
-        U.load(((long long)(1 - hp.out_parity) * 4 + MU) * g.Vh + jb, u);
-        const bool tm = MU == 3 && hp.chem;
-        transport_add<true, MU, -SF>(acc, u, h, tm ? f * hp.ebwd : f, SCALED || tm);
-    }
-}
-
-// ------------------------------------------------ staged neighbour loads
-//
-// The staged variant (STAGE) copies each neighbour spinor of a thread into
-// shared memory with cp.async (LDGSTS) one neighbour ahead of its use, so two
-// neighbour loads per thread are in flight without holding registers; the
-// plain variant loads into registers when the spinor is needed. Buffers are
-// [2][chunk][thread] so that a warp's 16-byte accesses are contiguous.
-
-__device__ __forceinline__ void cp_async(void* smem, const void* gmem, int bytes) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    if (bytes == 16)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-    else if (bytes == 8)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-
-// bytes of the staging buffers per thread (two neighbour spinors)
-template <int P> struct StageBytes { static constexpr int value = 0; };
-template <> struct StageBytes<MDWF_F32> { static constexpr int value = 2 * 6 * 16; };
-template <> struct StageBytes<MDWF_F16N> { static constexpr int value = 2 * (6 * 8 + 4); };
-
-template <int P> struct Stager;
-template <> struct Stager<MDWF_F32> {
-    float4* buf;  // [2][6][nthr]
-    int nthr, tid;
-    __device__ __forceinline__ void issue(const Field<MDWF_F32>& in, long long sr, int s, int slot) const {
-        const float4* src = in.v + sr * 6 * in.Ls + s;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) cp_async(buf + (slot * 6 + k) * nthr + tid, src + (long long)k * in.Ls, 16);
-        cp_async_commit();
-    }
-    __device__ __forceinline__ float read(int slot, float* w) const {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const float4 d = buf[(slot * 6 + k) * nthr + tid];
-            w[4 * k] = d.x; w[4 * k + 1] = d.y; w[4 * k + 2] = d.z; w[4 * k + 3] = d.w;
-        }
-        return 1.0f;
-    }
-};
-template <> struct Stager<MDWF_F16N> {
-    uint2* buf;   // [2][6][nthr]
-    float* nrm;   // [2][nthr]
-    int nthr, tid;
-    __device__ __forceinline__ void issue(const Field<MDWF_F16N>& in, long long sr, int s, int slot) const {
-        const uint2* src = in.v + sr * 6 * in.Ls + s;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) cp_async(buf + (slot * 6 + k) * nthr + tid, src + (long long)k * in.Ls, 8);
-        cp_async(nrm + slot * nthr + tid, in.norm + sr * in.Ls + s, 4);
-        cp_async_commit();
-    }
-    // values without the norm (applied to the transported half spinor); returns the norm
-    __device__ __forceinline__ float read(int slot, float* w) const {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) Field<MDWF_F16N>::unpack_raw(buf[(slot * 6 + k) * nthr + tid], w + 4 * k);
-        return nrm[slot * nthr + tid];
-    }
-};
-
-// Hopping term n of the eight (MU, FWD) from staging slot n % 2: wait for its
-// copy, project it, refill the slot with neighbour `next` (< 0: none), then
-// transport and accumulate.
-template <int P, int MU, bool FWD, bool DAG, int WAITN, typename R>
-__device__ __forceinline__ void hop_term(R* acc, const Field<P>& in, const Gauge<P>& U, const HopParams<R>& hp,
-                                         const Stager<P>& st, long long site, int jb, int next, int s,
-                                         long long rbase) {
-    constexpr int SF = DAG ? +1 : -1;
-    constexpr int S = FWD ? SF : -SF;
-    constexpr int SLOT = FWD ? 0 : 1;
-    R h[12], u[18];
-    cp_async_wait<WAITN>();
-    R f;
-    {
-        R w[24];
-        f = st.read(SLOT, w);
-        project<MU, S>(w, h);
-    }
-    if (next >= 0) st.issue(in, rbase + next, s, SLOT);
-    if (FWD) U.load(((long long)hp.out_parity * 4 + MU) * hp.g.Vh + site, u);
-    else U.load(((long long)(1 - hp.out_parity) * 4 + MU) * hp.g.Vh + jb, u);
-    const bool tm = MU == 3 && hp.chem;
-    transport_add<!FWD, MU, S>(acc, u, h, tm ? f * (FWD ? hp.efwd : hp.ebwd) : f, P == MDWF_F16N || tm);
-}
-
-// The eight terms with the next neighbour in flight while one is computed.
-template <int P, bool DAG, typename R>
-__device__ __forceinline__ void hop_staged(R* acc, const Field<P>& in, const Gauge<P>& U, const HopParams<R>& hp,
-                                           const Stager<P>& st, int4 f, int4 b, long long site, int s,
-                                           long long rbase) {
-    st.issue(in, rbase + f.x, s, 0);
-    st.issue(in, rbase + b.x, s, 1);
-    hop_term<P, 0, true, DAG, 1>(acc, in, U, hp, st, site, 0, f.y, s, rbase);
-    hop_term<P, 0, false, DAG, 1>(acc, in, U, hp, st, site, b.x, b.y, s, rbase);
-    hop_term<P, 1, true, DAG, 1>(acc, in, U, hp, st, site, 0, f.z, s, rbase);
-    hop_term<P, 1, false, DAG, 1>(acc, in, U, hp, st, site, b.y, b.z, s, rbase);
-    hop_term<P, 2, true, DAG, 1>(acc, in, U, hp, st, site, 0, f.w, s, rbase);
-    hop_term<P, 2, false, DAG, 1>(acc, in, U, hp, st, site, b.z, b.w, s, rbase);
-    hop_term<P, 3, true, DAG, 1>(acc, in, U, hp, st, site, 0, -1, s, rbase);
-    hop_term<P, 3, false, DAG, 0>(acc, in, U, hp, st, site, b.w, -1, s, rbase);
-}
-
-// ------------------------------------------ bulk copies of neighbour columns
-//
-// The bulk variant (STAGE == 2) lets the copy engine (TMA, cp.async.bulk)
-// fetch whole neighbour columns: in the [site][chunk][s] layout the Ls
-// spinors of a 4d site are one contiguous run of 96 Ls bytes (FP32), so one
-// instruction of the row's s = 0 thread moves a column into shared memory
-// while the threads compute the previous hopping term; the threads spend no
-// load instructions on the global copy. Two buffers [2][SB][column] alternate
-// over the eight terms, each with an mbarrier that counts the bytes of the
-// SB copies of its term. Every wait is bounded: after kWaitLimit polls it sets
-// the device error word and gives up (the results are then not valid; the
-// host reports MDWF_ETIMEOUT).
-
-constexpr int kWaitLimit = 1 << 20;
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_init_fence() {
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-// non-blocking test of the phase with parity `parity`
-__device__ __forceinline__ bool mbar_test(unsigned long long* bar, unsigned parity) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-// bounded wait; false when the limit was reached
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-    for (int it = 0; it < kWaitLimit; ++it) {
-        if (mbar_test(bar, parity)) return true;
-        if (it >= 64) __nanosleep(64);
-    }
-    return false;
-}
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
-// global -> shared, completing `bytes` on the mbarrier (16-byte aligned, size a multiple of 16)
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-template <int P> struct BulkBytes { static constexpr int value = 0; };  // per slice of a column
-template <> struct BulkBytes<MDWF_F32> { static constexpr int value = 96; };
-template <> struct BulkBytes<MDWF_F16N> { static constexpr int value = 52; };
-
-template <int P> struct Bulk;
-template <> struct Bulk<MDWF_F32> {
-    float4* buf;  // [2][SB][6 Ls]
-    int Ls, SB;
-    __device__ __forceinline__ void issue(const Field<MDWF_F32>& in, long long sr, int slot, int ly,
-                                          unsigned long long* bar) const {
-        const unsigned bytes = 96u * (unsigned)Ls;
-        mbar_arrive_expect_tx(bar, bytes);
-        bulk_g2s(buf + ((size_t)slot * SB + ly) * 6 * Ls, in.v + sr * 6 * Ls, bytes, bar);
-    }
-    __device__ __forceinline__ float read(int slot, int ly, int s, float* w) const {
-        const float4* p = buf + ((size_t)slot * SB + ly) * 6 * Ls + s;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            const float4 d = p[k * Ls];
-            w[4 * k] = d.x; w[4 * k + 1] = d.y; w[4 * k + 2] = d.z; w[4 * k + 3] = d.w;
-        }
-        return 1.0f;
-    }
-};
-template <> struct Bulk<MDWF_F16N> {
-    uint2* buf;  // [2][SB][6 Ls]
-    float* nrm;  // [2][SB][Ls]
-    int Ls, SB;
-    __device__ __forceinline__ void issue(const Field<MDWF_F16N>& in, long long sr, int slot, int ly,
-                                          unsigned long long* bar) const {
-        mbar_arrive_expect_tx(bar, 52u * (unsigned)Ls);
-        bulk_g2s(buf + ((size_t)slot * SB + ly) * 6 * Ls, in.v + sr * 6 * Ls, 48u * (unsigned)Ls, bar);
-        bulk_g2s(nrm + ((size_t)slot * SB + ly) * Ls, in.norm + sr * Ls, 4u * (unsigned)Ls, bar);
-    }
-    // values without the norm (applied to the transported half spinor); returns the norm
-    __device__ __forceinline__ float read(int slot, int ly, int s, float* w) const {
-        const uint2* p = buf + ((size_t)slot * SB + ly) * 6 * Ls + s;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) Field<MDWF_F16N>::unpack_raw(p[k * Ls], w + 4 * k);
-        return nrm[((size_t)slot * SB + ly) * Ls + s];
-    }
-};
-
-// Hopping term T (0..7 = mu 0 forward, mu 0 backward, mu 1 forward, ...) from
-// buffer T % 2: wait for its columns, project, release the buffer to the copy
-// of term T + 2 (neighbour `next`), then transport and accumulate. Every
-// thread of the block takes part in the waits and barriers.
-template <int P, int T, bool DAG, typename R>
-__device__ __forceinline__ void bulk_term(R* acc, const Field<P>& in, const Gauge<P>& U, const HopParams<R>& hp,
-                                          const Bulk<P>& bk, unsigned long long* bars, bool& ok, bool active,
-                                          long long site, int jb, int next, int s, int ly, long long rbase) {
-    constexpr int MU = T / 2, SLOT = T % 2;
-    constexpr bool FWD = SLOT == 0;
-    constexpr int SF = DAG ? +1 : -1;
-    constexpr int S = FWD ? SF : -SF;
-    if (ok && !mbar_wait(bars + SLOT, (T / 2) & 1)) {
-        ok = false;
-        atomicOr(hp.err, 1);
-    }
-    R h[12], f = R(1);
-    if (active) {
-        R w[24];
-        f = bk.read(SLOT, ly, s, w);
-        project<MU, S>(w, h);
-    }
-    if (T + 2 < 8) {
-        __syncthreads();  // every thread is done with this buffer
-        if (s == 0) {
-            if (active && ok) {
-                fence_proxy_async();
-                bk.issue(in, rbase + next, SLOT, ly, bars + SLOT);
-            } else {
-                mbar_arrive(bars + SLOT);
-            }
-        }
-    }
-    if (active) {
-        R u[18];
-        if (FWD) U.load(((long long)hp.out_parity * 4 + MU) * hp.g.Vh + site, u);
-        else U.load(((long long)(1 - hp.out_parity) * 4 + MU) * hp.g.Vh + jb, u);
-        const bool tm = MU == 3 && hp.chem;
-        transport_add<!FWD, MU, S>(acc, u, h, tm ? f * (FWD ? hp.efwd : hp.ebwd) : f, P == MDWF_F16N || tm);
-    }
-}
-
-// The eight terms, two neighbour columns in flight per site row. bars[0..1]
-// are initialised here with one arrival per site row of the block.
-template <int P, bool DAG, typename R>
-__device__ __forceinline__ void hop_bulk(R* acc, const Field<P>& in, const Gauge<P>& U, const HopParams<R>& hp,
-                                         const Bulk<P>& bk, unsigned long long* bars, bool active, long long site,
-                                         int s, int ly, int tid, long long rbase) {
-    int4 f = make_int4(0, 0, 0, 0), b = f;
-    if (active) {
-        const int4* nb = hp.nbr + ((long long)hp.out_parity * hp.g.Vh + site) * 2;
-        f = __ldg(nb);
-        b = __ldg(nb + 1);
-    }
-    if (tid == 0) {
-        mbar_init(bars, (unsigned)bk.SB);
-        mbar_init(bars + 1, (unsigned)bk.SB);
-        mbar_init_fence();
-    }
-    __syncthreads();
-    bool ok = true;
-    if (s == 0) {
-        if (active) {
-            bk.issue(in, rbase + f.x, 0, ly, bars);
-            bk.issue(in, rbase + b.x, 1, ly, bars + 1);
-        } else {
-            mbar_arrive(bars);
-            mbar_arrive(bars + 1);
-        }
-    }
-    bulk_term<P, 0, DAG>(acc, in, U, hp, bk, bars, ok, active, site, 0, f.y, s, ly, rbase);
-    bulk_term<P, 1, DAG>(acc, in, U, hp, bk, bars, ok, active, site, b.x, b.y, s, ly, rbase);
-    bulk_term<P, 2, DAG>(acc, in, U, hp, bk, bars, ok, active, site, 0, f.z, s, ly, rbase);
-    bulk_term<P, 3, DAG>(acc, in, U, hp, bk, bars, ok, active, site, b.y, b.z, s, ly, rbase);
-    bulk_term<P, 4, DAG>(acc, in, U, hp, bk, bars, ok, active, site, 0, f.w, s, ly, rbase);
-    bulk_term<P, 5, DAG>(acc, in, U, hp, bk, bars, ok, active, site, b.z, b.w, s, ly, rbase);
-    bulk_term<P, 6, DAG>(acc, in, U, hp, bk, bars, ok, active, site, 0, -1, s, ly, rbase);
-    bulk_term<P, 7, DAG>(acc, in, U, hp, bk, bars, ok, active, site, b.w, -1, s, ly, rbase);
-}
-
-// Fused CG epilogues (structured s-operators only):
-//   FUSE_T : after out = t = M p is formed, also write v = A^dag t (the first
-//            factor of M^dag) to out2 and the block's partial |t|^2 to part
-//   FUSE_R : out = Ap = M^dag t is not stored; instead r -= alpha Ap in the
-//            residual field (precision PR) and the partial |r|^2 goes to part
-enum { FUSE_NONE = 0, FUSE_T = 1, FUSE_R = 2 };
-
-template <int P> struct ResPrec { static constexpr int value = P == MDWF_F64 ? MDWF_F64 : MDWF_F32; };
-
-template <int P> struct FuseArgs {
-    Field<P> out2;                     // FUSE_T: v = A^dag t
-    Field<ResPrec<P>::value> rf;       // FUSE_R: residual r
-    double* part;                      // [rhs][blockIdx.x] partial sums
-    const double* sc;                  // CG scalars [slot][64]: alpha at slot 2, active flag at slot 5
-};
-
-__device__ __forceinline__ double block_sum128(double v, double* red) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const int nthr = blockDim.x * blockDim.y;
-    if ((tid & 31) == 0) red[tid >> 5] = v;
-    __syncthreads();
-    double tot = 0;
-    if (tid == 0)
-        for (int w = 0; w < (nthr + 31) / 32; ++w) tot += red[w];
-    return tot;
-}
-
-// shared memory of a hop block: [4 doubles: block reduction][2 mbarriers] then
-// the dense tables and the rows / staging buffers
-constexpr int kHopHeader = 4 * sizeof(double) + 2 * sizeof(unsigned long long);
-
-#ifndef MDWF_MINB_STAGE
-#define MDWF_MINB_STAGE 6
-#endif
-
-// STAGE: 0 neighbour spinors loaded into registers, 1 staged per thread with
-// cp.async, 2 whole neighbour columns copied by the copy engine (bulk).
-template <int P, bool GATHER, bool DAG, bool XPAY, int FUSE, int STAGE>
-__global__ void __launch_bounds__(128, STAGE == 1 ? MDWF_MINB_STAGE : PrecTraits<P>::min_blocks - (GATHER ? 1 : 0))
-    hop_kernel(Field<P> out, Field<P> in, Field<P> xf, Gauge<P> U, HopParams<typename PrecTraits<P>::real> hp,
-               FuseArgs<P> fa) {
-    static_assert(!STAGE || (!GATHER && P != MDWF_F64), "staged loads: FP32 / FP16 operators without gather");
-    typedef typename PrecTraits<P>::real R;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Ls = hp.g.Ls;
-    const bool dense = hp.sop == SOP_DENSE;
-    double* red = reinterpret_cast<double*>(smem_raw);          // [4] block reduction
-    unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem_raw + 4 * sizeof(double));  // [2]
-    R* mat = reinterpret_cast<R*>(smem_raw + kHopHeader);       // [chir][s'][s] (dense only)
-    R* hs = mat + (dense ? 2 * Ls * Ls : 0);                      // [SB][site_stride], rows of kRowStride
-    const int s = threadIdx.x, ly = threadIdx.y;
-    const int rhs = blockIdx.x % hp.nrhs;
-    const long long sblk = blockIdx.x / hp.nrhs;
-    const int tid = ly * blockDim.x + s, nthr = blockDim.x * blockDim.y;
-    if (dense) {
-        const R* gm = hp.mat + (size_t)rhs * 2 * Ls * Ls;
-        for (int i = tid; i < 2 * Ls * Ls; i += nthr) mat[i] = gm[i];
-    }
-    const long long site = sblk * blockDim.y + ly;
-    const bool active = site < hp.g.Vh;
-    const long long rbase = (long long)rhs * hp.g.Vh;
-    const R mass = hp.mass[rhs];
-    R gown = hp.gown, gfac = hp.gfac, gpre = R(1);
-    if (GATHER && hp.gs) {
-        gown = hp.gs[s];
-        gfac = hp.gs[64 + s];
-        gpre = hp.gs[128 + s];
-    }
-    R acc[24];
-#pragma unroll
-    for (int k = 0; k < 24; ++k) acc[k] = 0;
-    if constexpr (STAGE == 2) {
-        // the buffers alias the rows of the epilogue (used after a barrier)
-        Bulk<P> bk;
-        bk.Ls = Ls;
-        bk.SB = blockDim.y;
-        if constexpr (P == MDWF_F32) {
-            bk.buf = reinterpret_cast<float4*>(hs);
-        } else {
-            bk.buf = reinterpret_cast<uint2*>(hs);
-            bk.nrm = reinterpret_cast<float*>(bk.buf + (size_t)2 * blockDim.y * 6 * Ls);
-        }
-        hop_bulk<P, DAG>(acc, in, U, hp, bk, bars, active, site, s, ly, tid, rbase);
-    } else if (active) {
-        const int4* nb = hp.nbr + ((long long)hp.out_parity * hp.g.Vh + site) * 2;
-        const int4 f = __ldg(nb), b = __ldg(nb + 1);
-        if constexpr (STAGE == 1) {
-            // the staging buffers alias the rows of the epilogue (used after a barrier)
-            Stager<P> st;
-            if constexpr (P == MDWF_F32) {
-                st.buf = reinterpret_cast<float4*>(hs);
-            } else {
-                st.buf = reinterpret_cast<uint2*>(hs);
-                st.nrm = reinterpret_cast<float*>(st.buf + 2 * 6 * nthr);
-            }
-            st.nthr = nthr;
-            st.tid = tid;
-            hop_staged<P, DAG>(acc, in, U, hp, st, f, b, site, s, rbase);
-        } else {
-            hop_dir<P, 0, GATHER, DAG>(acc, in, U, hp, f.x, b.x, site, s, rbase, mass, gown, gfac);
-            hop_dir<P, 1, GATHER, DAG>(acc, in, U, hp, f.y, b.y, site, s, rbase, mass, gown, gfac);
-            hop_dir<P, 2, GATHER, DAG>(acc, in, U, hp, f.z, b.z, site, s, rbase, mass, gown, gfac);
-            hop_dir<P, 3, GATHER, DAG>(acc, in, U, hp, f.w, b.w, site, s, rbase, mass, gown, gfac);
-        }
-    }
-    if constexpr (STAGE != 0) __syncthreads();
-    if (GATHER && hp.gs) {
-#pragma unroll
-        for (int k = 0; k < 24; ++k) acc[k] *= gpre;
-    }
-    const int sst = site_stride(Ls);
-    R* mine = hs + (size_t)ly * sst + s * kRowStride;
-    row_store(mine, acc);
-    __syncthreads();
-    R res[24];
-    if (dense) {
-#pragma unroll
-        for (int k = 0; k < 24; ++k) res[k] = 0;
-        const R* col = hs + (size_t)ly * sst;
-        for (int sp = 0; sp < Ls; ++sp) {
-            const R mp = mat[sp * Ls + s];         // (s, s') of the P+ matrix
-            const R mm = mat[(Ls + sp) * Ls + s];  // (s, s') of the P- matrix
-            const R* h = col + sp * kRowStride;
-#pragma unroll
-            for (int k = 0; k < 12; ++k) res[k] += mp * h[k];
-#pragma unroll
-            for (int k = 12; k < 24; ++k) res[k] += mm * h[k];
-        }
-    } else {
-        block_columns(hs, blockDim.y, Ls, hp.sop, hp.swap != 0, hp.sc, mass, tid, nthr);
-        __syncthreads();
-        row_load(mine, res);
-    }
-    if (FUSE == FUSE_NONE && !active) return;
-    const R cf = hp.coef * hp.gscale;
-#pragma unroll
-    for (int k = 0; k < 24; ++k) res[k] *= cf;
-    if (XPAY && active) {
-        R xv[24];
-        xf.load(rbase + site, s, xv);
-#pragma unroll
-        for (int k = 0; k < 24; ++k) res[k] += xv[k];
-    }
-    if (FUSE == FUSE_NONE) {
-        out.store(rbase + site, s, res);
-        return;
-    }
-    double sq = 0;
-    if (FUSE == FUSE_T) {
-        if (active) {
-            out.store(rbase + site, s, res);
-#pragma unroll
-            for (int k = 0; k < 24; ++k) sq += (double)res[k] * (double)res[k];
-        }
-        // v = A^dag t through the same column machinery
-        __syncthreads();
-        if (!active) {
-#pragma unroll
-            for (int k = 0; k < 24; ++k) res[k] = R(0);
-        }
-        row_store(mine, res);
-        __syncthreads();
-        block_columns(hs, blockDim.y, Ls, SOP_A, true, hp.sc, mass, tid, nthr);
-        __syncthreads();
-        if (active) {
-            row_load(mine, res);
-            fa.out2.store(rbase + site, s, res);
-        }
-    } else {  // FUSE_R
-        typedef typename PrecTraits<ResPrec<P>::value>::real RR;
-        const bool live = fa.sc[5 * 64 + rhs] != 0.0;
-        if (active && live) {
-            const RR alpha = (RR)fa.sc[2 * 64 + rhs];
-            RR rv[24];
-            fa.rf.load(rbase + site, s, rv);
-#pragma unroll
-            for (int k = 0; k < 24; ++k) {
-                rv[k] -= alpha * (RR)res[k];
-                sq += (double)rv[k] * (double)rv[k];
-            }
-            fa.rf.store(rbase + site, s, rv);
-        }
-    }
-    const double tot = block_sum128(sq, red);
-    if (tid == 0) fa.part[(size_t)rhs * (gridDim.x / hp.nrhs) + sblk] = tot;
-}
-
-// ---------------------------------------------------------------- launcher
+template <int P> int launch_hop_t(mdwf_ctx* c, const HopLaunch& h);
 
 // 4d sites per block: the autotuned value for (precision, nrhs) if there is
 // one, else as many whole s-columns as fit 128 threads.
@@ -675,125 +21,6 @@ int hop_sites_per_block(const mdwf_ctx* c, int prec, int nrhs) {
 int hop_blocks(const mdwf_ctx* c, int prec, int nrhs) {
     const int SB = hop_sites_per_block(c, prec, nrhs);
     return (int)((c->g.Vh + SB - 1) / SB);
-}
-
-template <int P, bool G, bool D, bool X, int FU, int ST>
-static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<typename PrecTraits<P>::real>& hp) {
-    typedef typename PrecTraits<P>::real R;
-    const Geom& g = c->g;
-    const int SB = hop_sites_per_block(c, P, h.nrhs);
-    dim3 block(g.Ls, SB), grid((unsigned)((g.Vh + SB - 1) / SB * h.nrhs));
-    const size_t rows = (size_t)SB * site_stride(g.Ls) * sizeof(R);
-    const size_t stage = ST == 1 ? (size_t)StageBytes<P>::value * g.Ls * SB
-                         : ST == 2 ? (size_t)2 * BulkBytes<P>::value * g.Ls * SB : 0;
-    size_t smem = kHopHeader + (size_t)(hp.sop == SOP_DENSE ? 2 * g.Ls * g.Ls : 0) * sizeof(R) +
-                  (rows > stage ? rows : stage);
-    auto kern = hop_kernel<P, G, D, X, FU, ST>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_status(e);
-    }
-    if (ST != 0) {
-        // the staging buffers need shared memory for every resident block (once per device)
-        // (contexts on other host threads may launch at the same time: the mask is atomic, and
-        // setting the attribute twice is harmless)
-        static std::atomic<unsigned long long> carved{0};
-        if (c->device < 64 && !(carved.load() >> c->device & 1ull)) {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                                 (int)cudaSharedmemCarveoutMaxShared);
-            if (e != cudaSuccess) return cuda_status(e);
-            carved.fetch_or(1ull << c->device);
-        }
-    }
-    Field<P> out = make_field<P>(h.out, g, h.nrhs);
-    Field<P> in = make_field<P>(const_cast<void*>(h.in), g, h.nrhs);
-    Field<P> xf = h.x ? make_field<P>(const_cast<void*>(h.x), g, h.nrhs) : out;
-    FuseArgs<P> fa;
-    fa.out2 = make_field<P>(h.out2 ? h.out2 : h.out, g, h.nrhs);
-    fa.rf = make_field<ResPrec<P>::value>(h.rfield ? h.rfield : h.out, g, h.nrhs);
-    fa.part = h.part;
-    fa.sc = h.sc;
-    Gauge<P> U;
-    U.u = reinterpret_cast<decltype(U.u)>(c->gauge[link_copy(P)]);
-    const int base = D ? (X ? KB_HOP_DAG_XPAY : KB_HOP_DAG)
-                       : G ? (X ? KB_HOP_GATHER_XPAY : KB_HOP_GATHER) : (X ? KB_HOP_XPAY : KB_HOP);
-    const double n5 = (double)g.Vh * g.Ls * h.nrhs;
-    // fields moved: in, out (+x), and for the fused epilogues v (FUSE_T) or r read+write instead of out (FUSE_R)
-    const double sp = site_bytes(P), sr = site_bytes(ResPrec<P>::value);
-    double fields = sp + sp + (X ? sp : 0.0);
-    if (FU == FUSE_T) fields += sp;
-    if (FU == FUSE_R) fields += 2.0 * sr - sp;
-    const double bytes = n5 * fields + 8.0 * g.Vh * link_bytes(P);
-    const double flops = n5 * (1320.0 + (G ? 72.0 : 0.0) + 144.0 + (X ? 48.0 : 0.0) + (FU ? 144.0 : 0.0));
-    LaunchScope scope(c, base * 3 + P, bytes, flops);
-    kern<<<grid, block, smem, c->stream>>>(out, in, xf, U, hp, fa);
-    return check_launch();
-}
-
-// The staged variant where it exists (FP32 and FP16 operators without the
-// input gather) and the context asks for it, else the plain one.
-template <int P, bool G, bool D, bool X, int FU>
-static int launch_hop_pick(mdwf_ctx* c, const HopLaunch& h, const HopParams<typename PrecTraits<P>::real>& hp) {
-    if constexpr (!G && P != MDWF_F64) {
-        if (c->hop_stage[P] == 1) return launch_hop_variant<P, G, D, X, FU, 1>(c, h, hp);
-        if (c->hop_stage[P] == 2) return launch_hop_variant<P, G, D, X, FU, 2>(c, h, hp);
-    }
-    return launch_hop_variant<P, G, D, X, FU, 0>(c, h, hp);
-}
-
-template <int P>
-static int launch_hop_t(mdwf_ctx* c, const HopLaunch& h) {
-    typedef typename PrecTraits<P>::real R;
-    HopParams<R> hp;
-    hp.g = c->g;
-    hp.nrhs = h.nrhs;
-    hp.out_parity = h.out_parity;
-    hp.coef = (R)h.coef;
-    // M_phi = b5 + c5 C folded as b5 (1 + (c5/b5) C) when b5 != 0
-    if (h.b5 != 0.0) {
-        hp.gown = R(1); hp.gfac = (R)(h.c5 / h.b5); hp.gscale = (R)h.b5;
-    } else {
-        hp.gown = R(0); hp.gfac = (R)h.c5; hp.gscale = R(1);
-    }
-    if (!h.gather) { hp.gown = R(1); hp.gfac = R(0); hp.gscale = R(1); }
-    hp.gs = nullptr;
-    if (h.gather && c->sdep) {
-        hp.gown = R(1); hp.gfac = R(0); hp.gscale = R(1);
-        hp.gs = P == MDWF_F64 ? reinterpret_cast<const R*>(c->gs64) : reinterpret_cast<const R*>(c->gs32);
-        if (h.sop != SOP_DENSE || !hp.gs) return MDWF_EINVAL;
-    }
-    hp.mass = reinterpret_cast<const R*>(h.mass);
-    hp.mat = reinterpret_cast<const R*>(h.mat);
-    hp.nbr = reinterpret_cast<const int4*>(c->nbr);
-    hp.sop = h.sop;
-    hp.swap = h.swap;
-    hp.sc.b5 = (R)c->b5;
-    hp.sc.c5 = (R)c->c5;
-    hp.sc.Mp = (R)(c->b5 * (4.0 - c->M5) + 1.0);
-    hp.sc.Mm = (R)(c->c5 * (4.0 - c->M5) - 1.0);
-    // the adjoint's hopping matrix is transposed: the two factors exchange
-    hp.chem = c->chem != 0.0;
-    hp.efwd = (R)exp(h.dagger ? -c->chem : c->chem);
-    hp.ebwd = (R)exp(h.dagger ? c->chem : -c->chem);
-    hp.err = c->dev_err;
-    const bool X = h.x != nullptr;
-    if (h.fuse != FUSE_NONE) {
-        // fused CG epilogues: t = M p with v = A^dag t, or Ap = M^dag t folded into r
-        if (h.sop == SOP_DENSE || !X || h.gather || !h.part || !h.sc) return MDWF_EINVAL;
-        if (h.fuse == FUSE_T && !h.dagger && h.out2) return launch_hop_pick<P, false, false, true, FUSE_T>(c, h, hp);
-        if (h.fuse == FUSE_R && h.dagger && h.rfield) return launch_hop_pick<P, false, true, true, FUSE_R>(c, h, hp);
-        return MDWF_EINVAL;
-    }
-    if (h.gather) {
-        if (h.dagger) return MDWF_EINVAL;
-        return X ? launch_hop_pick<P, true, false, true, FUSE_NONE>(c, h, hp)
-                 : launch_hop_pick<P, true, false, false, FUSE_NONE>(c, h, hp);
-    }
-    if (h.dagger)
-        return X ? launch_hop_pick<P, false, true, true, FUSE_NONE>(c, h, hp)
-                 : launch_hop_pick<P, false, true, false, FUSE_NONE>(c, h, hp);
-    return X ? launch_hop_pick<P, false, false, true, FUSE_NONE>(c, h, hp)
-             : launch_hop_pick<P, false, false, false, FUSE_NONE>(c, h, hp);
 }
 
 // One thread waits, bounded, on an mbarrier that expects two arrivals of

@@ -473,7 +473,11 @@ __host__ __device__ inline int site_stride(int Ls) {
 // half of the task slots and the P- components the second, each half rounded
 // up to whole warps so that a warp walks all its columns in one direction.
 // Dense tables are applied by the caller instead.
-template <typename R>
+// LSR > 0: the columns are held in registers with Ls = LSR fixed at compile
+// time (the caller guarantees Ls == LSR); LSR = -1: held in registers for
+// Ls = 8, 12, 16 (chosen at run time) when in_registers, else streamed
+// through shared memory.
+template <int LSR = -1, typename R>
 __device__ __forceinline__ void block_columns(R* hs, int SB, int Ls, int op, bool swap, const SCoef<R>& sc,
                                               R m, int tid, int nthr, bool in_registers = true) {
     const int ss = site_stride(Ls);
@@ -483,7 +487,8 @@ __device__ __forceinline__ void block_columns(R* hs, int SB, int Ls, int op, boo
         if (r >= per) continue;
         const int ly = r / 6, j = chir * 6 + (r - 6 * (r / 6));
         const bool up = (chir == 1) != swap;  // P- uses N' unless the adjoint swaps
-        if (in_registers) column_op_any(hs + (size_t)ly * ss + 2 * j, kRowStride, Ls, op, up, sc, m);
+        if constexpr (LSR > 0) column_op_reg<LSR>(hs + (size_t)ly * ss + 2 * j, kRowStride, op, up, sc, m);
+        else if (in_registers) column_op_any(hs + (size_t)ly * ss + 2 * j, kRowStride, Ls, op, up, sc, m);
         else column_op(hs + (size_t)ly * ss + 2 * j, kRowStride, Ls, op, up, sc, m);
     }
 }
