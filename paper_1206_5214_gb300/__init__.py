@@ -25,7 +25,7 @@ __all__ = [
     "mdwf_strerror", "mdwf_force", "mdwf_apply_noalloc", "mdwf_autotune", "mdwf_set_tuning",
     "mdwf_get_tuning", "mdwf_set_staging", "mdwf_get_staging", "mdwf_device_status", "mdwf_selftest_wait",
     "mdwf_profile_enable", "mdwf_profile_read", "mdwf_counters", "SolveParams", "SolveInfo", "KernelStat",
-    "MDWF_OK", "MDWF_ETIMEOUT", "STAGE_REGISTERS", "STAGE_CP_ASYNC", "STAGE_BULK",
+    "MDWF_OK", "MDWF_ETIMEOUT", "STAGE_AUTO", "STAGE_CP_ASYNC", "STAGE_BULK", "STAGE_PREFETCH", "STAGE_REGISTERS",
 ]
 
 MDWF_F64, MDWF_F32, MDWF_F16N = 0, 1, 2
@@ -373,12 +373,14 @@ def mdwf_profile_read(ctx, reset: bool = False) -> list[dict]:
              "bytes": out[i].bytes, "flops": out[i].flops} for i in range(n.value)]
 
 
-STAGE_REGISTERS, STAGE_CP_ASYNC, STAGE_BULK = 0, 1, 2
+STAGE_AUTO, STAGE_CP_ASYNC, STAGE_BULK, STAGE_PREFETCH, STAGE_REGISTERS = 0, 1, 2, 3, 4
 
 
 def mdwf_set_staging(ctx, prec: int, staged: int) -> None:
-    """Neighbour loads of the FP32 / FP16 hop kernels: 0 into registers, 1 through shared
-    memory with per-thread cp.async, 2 whole neighbour columns by bulk copies (TMA)."""
+    """Neighbour loads of the FP32 / FP16 hop kernels: 0 the default (register prefetch except
+    in the fused residual update), 1 through shared memory with per-thread cp.async, 2 whole
+    neighbour columns by bulk copies (TMA), 3 register prefetch everywhere, 4 plain register
+    loads everywhere."""
     _check(load().mdwf_set_staging(ctx, int(prec), int(staged)), "mdwf_set_staging")
 
 

@@ -708,7 +708,7 @@ int mdwf_get_tuning(const mdwf_ctx* c, int prec, int nrhs, int* sites_per_block)
 }
 
 int mdwf_set_staging(mdwf_ctx* c, int prec, int staged) {
-    if (!c || !valid_prec(prec) || staged < 0 || staged > 2) return MDWF_EINVAL;
+    if (!c || !valid_prec(prec) || staged < 0 || staged > 4) return MDWF_EINVAL;
     if (prec == MDWF_F64 && staged) return MDWF_EINVAL;
     // bulk copies of the FP16 norms need 16-byte columns (4 Ls bytes)
     if (prec == MDWF_F16N && staged == 2 && c->g.Ls % 4 != 0) return MDWF_EINVAL;

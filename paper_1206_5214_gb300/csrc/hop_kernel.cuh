@@ -298,6 +298,62 @@ __device__ __forceinline__ void hop_staged(R* acc, const Field<P>& in, const Gau
     hop_term<P, 3, false, DAG, 0>(acc, in, U, hp, st, site, b.w, -1, s, rbase);
 }
 
+// ------------------------------------------ register double buffer
+//
+// The prefetch variant (STAGE == 3) keeps two neighbour spinors in registers:
+// the load of term T + 1 is issued before term T is projected and transported,
+// so every thread has the next neighbour in flight while it computes. It
+// trades occupancy (72 registers, 7 blocks of 128 threads per SM, against 64
+// and 8 for the plain loads) for memory-level parallelism per thread.
+
+constexpr int kPrefetchMinBlocks = 7;
+
+template <int T> struct TermOf {
+    static constexpr int MU = T / 2;
+    static constexpr bool FWD = T % 2 == 0;
+    static constexpr int NB = FWD ? MU : 4 + MU;  // slot in the neighbour table
+};
+
+template <int P, int T, bool DAG, typename R>
+__device__ __forceinline__ void pf_term(R* acc, const Field<P>& in, const Gauge<P>& U, const HopParams<R>& hp,
+                                        const int* nbi, long long site, int s, long long rbase, const R* cur,
+                                        R fcur, R* nxt, R& fnxt) {
+    constexpr int MU = TermOf<T>::MU;
+    constexpr bool FWD = TermOf<T>::FWD;
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int S = FWD ? SF : -SF;
+    if constexpr (T < 7) {
+        const long long jn = __ldg(nbi + TermOf<T + 1>::NB);
+        fnxt = load_input<P, false>(in, rbase + jn, s, hp.g.Ls, R(1), R(0), R(0), nxt);
+    }
+    R h[12], u[18];
+    project<MU, S>(cur, h);
+    if constexpr (FWD) {
+        U.load(((long long)hp.out_parity * 4 + MU) * hp.g.Vh + site, u);
+    } else {
+        const long long jb = __ldg(nbi + TermOf<T>::NB);
+        U.load(((long long)(1 - hp.out_parity) * 4 + MU) * hp.g.Vh + jb, u);
+    }
+    const bool tm = MU == 3 && hp.chem;
+    transport_add<!FWD, MU, S>(acc, u, h, tm ? fcur * (FWD ? hp.efwd : hp.ebwd) : fcur, P == MDWF_F16N || tm);
+}
+
+template <int P, bool DAG, typename R>
+__device__ __forceinline__ void hop_prefetch(R* acc, const Field<P>& in, const Gauge<P>& U, const HopParams<R>& hp,
+                                             const int* nbi, long long site, int s, long long rbase) {
+    R wa[24], wb[24];
+    R fa, fb = R(1);
+    fa = load_input<P, false>(in, rbase + __ldg(nbi + TermOf<0>::NB), s, hp.g.Ls, R(1), R(0), R(0), wa);
+    pf_term<P, 0, DAG>(acc, in, U, hp, nbi, site, s, rbase, wa, fa, wb, fb);
+    pf_term<P, 1, DAG>(acc, in, U, hp, nbi, site, s, rbase, wb, fb, wa, fa);
+    pf_term<P, 2, DAG>(acc, in, U, hp, nbi, site, s, rbase, wa, fa, wb, fb);
+    pf_term<P, 3, DAG>(acc, in, U, hp, nbi, site, s, rbase, wb, fb, wa, fa);
+    pf_term<P, 4, DAG>(acc, in, U, hp, nbi, site, s, rbase, wa, fa, wb, fb);
+    pf_term<P, 5, DAG>(acc, in, U, hp, nbi, site, s, rbase, wb, fb, wa, fa);
+    pf_term<P, 6, DAG>(acc, in, U, hp, nbi, site, s, rbase, wa, fa, wb, fb);
+    pf_term<P, 7, DAG>(acc, in, U, hp, nbi, site, s, rbase, wb, fb, wa, fa);
+}
+
 // ------------------------------------------ bulk copies of neighbour columns
 //
 // The bulk variant (STAGE == 2) lets the copy engine (TMA, cp.async.bulk)
@@ -478,7 +534,9 @@ constexpr int kHopHeader = 4 * sizeof(double) + 2 * sizeof(unsigned long long);
 // fixed length leaves the other lengths' code and its register demand out of
 // the kernel.
 template <int P, bool GATHER, bool DAG, bool XPAY, int FUSE, int STAGE, int LSR>
-__global__ void __launch_bounds__(128, STAGE == 1 ? MDWF_MINB_STAGE : PrecTraits<P>::min_blocks - (GATHER ? 1 : 0))
+__global__ void __launch_bounds__(128, STAGE == 1   ? MDWF_MINB_STAGE
+                                      : STAGE == 3 ? kPrefetchMinBlocks
+                                                   : PrecTraits<P>::min_blocks - (GATHER ? 1 : 0))
     hop_kernel(Field<P> out, Field<P> in, Field<P> xf, Gauge<P> U, HopParams<typename PrecTraits<P>::real> hp,
                FuseArgs<P> fa) {
     static_assert(!STAGE || (!GATHER && P != MDWF_F64), "staged loads: FP32 / FP16 operators without gather");
@@ -525,7 +583,9 @@ __global__ void __launch_bounds__(128, STAGE == 1 ? MDWF_MINB_STAGE : PrecTraits
         hop_bulk<P, DAG>(acc, in, U, hp, bk, bars, active, site, s, ly, tid, rbase);
     } else if (active) {
         const int4* nb = hp.nbr + ((long long)hp.out_parity * hp.g.Vh + site) * 2;
-        if constexpr (STAGE == 1) {
+        if constexpr (STAGE == 3) {
+            hop_prefetch<P, DAG>(acc, in, U, hp, reinterpret_cast<const int*>(nb), site, s, rbase);
+        } else if constexpr (STAGE == 1) {
             const int4 f = __ldg(nb), b = __ldg(nb + 1);
             // the staging buffers alias the rows of the epilogue (used after a barrier)
             Stager<P> st;
@@ -546,7 +606,7 @@ __global__ void __launch_bounds__(128, STAGE == 1 ? MDWF_MINB_STAGE : PrecTraits
             hop_dir<P, 3, GATHER, DAG>(acc, in, U, hp, nbi, site, s, rbase, mass, gown, gfac);
         }
     }
-    if constexpr (STAGE != 0) __syncthreads();
+    if constexpr (STAGE == 1 || STAGE == 2) __syncthreads();
     if (GATHER && hp.gs) {
 #pragma unroll
         for (int k = 0; k < 24; ++k) acc[k] *= gpre;
@@ -646,7 +706,7 @@ static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<t
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_status(e);
     }
-    if (ST != 0) {
+    if (ST == 1 || ST == 2) {
         // the staging buffers need shared memory for every resident block (once per device)
         // (contexts on other host threads may launch at the same time: the mask is atomic, and
         // setting the attribute twice is harmless)
@@ -683,13 +743,21 @@ static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<t
     return check_launch();
 }
 
-// The staged variant where it exists (FP32 and FP16 operators without the
-// input gather) and the context asks for it, else the plain one.
+// Load strategy per launch (mdwf_set_staging). The FP32 and FP16 operators
+// without the input gather have the staged variants; by default (mode 0) they
+// prefetch the next neighbour into registers, except the FUSE_R epilogue,
+// whose residual update runs best at the occupancy of the plain loads.
+// Mode 4 uses the plain loads everywhere.
 template <int P, bool G, bool D, bool X, int FU>
 static int launch_hop_pick(mdwf_ctx* c, const HopLaunch& h, const HopParams<typename PrecTraits<P>::real>& hp) {
     if constexpr (!G && P != MDWF_F64) {
-        if (c->hop_stage[P] == 1) return launch_hop_variant<P, G, D, X, FU, 1, -1>(c, h, hp);
-        if (c->hop_stage[P] == 2) return launch_hop_variant<P, G, D, X, FU, 2, -1>(c, h, hp);
+        const int mode = c->hop_stage[P];
+        if (mode == 1) return launch_hop_variant<P, G, D, X, FU, 1, -1>(c, h, hp);
+        if (mode == 2) return launch_hop_variant<P, G, D, X, FU, 2, -1>(c, h, hp);
+        if (mode == 3 || (mode == 0 && FU != FUSE_R)) {
+            if (c->g.Ls == 16) return launch_hop_variant<P, G, D, X, FU, 3, 16>(c, h, hp);
+            return launch_hop_variant<P, G, D, X, FU, 3, -1>(c, h, hp);
+        }
     }
     // the FP32 / FP16 operators at Ls = 16 (the common length) with the
     // column length fixed at compile time

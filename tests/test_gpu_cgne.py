@@ -52,7 +52,7 @@ def gpu_solve(dims, Ls, b5, c5, mf, U, b, inner, nrhs=1, masses=None, host=False
         mdwf.mdwf_destroy(h)
 
 
-@pytest.mark.parametrize("staged", [0, 1, 2], ids=["plain", "cp.async", "bulk"])
+@pytest.mark.parametrize("staged", [0, 1, 2, 3, 4], ids=["default", "cp.async", "bulk", "prefetch", "registers"])
 @pytest.mark.parametrize("b5,c5", [(1.0, 0.0), (1.5, 0.5)], ids=["shamir", "moebius"])
 @pytest.mark.parametrize("inner", [F64, F32, F16N], ids=["f64", "mixed-f32", "mixed-f16n"])
 def test_cgne_4x4x4x4_matches_oracle_solve(b5, c5, inner, staged):

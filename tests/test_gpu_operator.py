@@ -213,13 +213,15 @@ def test_autotune_keeps_results_and_cache(tmp_path):
             check(c.apply(odd, F32)[0], ref, F32)
 
 
-@pytest.mark.parametrize("mode", [mdwf.STAGE_CP_ASYNC, mdwf.STAGE_BULK], ids=["cp.async", "bulk"])
+@pytest.mark.parametrize("mode", [mdwf.STAGE_AUTO, mdwf.STAGE_CP_ASYNC, mdwf.STAGE_BULK, mdwf.STAGE_PREFETCH],
+                         ids=["default", "cp.async", "bulk", "prefetch"])
 @pytest.mark.parametrize("prec", [F32, F16N])
 @pytest.mark.parametrize("dims,Ls", [((8, 4, 4, 4), 16), ((6, 2, 2, 4), 6), ((6, 4, 2, 2), 12), ((4, 2, 2, 6), 32)],
                          ids=["Ls16", "ragged-Ls6", "ragged-Ls12", "Ls32"])
 def test_staged_loads_match_plain(mode, prec, dims, Ls):
     """Neighbour spinors staged in shared memory (per-thread cp.async, or whole
-    columns by bulk copies) give the operator of the plain loads (the same
+    columns by bulk copies) or prefetched into a second register buffer give
+    the operator of the plain loads (the same
     arithmetic), and all match the oracle. Vh is not a multiple of the sites per
     block in the ragged cases, so the last block has idle site rows; at Ls = 12
     a site row straddles two warps."""
@@ -239,10 +241,11 @@ def test_staged_loads_match_plain(mode, prec, dims, Ls):
             assert np.abs(a - b).max() <= 1e-6 * np.abs(a).max()
             check(b, ref, prec)
         assert mdwf.mdwf_device_status(c.h) == mdwf.MDWF_OK
+        if mode != mdwf.STAGE_AUTO:
+            with pytest.raises(mdwf.MdwfError):
+                mdwf.mdwf_set_staging(c.h, F64, mode)
         with pytest.raises(mdwf.MdwfError):
-            mdwf.mdwf_set_staging(c.h, F64, mode)
-        with pytest.raises(mdwf.MdwfError):
-            mdwf.mdwf_set_staging(c.h, prec, 3)
+            mdwf.mdwf_set_staging(c.h, prec, 5)
 
 
 @pytest.mark.parametrize("arrivals", [0, 1, 2])
