@@ -40,6 +40,9 @@ FLOPS_PER_SITE = 3120.0      # per odd 5d site and M (or M^dag) application
 # a kernel that changes drops out of this table until it is captured again.
 NCU_TRAFFIC = {"hop_xpay_f32": 252.393984e6 + 171.550720e6}
 METRIC = "Moebius Dslash GFLOP/s in CGNE to 1e-10 (mixed FP32/FP64)"
+# spectrum bounds of the Zolotarev coefficients of the per-slice solve: the upper one is
+# lambda_max = (8 - M5) / (10 - M5) of the Shamir kernel at M5 = 1.8 (Sec. 2)
+ZOLO_RANGE = (0.05, 0.756)
 N5 = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2 * LS
 
 
@@ -432,6 +435,24 @@ def main() -> None:
         torch.cuda.synchronize()
         cg[name] = {"ms": e0.elapsed_time(e1), "iters": inf.iters, "reliable_updates": inf.reliable_updates,
                     "true_res": inf.true_res, "res_m": inf.res_m}
+
+    # ---------------- the same solve with per-slice (Zolotarev) b5(s), c5(s): dense s-operators
+    if not args.no_extras:
+        from paper_1206_5214_gb300 import zolotarev
+        b5s, c5s = zolotarev.zolotarev_coefficients(Ls, *ZOLO_RANGE)
+        mdwf.mdwf_set_s_coefficients(h, list(b5s), list(c5s))
+        solve(inner)  # tables and graph
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        inf = solve(inner)
+        e1.record()
+        torch.cuda.synchronize()
+        cg[f"mixed_{args.inner}_zolotarev"] = {
+            "ms": e0.elapsed_time(e1), "iters": inf.iters, "reliable_updates": inf.reliable_updates,
+            "true_res": inf.true_res, "ms_per_iter": e0.elapsed_time(e1) / max(inf.iters, 1),
+            "lambda_range": list(ZOLO_RANGE)}
+        mdwf.mdwf_set_s_coefficients(h, None, None)
 
     # ---------------- end to end through the C ABI with host buffers
     e2e = None

@@ -123,102 +123,19 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const double* part, in
     }
 }
 
-// x += alpha p; r -= alpha ap; partial |r|^2
-template <int PX, int PR, int PP>
-__global__ void __launch_bounds__(kRedThreads) k_update(Field<PX> x, Field<PR> r, Field<PP> p, Field<PP> ap,
-                                                       double* part, const double* sc, Geom g) {
-    typedef typename PrecTraits<PX>::real RX;
-    typedef typename PrecTraits<PR>::real RR;
-    typedef typename PrecTraits<PP>::real RP;
-    const int rhs = blockIdx.y;
-    double acc = 0;
-    if (SC(S_ACTIVE, rhs) != 0.0) {
-        const double alpha = SC(S_ALPHA, rhs);
-        SITE_LOOP(g) {
-            const int s = (int)(i % g.Ls);
-            const long long sr = rhs * g.Vh + i / g.Ls;
-            RX xv[24];
-            RR rv[24];
-            RP pv[24], av[24];
-            x.load(sr, s, xv);
-            r.load(sr, s, rv);
-            p.load(sr, s, pv);
-            ap.load(sr, s, av);
-#pragma unroll
-            for (int k = 0; k < 24; ++k) {
-                xv[k] += (RX)alpha * (RX)pv[k];
-                rv[k] -= (RR)alpha * (RR)av[k];
-                acc += (double)rv[k] * (double)rv[k];
-            }
-            x.store(sr, s, xv);
-            r.store(sr, s, rv);
-        }
-    }
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) part[rhs * gridDim.x + blockIdx.x] = acc;
-}
-
-// p = r + beta p
-template <int PR, int PP>
-__global__ void __launch_bounds__(kRedThreads) k_pupdate(Field<PP> p, Field<PR> r, const double* sc, Geom g) {
-    typedef typename PrecTraits<PR>::real RR;
-    typedef typename PrecTraits<PP>::real RP;
-    const int rhs = blockIdx.y;
-    if (SC(S_ACTIVE, rhs) == 0.0) return;
-    const RP beta = (RP)SC(S_BETA, rhs);
-    SITE_LOOP(g) {
-        const int s = (int)(i % g.Ls);
-        const long long sr = rhs * g.Vh + i / g.Ls;
-        RR rv[24];
-        RP pv[24];
-        r.load(sr, s, rv);
-        p.load(sr, s, pv);
-#pragma unroll
-        for (int k = 0; k < 24; ++k) pv[k] = (RP)rv[k] + beta * pv[k];
-        p.store(sr, s, pv);
-    }
-}
-
-// x += alpha p; p = r + beta p (the old p feeds both)
-template <int PX, int PR, int PP>
-__global__ void __launch_bounds__(kRedThreads) k_pupd(Field<PX> x, Field<PR> r, Field<PP> p, const double* sc,
-                                                     Geom g) {
-    typedef typename PrecTraits<PX>::real RX;
-    typedef typename PrecTraits<PR>::real RR;
-    typedef typename PrecTraits<PP>::real RP;
-    const int rhs = blockIdx.y;
-    if (SC(S_ACTIVE, rhs) == 0.0) return;
-    const double alpha = SC(S_ALPHA, rhs);
-    const RP beta = (RP)SC(S_BETA, rhs);
-    SITE_LOOP(g) {
-        const int s = (int)(i % g.Ls);
-        const long long sr = rhs * g.Vh + i / g.Ls;
-        RX xv[24];
-        RR rv[24];
-        RP pv[24];
-        x.load(sr, s, xv);
-        r.load(sr, s, rv);
-        p.load(sr, s, pv);
-#pragma unroll
-        for (int k = 0; k < 24; ++k) {
-            xv[k] += (RX)alpha * (RX)pv[k];
-            pv[k] = (RP)rv[k] + beta * pv[k];
-        }
-        x.store(sr, s, xv);
-        p.store(sr, s, pv);
-    }
-}
-
 // Column-blocked update for the fused iteration: block = (Ls, SB) threads
 // covering SB whole s-columns. x += alpha p; p = r + beta p; then
 // w = M_phi p = b5 p_s + c5 (P+ p_{s-1} + P- p_{s+1}) (mass -m on the
 // wrap-around) with the new p of the neighbouring slices taken from shared
 // memory, so that the first hop of the next iteration reads w without
-// gathering along s.
+// gathering along s. With per-slice coefficients gs holds the gather factors
+// of row s, [gown][gfac][gscale] (64 each): b5(s) = gscale gown and
+// c5(s) = gscale gfac.
 template <int PX, int PR, int PP>
 __global__ void __launch_bounds__(128) k_pupd_w(Field<PX> x, Field<PR> r, Field<PP> p, Field<PP> w,
                                                const double* sc, const typename PrecTraits<PP>::real* mass,
-                                               Geom g, double b5, double c5) {
+                                               const typename PrecTraits<PP>::real* gs, Geom g, double b5,
+                                               double c5) {
     typedef typename PrecTraits<PX>::real RX;
     typedef typename PrecTraits<PR>::real RR;
     typedef typename PrecTraits<PP>::real RP;
@@ -257,12 +174,17 @@ __global__ void __launch_bounds__(128) k_pupd_w(Field<PX> x, Field<PR> r, Field<
     if (!active) return;
     const RP m = mass[rhs];
     const int sm = s > 0 ? s - 1 : Ls - 1, sp = s < Ls - 1 ? s + 1 : 0;
-    const RP fm = (RP)c5 * (s > 0 ? RP(1) : -m), fp = (RP)c5 * (s < Ls - 1 ? RP(1) : -m);
+    RP bs = (RP)b5, cs = (RP)c5;
+    if (gs) {
+        bs = gs[128 + s] * gs[s];
+        cs = gs[128 + s] * gs[64 + s];
+    }
+    const RP fm = cs * (s > 0 ? RP(1) : -m), fp = cs * (s < Ls - 1 ? RP(1) : -m);
     RP wv[24];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) wv[k] = (RP)b5 * pv[k] + fm * row[sm * kRowStride + k];
+    for (int k = 0; k < 12; ++k) wv[k] = bs * pv[k] + fm * row[sm * kRowStride + k];
 #pragma unroll
-    for (int k = 12; k < 24; ++k) wv[k] = (RP)b5 * pv[k] + fp * row[sp * kRowStride + k];
+    for (int k = 12; k < 24; ++k) wv[k] = bs * pv[k] + fp * row[sp * kRowStride + k];
     w.store(sr, s, wv);
 }
 
@@ -408,38 +330,11 @@ void begin_capture(mdwf_ctx* c) {
 
 }  // namespace
 
-// one CG iteration on fields of operator precision PP, residual/solution precision PR
-template <int PR, int PP>
-static int cg_iteration(Solver& S, void* x, void* r, void* p, void* t, void* ap) {
-    mdwf_ctx* c = S.c;
-    int st;
-    if ((st = apply_op(c, t, p, PP, S.nrhs, 0))) return st;
-    if ((st = apply_op(c, ap, t, PP, S.nrhs, 1))) return st;
-    {
-        LaunchScope scope(c, KB_BLAS * 3 + PP, S.n5() * site_bytes(PP), S.n5() * 48.0);
-        k_norm<PP><<<S.grid(), kRedThreads, 0, c->stream>>>(make_field<PP>(t, S.g, S.nrhs), S.part, S.g, S.sc);
-    }
-    if ((st = check_launch())) return st;
-    if ((st = S.fin(FIN_ALPHA))) return st;
-    {
-    LaunchScope scope(c, KB_BLAS * 3 + PP, S.n5() * (4.0 * site_bytes(PR) + 2.0 * site_bytes(PP)), S.n5() * 144.0);
-    k_update<PR, PR, PP><<<S.grid(), kRedThreads, 0, c->stream>>>(
-        make_field<PR>(x, S.g, S.nrhs), make_field<PR>(r, S.g, S.nrhs), make_field<PP>(p, S.g, S.nrhs),
-        make_field<PP>(ap, S.g, S.nrhs), S.part, S.sc, S.g);
-    }
-    if ((st = check_launch())) return st;
-    if ((st = S.fin(FIN_BETA))) return st;
-    LaunchScope scope(c, KB_BLAS * 3 + PP, S.n5() * (site_bytes(PR) + 2.0 * site_bytes(PP)), S.n5() * 48.0);
-    k_pupdate<PR, PP><<<S.grid(), kRedThreads, 0, c->stream>>>(make_field<PP>(p, S.g, S.nrhs),
-                                                                make_field<PR>(r, S.g, S.nrhs), S.sc, S.g);
-    return check_launch();
-}
-
 struct Fields {
     // FP64: solution, right-hand side of the normal equations, residual, operator temporary
     void *xo, *src, *r, *t64;
-    // inner iteration (w = M_phi p for the fused iteration)
-    void *xs, *rs, *p, *t, *ap, *w;
+    // inner iteration (w = M_phi p, read by the first hop)
+    void *xs, *rs, *p, *t, *w;
 };
 
 template <int PR, int PP>
@@ -450,11 +345,13 @@ static int launch_pupd_w(Solver& S, void* x, void* r, void* p, void* w) {
     dim3 block(S.g.Ls, SB), grid((unsigned)((S.g.Vh + SB - 1) / SB), S.nrhs);
     const size_t smem = (size_t)SB * site_stride(S.g.Ls) * sizeof(RP);
     const RP* mass = reinterpret_cast<const RP*>(PP == MDWF_F64 ? (const void*)c->mass64 : (const void*)c->mass32);
+    const RP* gs = !c->sdep ? nullptr
+                            : reinterpret_cast<const RP*>(PP == MDWF_F64 ? (const void*)c->gs64 : (const void*)c->gs32);
     LaunchScope scope(c, KB_BLAS * 3 + PP, S.n5() * (3.0 * site_bytes(PR) + 3.0 * site_bytes(PP)), S.n5() * 144.0);
     k_pupd_w<PR, PR, PP><<<grid, block, smem, c->stream>>>(make_field<PR>(x, S.g, S.nrhs),
                                                             make_field<PR>(r, S.g, S.nrhs),
                                                             make_field<PP>(p, S.g, S.nrhs),
-                                                            make_field<PP>(w, S.g, S.nrhs), S.sc, mass, S.g,
+                                                            make_field<PP>(w, S.g, S.nrhs), S.sc, mass, gs, S.g,
                                                             c->b5, c->c5);
     return check_launch();
 }
@@ -462,14 +359,14 @@ static int launch_pupd_w(Solver& S, void* x, void* r, void* p, void* w) {
 // w = M_phi p (the fused iteration's first hop reads w)
 template <int PP>
 static int init_w(Solver& S, void* w, const void* p) {
-    if (S.c->dense_s) return MDWF_OK;
     M5Launch m{};
     m.out = w; m.in = p; m.x = nullptr; m.coef = 1.0; m.nrhs = S.nrhs;
     set_sop(S.c, PP, SOP_MPHI, 0, m);
     return launch_m5(S.c, PP, m);
 }
 
-// The same iteration with the BLAS folded into the operator kernels:
+// One CG iteration on M^dag M with the BLAS folded into the operator kernels
+// (structured s-operators or dense tables alike):
 //   z = K H_eo M_phi p;  t = p - 1/4 A H_oe z, v = A^dag t, |t|^2 (-> alpha);
 //   z = K^dag H'_eo v;   r -= alpha (t - 1/4 M_phi^dag H'_oe z), |r|^2 (-> beta);
 //   x += alpha p, p = r + beta p.
@@ -490,8 +387,15 @@ static int cg_iteration_fused(Solver& S, void* x, void* r, void* p, void* t, voi
     if ((st = launch_hop(c, PP, h))) return st;
     h.out = t; h.in = c->tmp[0].p; h.x = p; h.coef = -0.25; h.out_parity = 1; h.gather = 0; h.dagger = 0;
     set_sop(c, PP, SOP_A, 0, h);
+    h.mat2 = nullptr;
+    if (h.sop == SOP_DENSE) {  // the table of A^dag for v
+        HopLaunch a{};
+        set_sop(c, PP, SOP_A, 1, a);
+        h.mat2 = a.mat;
+    }
     h.fuse = 1; h.out2 = c->tmp[1].p; h.part = S.hpart; h.sc = S.sc;
     if ((st = launch_hop(c, PP, h))) return st;
+    h.mat2 = nullptr;
     if ((st = S.fin_hop(FIN_ALPHA))) return st;
     h.out = c->tmp[0].p; h.in = c->tmp[1].p; h.x = nullptr; h.coef = 1.0; h.out_parity = 0; h.dagger = 1;
     set_sop(c, PP, SOP_K, 1, h);
@@ -507,8 +411,7 @@ static int cg_iteration_fused(Solver& S, void* x, void* r, void* p, void* t, voi
 
 template <int PR, int PP>
 static int iterate(Solver& S, Fields& F, void* x, void* r) {
-    if (!S.c->dense_s) return cg_iteration_fused<PR, PP>(S, x, r, F.p, F.t, F.w);
-    return cg_iteration<PR, PP>(S, x, r, F.p, F.t, F.ap);
+    return cg_iteration_fused<PR, PP>(S, x, r, F.p, F.t, F.w);
 }
 
 // r = src - M^dag M x in FP64 (active rhs), r_s = r in precision PS; |r|^2 -> S_AUX.
@@ -763,12 +666,12 @@ int field_dot64(mdwf_ctx* c, const void* a, const void* b, int nrhs, double* out
 static size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
 // Bytes of the solver workspace of solve_normal: FP64 r and t64, the inner
-// fields (x_s and r_s in FP32 for a mixed solve; p, t and w, or p, t and ap for
-// the unfused iteration), CG scalars and reduction partials.
+// fields (x_s and r_s in FP32 for a mixed solve; p, t and w), CG scalars and
+// reduction partials.
 static size_t solver_bytes(const mdwf_ctx* c, int nrhs, int inner, int nb, int hb) {
     const size_t f64 = field_bytes(MDWF_F64, c->g, nrhs), f32 = field_bytes(MDWF_F32, c->g, nrhs);
     const size_t fpp = field_bytes(inner, c->g, nrhs);
-    const int inner_fields = c->dense_s ? 4 : 3;
+    const int inner_fields = 3;
     return up256(f64) * 2 +
            (inner == MDWF_F64 ? up256(f64) * inner_fields : up256(f32) * 2 + up256(fpp) * inner_fields) +
            up256(sizeof(double) * S_NUM * kMaxRhs) + up256(sizeof(double) * nrhs * nb) +
@@ -810,7 +713,6 @@ int solve_normal(mdwf_ctx* c, int nrhs, void* xo, const void* src, const mdwf_so
         if ((st = tune_hop(c, MDWF_F64, nrhs, &sb))) return st;
     }
     const int hb = hop_blocks(c, inner, nrhs);
-    // the fused iteration (structured s-operators) needs no separate M^dag M p field
     const size_t need = solver_bytes(c, nrhs, inner, nb, hb);
     Fields F{};
     Solver S{};
@@ -829,8 +731,7 @@ int solve_normal(mdwf_ctx* c, int nrhs, void* xo, const void* src, const mdwf_so
         const size_t fi = inner == MDWF_F64 ? f64 : fpp;
         if (inner != MDWF_F64) { F.xs = take(f32); F.rs = take(f32); }
         F.p = take(fi); F.t = take(fi);
-        // unfused iteration: ap = M^dag M p; fused: w = M_phi p
-        if (c->dense_s) F.ap = take(fi); else F.w = take(fi);
+        F.w = take(fi);  // w = M_phi p
         S.c = c; S.g = g; S.nrhs = nrhs; S.nb = nb;
         S.sc = (double*)take(sizeof(double) * S_NUM * kMaxRhs);
         S.part = (double*)take(sizeof(double) * nrhs * nb);

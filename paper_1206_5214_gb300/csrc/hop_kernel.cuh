@@ -41,6 +41,7 @@ template <typename R> struct HopParams {
     const R* gs;
     const R* mass;   // [rhs]
     const R* mat;    // dense tables [rhs][chir][s'][s] (sop == SOP_DENSE)
+    const R* mat2;   // dense A^dag tables of the FUSE_T epilogue, same layout
     const int4* nbr; // [parity][site][2] = cb index of x+mu (mu = 0..3), then of x-mu
     int sop, swap;
     SCoef<R> sc;
@@ -497,6 +498,23 @@ __device__ __forceinline__ void hop_bulk(R* acc, const Field<P>& in, const Gauge
 //            residual field (precision PR) and the partial |r|^2 goes to part
 enum { FUSE_NONE = 0, FUSE_T = 1, FUSE_R = 2 };
 
+// res = Mat col for the thread's slice s: Mat is the [chir][s'][s] table of one
+// right-hand side in shared memory, col the block row of the thread's site.
+template <typename R>
+__device__ __forceinline__ void dense_columns(const R* mat, const R* col, int s, int Ls, R* res) {
+#pragma unroll
+    for (int k = 0; k < 24; ++k) res[k] = 0;
+    for (int sp = 0; sp < Ls; ++sp) {
+        const R mp = mat[sp * Ls + s];         // (s, s') of the P+ matrix
+        const R mm = mat[(Ls + sp) * Ls + s];  // (s, s') of the P- matrix
+        const R* h = col + sp * kRowStride;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) res[k] += mp * h[k];
+#pragma unroll
+        for (int k = 12; k < 24; ++k) res[k] += mm * h[k];
+    }
+}
+
 template <int P> struct ResPrec { static constexpr int value = P == MDWF_F64 ? MDWF_F64 : MDWF_F32; };
 
 template <int P> struct FuseArgs {
@@ -547,7 +565,8 @@ __global__ void __launch_bounds__(128, STAGE == 1   ? MDWF_MINB_STAGE
     double* red = reinterpret_cast<double*>(smem_raw);          // [4] block reduction
     unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem_raw + 4 * sizeof(double));  // [2]
     R* mat = reinterpret_cast<R*>(smem_raw + kHopHeader);       // [chir][s'][s] (dense only)
-    R* hs = mat + (dense ? 2 * Ls * Ls : 0);                      // [SB][site_stride], rows of kRowStride
+    R* mat2 = mat + (dense ? 2 * Ls * Ls : 0);                    // A^dag (dense FUSE_T only)
+    R* hs = mat2 + (dense && FUSE == FUSE_T ? 2 * Ls * Ls : 0);   // [SB][site_stride], rows of kRowStride
     const int s = threadIdx.x, ly = threadIdx.y;
     const int rhs = blockIdx.x % hp.nrhs;
     const long long sblk = blockIdx.x / hp.nrhs;
@@ -555,6 +574,10 @@ __global__ void __launch_bounds__(128, STAGE == 1   ? MDWF_MINB_STAGE
     if (dense) {
         const R* gm = hp.mat + (size_t)rhs * 2 * Ls * Ls;
         for (int i = tid; i < 2 * Ls * Ls; i += nthr) mat[i] = gm[i];
+        if (FUSE == FUSE_T) {
+            const R* gm2 = hp.mat2 + (size_t)rhs * 2 * Ls * Ls;
+            for (int i = tid; i < 2 * Ls * Ls; i += nthr) mat2[i] = gm2[i];
+        }
     }
     const long long site = sblk * blockDim.y + ly;
     const bool active = site < hp.g.Vh;
@@ -617,18 +640,7 @@ __global__ void __launch_bounds__(128, STAGE == 1   ? MDWF_MINB_STAGE
     __syncthreads();
     R res[24];
     if (dense) {
-#pragma unroll
-        for (int k = 0; k < 24; ++k) res[k] = 0;
-        const R* col = hs + (size_t)ly * sst;
-        for (int sp = 0; sp < Ls; ++sp) {
-            const R mp = mat[sp * Ls + s];         // (s, s') of the P+ matrix
-            const R mm = mat[(Ls + sp) * Ls + s];  // (s, s') of the P- matrix
-            const R* h = col + sp * kRowStride;
-#pragma unroll
-            for (int k = 0; k < 12; ++k) res[k] += mp * h[k];
-#pragma unroll
-            for (int k = 12; k < 24; ++k) res[k] += mm * h[k];
-        }
+        dense_columns(mat, hs + (size_t)ly * sst, s, Ls, res);
     } else {
         block_columns<LSR>(hs, blockDim.y, Ls, hp.sop, hp.swap != 0, hp.sc, mass, tid, nthr);
         __syncthreads();
@@ -663,11 +675,16 @@ __global__ void __launch_bounds__(128, STAGE == 1   ? MDWF_MINB_STAGE
         }
         row_store(mine, res);
         __syncthreads();
-        block_columns<LSR>(hs, blockDim.y, Ls, SOP_A, true, hp.sc, mass, tid, nthr);
-        __syncthreads();
-        if (active) {
-            row_load(mine, res);
-            fa.out2.store(rbase + site, s, res);
+        if (dense) {
+            dense_columns(mat2, hs + (size_t)ly * sst, s, Ls, res);
+            if (active) fa.out2.store(rbase + site, s, res);
+        } else {
+            block_columns<LSR>(hs, blockDim.y, Ls, SOP_A, true, hp.sc, mass, tid, nthr);
+            __syncthreads();
+            if (active) {
+                row_load(mine, res);
+                fa.out2.store(rbase + site, s, res);
+            }
         }
     } else {  // FUSE_R
         typedef typename PrecTraits<ResPrec<P>::value>::real RR;
@@ -699,8 +716,8 @@ static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<t
     const size_t rows = (size_t)SB * site_stride(g.Ls) * sizeof(R);
     const size_t stage = ST == 1 ? (size_t)StageBytes<P>::value * g.Ls * SB
                          : ST == 2 ? (size_t)2 * BulkBytes<P>::value * g.Ls * SB : 0;
-    size_t smem = kHopHeader + (size_t)(hp.sop == SOP_DENSE ? 2 * g.Ls * g.Ls : 0) * sizeof(R) +
-                  (rows > stage ? rows : stage);
+    const int ntab = hp.sop == SOP_DENSE ? (FU == FUSE_T ? 2 : 1) : 0;
+    size_t smem = kHopHeader + (size_t)ntab * 2 * g.Ls * g.Ls * sizeof(R) + (rows > stage ? rows : stage);
     auto kern = hop_kernel<P, G, D, X, FU, ST, LSR>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -790,6 +807,7 @@ int launch_hop_t(mdwf_ctx* c, const HopLaunch& h) {
     }
     hp.mass = reinterpret_cast<const R*>(h.mass);
     hp.mat = reinterpret_cast<const R*>(h.mat);
+    hp.mat2 = reinterpret_cast<const R*>(h.mat2);
     hp.nbr = reinterpret_cast<const int4*>(c->nbr);
     hp.sop = h.sop;
     hp.swap = h.swap;
@@ -805,7 +823,9 @@ int launch_hop_t(mdwf_ctx* c, const HopLaunch& h) {
     const bool X = h.x != nullptr;
     if (h.fuse != FUSE_NONE) {
         // fused CG epilogues: t = M p with v = A^dag t, or Ap = M^dag t folded into r
-        if (h.sop == SOP_DENSE || !X || h.gather || !h.part || !h.sc) return MDWF_EINVAL;
+        // (structured s-operators or dense tables)
+        if (!X || h.gather || !h.part || !h.sc) return MDWF_EINVAL;
+        if (h.sop == SOP_DENSE && (!h.mat || (h.fuse == FUSE_T && !h.mat2))) return MDWF_EINVAL;
         if (h.fuse == FUSE_T && !h.dagger && h.out2) return launch_hop_pick<P, false, false, true, FUSE_T>(c, h, hp);
         if (h.fuse == FUSE_R && h.dagger && h.rfield) return launch_hop_pick<P, false, true, true, FUSE_R>(c, h, hp);
         return MDWF_EINVAL;

@@ -659,6 +659,7 @@ struct HopLaunch {
     int gather;           // 1: apply M_phi (b5 + c5 C) to the input column before the hop
     int dagger;           // 1: hopping term of D_W^dag (projector signs flipped)
     const void* mat;      // dense table of the output Ls x Ls matrix (sop == SOP_DENSE), per rhs
+    const void* mat2;     // dense table of A^dag for the FUSE_T epilogue (sop == SOP_DENSE)
     int sop;              // output s-operator (SOp)
     int swap;             // 1: the adjoint (chirality-swapped) s-operator
     const void* mass;     // per-rhs masses (double for F64, float otherwise)

@@ -118,7 +118,7 @@ def test_multi_mass_per_slice(prec):
                 check(got[r], oracle.m(odd[r], U, p, dagger=dagger), prec)
 
 
-@pytest.mark.parametrize("inner", [F64, F32], ids=["f64", "mixed-f32"])
+@pytest.mark.parametrize("inner", [F64, F32, F16N], ids=["f64", "mixed-f32", "mixed-f16n"])
 def test_cgne_per_slice(inner):
     """prepare -> CGNE -> reconstruct to 1e-10 with the cosine profile; the
     oracle checks the normal-equation and the first-order residuals."""
@@ -177,3 +177,52 @@ def test_apply_parity_full_16x16x16x32_per_slice():
             ref = oracle.m(odd, U, p, dagger=d)
             for prec in (F64, F32):
                 check(c.apply(odd, prec, d)[0], ref, prec)
+
+
+def test_cgne_multi_mass_per_slice():
+    """Three masses in one mixed FP32 solve with per-slice coefficients: the fused
+    iteration with one dense table per right-hand side; each solution against the
+    oracle's residuals at its own mass."""
+    dims, Ls = (4, 4, 2, 4), 8
+    prof = generic_profile(Ls, 9)
+    masses = [0.01, 0.04, 0.2]
+    U = sy.gauge_field(dims, 0.3, 1045)
+    b = sy.gaussian_field(dims, Ls, 2045, nrhs=3)
+    h = mdwf.mdwf_create(dims, Ls, 1.8, 1.5, 0.5, 0.01)
+    try:
+        mdwf.mdwf_set_s_coefficients(h, *prof)
+        mdwf.mdwf_load_gauge(h, torch.from_numpy(U).cuda())
+        bb = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+        x = torch.zeros_like(bb)
+        st, info = mdwf.mdwf_cgne(h, x, bb, nrhs=3, mf_per_rhs=masses, tol=1e-10, inner_prec=F32)
+        assert st == 0 and all(i.true_res <= 1e-10 for i in info)
+        xs = x.cpu().numpy()
+    finally:
+        mdwf.mdwf_destroy(h)
+    for r, m in enumerate(masses):
+        p = oracle.Params(dims, Ls, 1.8, 1.5, 0.5, m, b5s=tuple(prof[0]), c5s=tuple(prof[1]))
+        res = b[r] - oracle.ddw(xs[r], U, p)
+        assert np.linalg.norm(res) / np.linalg.norm(b[r]) <= 1e-7, r
+
+
+@pytest.mark.parametrize("inner", [F64, F32], ids=["f64", "mixed-f32"])
+def test_cgne_dense_tables_match_structured(inner):
+    """Constant coefficients with the s-operators as dense tables (dense_s) give the
+    solve of the structured recursion (the fused iteration with dense epilogues)."""
+    dims, Ls = (4, 4, 4, 4), 8
+    U = sy.gauge_field(dims, 0.3, 1046)
+    b = sy.gaussian_field(dims, Ls, 2046)
+    out = []
+    for dense in (False, True):
+        h = mdwf.mdwf_create(dims, Ls, 1.8, 1.5, 0.5, 0.02, dense_s=dense)
+        try:
+            mdwf.mdwf_load_gauge(h, torch.from_numpy(U).cuda())
+            bb = torch.from_numpy(b).cuda()
+            x = torch.zeros_like(bb)
+            st, info = mdwf.mdwf_cgne(h, x, bb, tol=1e-11, inner_prec=inner)
+            assert st == 0 and info[0].true_res <= 1e-11
+            out.append(x.cpu().numpy())
+        finally:
+            mdwf.mdwf_destroy(h)
+    # both stop at 1e-11 in M^dag M: the iterates agree to about cond(M^dag M) x 1e-11
+    assert np.linalg.norm(out[0] - out[1]) <= 1e-6 * np.linalg.norm(out[0])
