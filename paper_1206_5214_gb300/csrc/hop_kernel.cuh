@@ -541,6 +541,11 @@ __device__ __forceinline__ double block_sum128(double v, double* red) {
 // the dense tables and the rows / staging buffers
 constexpr int kHopHeader = 4 * sizeof(double) + 2 * sizeof(unsigned long long);
 
+#ifndef MDWF_EPILOGUE_PREFETCH
+#define MDWF_EPILOGUE_PREFETCH 1
+#endif
+constexpr bool kEpiloguePrefetch = MDWF_EPILOGUE_PREFETCH != 0;
+
 #ifndef MDWF_MINB_STAGE
 #define MDWF_MINB_STAGE 6
 #endif
@@ -630,6 +635,12 @@ __global__ void __launch_bounds__(128, STAGE == 1   ? MDWF_MINB_STAGE
         }
     }
     if constexpr (STAGE == 1 || STAGE == 2) __syncthreads();
+    // the epilogue's own operands (xpay addend, residual) are fetched into L1
+    // while the s-operator runs on the shared-memory rows
+    if (active && kEpiloguePrefetch) {
+        if constexpr (XPAY) xf.prefetch(rbase + site, s);
+        if constexpr (FUSE == FUSE_R) fa.rf.prefetch(rbase + site, s);
+    }
     if (GATHER && hp.gs) {
 #pragma unroll
         for (int k = 0; k < 24; ++k) acc[k] *= gpre;

@@ -87,7 +87,13 @@ inline size_t field_bytes(int prec, const Geom& g, int nrhs) {
     return 0;
 }
 
+// Cache hint: fetch the line of p into L1 (no register is written).
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+    asm volatile("prefetch.global.L1 [%0];\n" ::"l"(p));
+}
+
 // Device view of an internal field. `sr` below is rhs * Vh + site.
+// prefetch(sr, s) asks L1 for the lines that load(sr, s) will read.
 template <int P> struct Field;
 
 template <> struct Field<MDWF_F64> {
@@ -111,6 +117,11 @@ template <> struct Field<MDWF_F64> {
             o[2 * k] = d.x;
             o[2 * k + 1] = d.y;
         }
+    }
+    __device__ __forceinline__ void prefetch(long long sr, int s) const {
+        const double2* p = v + sr * 12 * Ls + s;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) prefetch_l1(p + (long long)k * Ls);
     }
     __device__ __forceinline__ void store(long long sr, int s, const double* i) const {
         double2* p = v + sr * 12 * Ls + s;
@@ -137,6 +148,11 @@ template <> struct Field<MDWF_F32> {
             float4 d = __ldg(p + (long long)k * Ls);
             o[4 * k] = d.x; o[4 * k + 1] = d.y; o[4 * k + 2] = d.z; o[4 * k + 3] = d.w;
         }
+    }
+    __device__ __forceinline__ void prefetch(long long sr, int s) const {
+        const float4* p = v + sr * 6 * Ls + s;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) prefetch_l1(p + (long long)k * Ls);
     }
     __device__ __forceinline__ void store(long long sr, int s, const float* i) const {
         float4* p = v + sr * 6 * Ls + s;
@@ -181,6 +197,12 @@ template <> struct Field<MDWF_F16N> {
         float nrm = __ldg(norm + sr * Ls + s);
 #pragma unroll
         for (int k = 0; k < 3; ++k) unpack(__ldg(p + (long long)k * Ls), nrm, o + 4 * k);
+    }
+    __device__ __forceinline__ void prefetch(long long sr, int s) const {
+        const uint2* p = v + sr * 6 * Ls + s;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) prefetch_l1(p + (long long)k * Ls);
+        prefetch_l1(norm + sr * Ls + s);
     }
     __device__ __forceinline__ void store(long long sr, int s, const float* i) const {
         float mx = 0.f;
