@@ -284,9 +284,16 @@ int apply_op(mdwf_ctx* c, void* out, const void* in, int prec, int nrhs, int dag
     h.c5 = c->c5;
     h.mass = mass;
     if (!dagger) {
-        // z_e = K H_eo (M_phi psi_o)
-        h.out = c->tmp[0].p; h.in = in; h.x = nullptr; h.coef = 1.0; h.out_parity = 0;
-        h.gather = 1; h.dagger = 0;
+        // w_o = M_phi psi_o by one site-local pass, so that the first hop loads w
+        // without the gather along s (and the FP32 / FP16 hops can prefetch)
+        M5Launch m{};
+        m.out = c->tmp[1].p; m.in = in; m.x = nullptr; m.coef = 1.0; m.nrhs = nrhs;
+        set_sop(c, prec, SOP_MPHI, 0, m);
+        offset_rhs(c, prec, rhs0, m);
+        if ((st = launch_m5(c, prec, m))) return st;
+        // z_e = K H_eo w_o
+        h.out = c->tmp[0].p; h.in = c->tmp[1].p; h.x = nullptr; h.coef = 1.0; h.out_parity = 0;
+        h.gather = 0; h.dagger = 0;
         set_sop(c, prec, SOP_K, 0, h);
         offset_rhs(c, prec, rhs0, h);
         if ((st = launch_hop(c, prec, h))) return st;

@@ -25,7 +25,6 @@
 
 namespace mdwf {
 
-enum { S_RR = 0, S_PAP, S_ALPHA, S_BETA, S_SRC2, S_ACTIVE, S_STATUS, S_AUX, S_ITERS, S_NUM };
 constexpr int kRedThreads = 256;
 #define SC(k, r) sc[(k) * kMaxRhs + (r)]
 
@@ -70,8 +69,6 @@ __global__ void __launch_bounds__(kRedThreads) k_norm(Field<PA> a, double* part,
     if (threadIdx.x == 0) part[rhs * gridDim.x + blockIdx.x] = acc;
 }
 
-enum { FIN_STORE = 0, FIN_ALPHA = 1, FIN_BETA = 2 };
-
 // One block of kFinThreads per right-hand side sums the nb partials in a
 // fixed order (four independent running sums per thread, so that the loads
 // of a thread are in flight together), then updates the CG scalars.
@@ -91,36 +88,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const double* part, in
     }
     for (; i < nb; i += bd) v0 += pp[i];
     double v = block_sum((v0 + v1) + (v2 + v3));
-    if (threadIdx.x != 0) return;
-    const bool active = SC(S_ACTIVE, rhs) != 0.0;
-    if (mode == FIN_STORE) {
-        SC(slot, rhs) = v;
-    } else if (mode == FIN_ALPHA) {
-        SC(S_PAP, rhs) = v;
-        double a = 0.0;
-        if (active) {
-            if (!(v > 0.0) || !isfinite(v)) {
-                SC(S_STATUS, rhs) = (double)MDWF_EBREAKDOWN;
-                SC(S_ACTIVE, rhs) = 0.0;
-            } else {
-                a = SC(S_RR, rhs) / v;
-            }
-        }
-        SC(S_ALPHA, rhs) = a;
-    } else {  // FIN_BETA: v = |r_new|^2
-        double b = 0.0;
-        if (active) {
-            if (!isfinite(v)) {
-                SC(S_STATUS, rhs) = (double)MDWF_EBREAKDOWN;
-                SC(S_ACTIVE, rhs) = 0.0;
-            } else {
-                b = v / SC(S_RR, rhs);
-                SC(S_RR, rhs) = v;
-                SC(S_ITERS, rhs) += 1.0;
-            }
-        }
-        SC(S_BETA, rhs) = b;
-    }
+    if (threadIdx.x == 0) cg_scalar_update(sc, rhs, mode, slot, v);
 }
 
 // Column-blocked update for the fused iteration: block = (Ls, SB) threads
@@ -801,6 +769,8 @@ struct RhsScratch {
 
 // b_r -> (b_e, b'_o) with b'_o = A b_o + 1/2 A H_oe M_phi (A b_e), A = I^-1
 // (the Schur decomposition, D_br = -1/2 H_oe M_phi); xe and t are scratch.
+// M_phi A b_e = K b_e is formed by the site-local pass, so the hop needs no
+// gather along s.
 int prepare_rhs(mdwf_ctx* c, const RhsScratch& w, const double* b, int where, int r) {
     const Geom& g = c->g;
     const size_t full1 = (size_t)g.Ls * 2 * g.Vh * 24 * sizeof(double);
@@ -813,15 +783,18 @@ int prepare_rhs(mdwf_ctx* c, const RhsScratch& w, const double* b, int where, in
     if ((st = launch_split_full(c, w.be, w.bp, bdev, MDWF_F64, 1))) return st;
     M5Launch m{};
     m.nrhs = 1; m.coef = 1.0; m.x = nullptr;
+    set_sop(c, MDWF_F64, SOP_K, 0, m);
+    offset_rhs(c, MDWF_F64, r, m);
+    m.out = w.xe; m.in = w.be;  // xe = K b_e = M_phi A b_e
+    if ((st = launch_m5(c, MDWF_F64, m))) return st;
+    m.mat = nullptr; m.mass = nullptr;
     set_sop(c, MDWF_F64, SOP_A, 0, m);
     offset_rhs(c, MDWF_F64, r, m);
-    m.out = w.xe; m.in = w.be;
-    if ((st = launch_m5(c, MDWF_F64, m))) return st;
-    m.out = w.t; m.in = w.bp;
+    m.out = w.t; m.in = w.bp;   // t = A b_o
     if ((st = launch_m5(c, MDWF_F64, m))) return st;
     HopLaunch h{};
     h.nrhs = 1; h.b5 = c->b5; h.c5 = c->c5; h.mass = c->mass64;
-    h.out = w.bp; h.in = w.xe; h.x = w.t; h.coef = 0.5; h.out_parity = 1; h.gather = 1; h.dagger = 0;
+    h.out = w.bp; h.in = w.xe; h.x = w.t; h.coef = 0.5; h.out_parity = 1; h.gather = 0; h.dagger = 0;
     set_sop(c, MDWF_F64, SOP_A, 0, h);
     offset_rhs(c, MDWF_F64, r, h);
     return launch_hop(c, MDWF_F64, h);
@@ -920,9 +893,16 @@ extern "C" int mdwf_cgne(mdwf_ctx* c, double* x, const double* b, int nrhs, cons
         }
         if ((st = field_dot64(c, sw.t, sw.t, 1, &rr[r]))) return st;
         if ((st = field_dot64(c, sw.bp, sw.bp, 1, &bb[r]))) return st;
+        {
+            M5Launch f{};  // xe (scratch until it is formed below) = M_phi x_o
+            f.nrhs = 1; f.out = sw.xe; f.in = xo_r; f.x = nullptr; f.coef = 1.0;
+            set_sop(c, MDWF_F64, SOP_MPHI, 0, f);
+            offset_rhs(c, MDWF_F64, r, f);
+            if ((st = launch_m5(c, MDWF_F64, f))) return st;
+        }
         HopLaunch h{};
         h.nrhs = 1; h.b5 = c->b5; h.c5 = c->c5; h.mass = c->mass64;
-        h.out = sw.t; h.in = xo_r; h.x = nullptr; h.coef = 0.5; h.out_parity = 0; h.gather = 1; h.dagger = 0;
+        h.out = sw.t; h.in = sw.xe; h.x = nullptr; h.coef = 0.5; h.out_parity = 0; h.gather = 0; h.dagger = 0;
         set_sop(c, MDWF_F64, SOP_A, 0, h);
         offset_rhs(c, MDWF_F64, r, h);
         if ((st = launch_hop(c, MDWF_F64, h))) return st;

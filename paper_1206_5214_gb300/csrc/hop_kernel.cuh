@@ -520,8 +520,8 @@ template <int P> struct ResPrec { static constexpr int value = P == MDWF_F64 ? M
 template <int P> struct FuseArgs {
     Field<P> out2;                     // FUSE_T: v = A^dag t
     Field<ResPrec<P>::value> rf;       // FUSE_R: residual r
-    double* part;                      // [rhs][blockIdx.x] partial sums
-    const double* sc;                  // CG scalars [slot][64]: alpha at slot 2, active flag at slot 5
+    double* part;                      // [rhs][blocks per rhs] partial sums
+    const double* sc;                  // CG scalars [slot][kMaxRhs]
 };
 
 __device__ __forceinline__ double block_sum128(double v, double* red) {
@@ -699,9 +699,9 @@ __global__ void __launch_bounds__(128, STAGE == 1   ? MDWF_MINB_STAGE
         }
     } else {  // FUSE_R
         typedef typename PrecTraits<ResPrec<P>::value>::real RR;
-        const bool live = fa.sc[5 * 64 + rhs] != 0.0;
+        const bool live = fa.sc[S_ACTIVE * kMaxRhs + rhs] != 0.0;
         if (active && live) {
-            const RR alpha = (RR)fa.sc[2 * 64 + rhs];
+            const RR alpha = (RR)fa.sc[S_ALPHA * kMaxRhs + rhs];
             RR rv[24];
             fa.rf.load(rbase + site, s, rv);
 #pragma unroll

@@ -50,6 +50,47 @@ struct NvtxRange {
 constexpr int kMaxLs = 32;
 constexpr int kMaxRhs = 64;  // right-hand sides per call
 
+// CG scalars per right-hand side, stored [slot][kMaxRhs] in device memory:
+// |r|^2, <p, M^dag M p>, alpha, beta, |src|^2, active flag, status, scratch,
+// iteration count.
+enum CgSlot { S_RR = 0, S_PAP, S_ALPHA, S_BETA, S_SRC2, S_ACTIVE, S_STATUS, S_AUX, S_ITERS, S_NUM };
+// What a finished reduction v does: store it in a slot, or form alpha from
+// v = <p, M^dag M p>, or beta from v = |r_new|^2 (and count the iteration).
+enum FinMode { FIN_STORE = 0, FIN_ALPHA = 1, FIN_BETA = 2 };
+
+__device__ inline void cg_scalar_update(double* sc, int rhs, int mode, int slot, double v) {
+    double* S = sc + rhs;  // S[k * kMaxRhs] is slot k of this right-hand side
+    const bool active = S[S_ACTIVE * kMaxRhs] != 0.0;
+    if (mode == FIN_STORE) {
+        S[slot * kMaxRhs] = v;
+    } else if (mode == FIN_ALPHA) {
+        S[S_PAP * kMaxRhs] = v;
+        double a = 0.0;
+        if (active) {
+            if (!(v > 0.0) || !isfinite(v)) {
+                S[S_STATUS * kMaxRhs] = (double)MDWF_EBREAKDOWN;
+                S[S_ACTIVE * kMaxRhs] = 0.0;
+            } else {
+                a = S[S_RR * kMaxRhs] / v;
+            }
+        }
+        S[S_ALPHA * kMaxRhs] = a;
+    } else {
+        double b = 0.0;
+        if (active) {
+            if (!isfinite(v)) {
+                S[S_STATUS * kMaxRhs] = (double)MDWF_EBREAKDOWN;
+                S[S_ACTIVE * kMaxRhs] = 0.0;
+            } else {
+                b = v / S[S_RR * kMaxRhs];
+                S[S_RR * kMaxRhs] = v;
+                S[S_ITERS * kMaxRhs] += 1.0;
+            }
+        }
+        S[S_BETA * kMaxRhs] = b;
+    }
+}
+
 struct Geom {
     int X, Y, Z, T, Ls;
     long long Vh;  // sites per parity

@@ -107,7 +107,11 @@ extern "C" int mdwf_apply_noalloc(mdwf_ctx* c, void* out, const void* in, int pr
     h.c5 = c->c5;
     h.mass = mass;
     if (!dagger) {
-        h.out = z; h.in = in; h.x = nullptr; h.coef = 1.0; h.out_parity = 0; h.gather = 1; h.dagger = 0;
+        M5Launch m{};  // v = M_phi psi (the first hop then needs no gather along s)
+        m.out = v; m.in = in; m.x = nullptr; m.coef = 1.0; m.nrhs = nrhs; m.mass = mass;
+        set_sop(c, prec, SOP_MPHI, 0, m);
+        if ((st = launch_m5(c, prec, m))) return st;
+        h.out = z; h.in = v; h.x = nullptr; h.coef = 1.0; h.out_parity = 0; h.gather = 0; h.dagger = 0;
         set_sop(c, prec, SOP_K, 0, h);
         if ((st = launch_hop(c, prec, h))) return st;
         h.out = out; h.in = z; h.x = in; h.coef = -0.25; h.out_parity = 1; h.gather = 0; h.dagger = 0;
