@@ -108,9 +108,10 @@ int mdwf_set_stream(mdwf_ctx *ctx, void *stream);
  * 1..Ls of the paper; copied, so the caller may free them on return. Both
  * NULL: back to the constant b5, c5 of mdwf_create.
  * While per-slice coefficients are set, every Ls x Ls factor is a dense
- * matrix (the closed form of Sec. 3 needs constant coefficients), the CG
- * iteration is the unfused one, and mdwf_force and mdwf_apply_noalloc
- * return MDWF_EINVAL. Waits for the context's stream. Errors: MDWF_EINVAL for
+ * matrix (the closed form of Sec. 3 needs constant coefficients) applied in
+ * the hop epilogues, mdwf_force returns dS/db5(s) and dS/dc5(s) per slice,
+ * and mdwf_apply_noalloc returns MDWF_EINVAL (its fixed scratch holds no
+ * dense tables). Waits for the context's stream. Errors: MDWF_EINVAL for
  * one array NULL and not the other, a non-finite value, or a singular
  * I = diag(M+(s)) + diag(M-(s)) C (the previous coefficients stay in force).
  */
@@ -121,11 +122,14 @@ int mdwf_set_s_coefficients(mdwf_ctx *ctx, const double *b5s, const double *c5s)
  * D_W carries e^{+mu} and the backward one e^{-mu} ((1 -+ g_4) U_{+-4} ->
  * e^{+-mu} (1 -+ g_4) U_{+-4}); D_W is then no longer gamma5-Hermitian and
  * every operator, solve and construction of this library uses D_W(mu) (the
- * adjoints D_W(mu)^dag). 0 turns it off. mdwf_force and mdwf_force4d return
- * MDWF_EINVAL while it is set. Errors: MDWF_EINVAL for a non-finite or
- * |mu| > 10 value.
+ * adjoints D_W(mu)^dag). 0 turns it off. The operators, solves and both
+ * forces (mdwf_force, mdwf_force4d) include it. Errors: MDWF_EINVAL for a
+ * non-finite or |mu| > 10 value.
  */
 int mdwf_set_chemical_potential(mdwf_ctx *ctx, double mu);
+
+/* The lattice of the context: dims[4] = x, y, z, t extents (host) and *Ls. */
+int mdwf_get_geometry(const mdwf_ctx *ctx, int dims[4], int *Ls);
 
 /* Writes the Ls coefficients in force to b5s, c5s (host, Ls values each) and
  * sets *per_slice to 1 when they are per-slice, 0 when constant. */
@@ -274,6 +278,8 @@ int mdwf_gw_violation(mdwf_ctx *ctx, double *out, const double *psi, int nrhs, c
  *           complex numbers, not restricted to SU(3));
  *   dSdb5, dSdc5: dS/db5 and dS/dc5 of the same S (M's dependence on b5, c5
  *           through M_phi = b5 + c5 C and I = (b5 (4 - M5) + 1) + (c5 (4 - M5) - 1) C);
+ *           with per-slice coefficients (mdwf_set_s_coefficients) each receives
+ *           Ls values, dS/db5(s) and dS/dc5(s), s = 0..Ls-1 (host memory);
  *   S     : the action.
  * phi: one odd field in the user odd format; phi and dSdU are both host or
  * both device memory (where). X = (M^dag M)^-1 phi is recomputed by the CG

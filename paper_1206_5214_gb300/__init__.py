@@ -115,6 +115,7 @@ def load(build_if_missing: bool = True):
         "mdwf_set_staging": (ip, [vp, ip, ip]),
         "mdwf_get_staging": (ip, [vp, ip, ctypes.POINTER(ctypes.c_int)]),
         "mdwf_device_status": (ip, [vp]),
+        "mdwf_get_geometry": (ip, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
         "mdwf_selftest_wait": (ip, [vp, ip]),
         "mdwf_strerror": (ctypes.c_char_p, [ip]),
         "mdwf_last_error": (ctypes.c_char_p, []),
@@ -201,6 +202,14 @@ def mdwf_set_s_coefficients(ctx, b5s, c5s) -> None:
 def mdwf_set_chemical_potential(ctx, mu: float) -> None:
     """Chemical potential on the time links (e^{+mu} forward, e^{-mu} backward); 0 turns it off."""
     _check(load().mdwf_set_chemical_potential(ctx, float(mu)), "mdwf_set_chemical_potential")
+
+
+def mdwf_get_geometry(ctx) -> tuple[tuple[int, int, int, int], int]:
+    """((x, y, z, t), Ls) of the context."""
+    d = (ctypes.c_int * 4)()
+    Ls = ctypes.c_int(0)
+    _check(load().mdwf_get_geometry(ctx, d, ctypes.byref(Ls)), "mdwf_get_geometry")
+    return tuple(d), Ls.value
 
 
 def mdwf_get_s_coefficients(ctx, Ls: int):
@@ -323,7 +332,8 @@ def mdwf_force(ctx, dSdU, phi, tol: float = 1e-12, maxiter: int = 40000, inner_p
                use_graph: bool = True, raise_on_error: bool = True):
     """S = phi^dag (M^dag M)^-1 phi, dS/dU (written into dSdU, gauge layout) and dS/db5, dS/dc5.
 
-    Returns (S, dSdb5, dSdc5, status, SolveInfo)."""
+    Returns (S, dSdb5, dSdc5, status, SolveInfo); with per-slice coefficients dSdb5 and
+    dSdc5 are arrays of Ls values (dS/db5(s), dS/dc5(s))."""
     pp, wp = _ptr_where(phi)
     if dSdU is None:
         pg = None
@@ -333,13 +343,18 @@ def mdwf_force(ctx, dSdU, phi, tol: float = 1e-12, maxiter: int = 40000, inner_p
             raise ValueError("dSdU and phi must both be host or both be device buffers")
     prm = SolveParams(float(tol), int(maxiter), int(inner_prec), 0.0, 8, int(bool(use_graph)))
     info = SolveInfo()
-    S, db5, dc5 = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+    _, Ls = mdwf_get_geometry(ctx)
+    per_slice = mdwf_get_s_coefficients(ctx, Ls)[2]
+    n = Ls if per_slice else 1
+    S, db5, dc5 = ctypes.c_double(0), (ctypes.c_double * n)(), (ctypes.c_double * n)()
     derivs = dSdU is not None
-    st = load().mdwf_force(ctx, pg, ctypes.byref(db5) if derivs else None, ctypes.byref(dc5) if derivs else None,
+    st = load().mdwf_force(ctx, pg, db5 if derivs else None, dc5 if derivs else None,
                            ctypes.byref(S), pp, wp, ctypes.byref(prm), ctypes.byref(info))
     if raise_on_error and st != 0:
         raise MdwfError(st, "mdwf_force")
-    return S.value, db5.value, dc5.value, st, info
+    if per_slice:
+        return S.value, np.array(db5[:]), np.array(dc5[:]), st, info
+    return S.value, db5[0], dc5[0], st, info
 
 
 def mdwf_force4d(ctx, dSdU, phi4, tol: float = 1e-12, maxiter: int = 40000, raise_on_error: bool = True):

@@ -546,6 +546,13 @@ int mdwf_set_chemical_potential(mdwf_ctx* c, double mu) {
     return MDWF_OK;
 }
 
+int mdwf_get_geometry(const mdwf_ctx* c, int dims[4], int* Ls) {
+    if (!c || !dims || !Ls) return MDWF_EINVAL;
+    dims[0] = c->g.X; dims[1] = c->g.Y; dims[2] = c->g.Z; dims[3] = c->g.T;
+    *Ls = c->g.Ls;
+    return MDWF_OK;
+}
+
 int mdwf_get_s_coefficients(const mdwf_ctx* c, double* b5s, double* c5s, int* per_slice) {
     if (!c || !b5s || !c5s || !per_slice) return MDWF_EINVAL;
     for (int s = 0; s < c->g.Ls; ++s) {

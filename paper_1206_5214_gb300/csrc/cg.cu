@@ -631,6 +631,69 @@ int field_dot64(mdwf_ctx* c, const void* a, const void* b, int nrhs, double* out
     return cuda_status(cudaStreamSynchronize(c->stream));
 }
 
+// Per-slice Re <a, b> of one FP64 field: block (Ls, SB) threads, a fixed grid
+// striding over the 4d sites, partials part[block][s]; then one block per
+// slice sums them in order (deterministic).
+__global__ void __launch_bounds__(128) k_dot_slices(Field<MDWF_F64> a, Field<MDWF_F64> b, double* part, Geom g) {
+    extern __shared__ double red_s[];  // [SB][Ls]
+    const int s = threadIdx.x, ly = threadIdx.y, Ls = g.Ls;
+    double v = 0;
+    for (long long site = (long long)blockIdx.x * blockDim.y + ly; site < g.Vh;
+         site += (long long)gridDim.x * blockDim.y) {
+        double x[24], y[24];
+        a.load(site, s, x);
+        b.load(site, s, y);
+#pragma unroll
+        for (int k = 0; k < 24; ++k) v += x[k] * y[k];
+    }
+    red_s[ly * Ls + s] = v;
+    __syncthreads();
+    if (ly != 0) return;
+    double t = 0;
+    for (int l = 0; l < (int)blockDim.y; ++l) t += red_s[l * Ls + s];
+    part[(size_t)blockIdx.x * Ls + s] = t;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_sum_slices(const double* part, int nb, int Ls, double* out) {
+    const int s = blockIdx.x;
+    double v = 0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) v += part[(size_t)i * Ls + s];
+    v = block_sum(v);
+    if (threadIdx.x == 0) out[s] = v;
+}
+
+int slice_dot64(mdwf_ctx* c, const void* a, const void* b, double* out_host) {
+    const Geom& g = c->g;
+    const size_t need = (size_t)kDotBlocks * g.Ls + g.Ls;
+    if (c->red_partials_len < need) {
+        cudaFree(c->red_partials);
+        c->red_partials = nullptr;
+        c->red_partials_len = 0;
+        int st = cuda_status(cudaMalloc(&c->red_partials, need * sizeof(double)));
+        if (st) return st;
+        c->red_partials_len = need;
+    }
+    const int SB = (128 / g.Ls) < 1 ? 1 : 128 / g.Ls;
+    const double n5 = (double)g.Vh * g.Ls;
+    {
+        LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, n5 * 2.0 * 192.0, n5 * 48.0);
+        k_dot_slices<<<kDotBlocks, dim3(g.Ls, SB), sizeof(double) * SB * g.Ls, c->stream>>>(
+            make_field<MDWF_F64>(const_cast<void*>(a), g, 1), make_field<MDWF_F64>(const_cast<void*>(b), g, 1),
+            c->red_partials, g);
+    }
+    int st = check_launch();
+    if (st) return st;
+    double* dout = c->red_partials + (size_t)kDotBlocks * g.Ls;
+    {
+        LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, 8.0 * kDotBlocks * g.Ls, 0.0);
+        k_sum_slices<<<g.Ls, kRedThreads, 0, c->stream>>>(c->red_partials, kDotBlocks, g.Ls, dout);
+    }
+    if ((st = check_launch())) return st;
+    if ((st = cuda_status(cudaMemcpyAsync(out_host, dout, sizeof(double) * g.Ls, cudaMemcpyDeviceToHost, c->stream))))
+        return st;
+    return cuda_status(cudaStreamSynchronize(c->stream));
+}
+
 static size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
 // Bytes of the solver workspace of solve_normal: FP64 r and t64, the inner

@@ -64,9 +64,12 @@ __device__ __forceinline__ void outer_add(double* acc, const double* p, const do
 // gauge layout [t][z][y][x][mu][3][3]. fa = field of x's parity used in the
 // forward term (gamma on even x, alpha on odd x), fb = its partner at x+mu,
 // fc = the out-parity field at x+mu of the backward term, fd = its partner at x.
+// With a chemical potential (Sec. 6.6) the time links enter the forward hop
+// with e^{+mu} and the backward hop with e^{-mu}: efwd, ebwd scale the two
+// outer products of mu = 3 (1 and 1 without).
 __global__ void __launch_bounds__(128) force_kernel(double2* dSdU, Field<MDWF_F64> fa, Field<MDWF_F64> fb,
                                                     Field<MDWF_F64> fc, Field<MDWF_F64> fd, const int4* nbr,
-                                                    Geom g, int par, double coef) {
+                                                    Geom g, int par, double coef, double efwd, double ebwd) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double* red = reinterpret_cast<double*>(smem_raw);  // [SB][Ls][18]
     const int Ls = g.Ls;
@@ -95,13 +98,18 @@ __global__ void __launch_bounds__(128) force_kernel(double2* dSdU, Field<MDWF_F6
             double b[24], cc[24], h1[12], h2[12];
             fb.load(j, s, b);
             fc.load(j, s, cc);
+            const double fw = mu == 3 ? efwd : 1.0, bw = mu == 3 ? ebwd : 1.0;
             // forward: sum (1 - g_mu) a_x (x) conj(b_{x+mu}) via the (1 - g_mu) half spinors
             proj_mu<-1>(mu, a, h1);
             proj_mu<-1>(mu, b, h2);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) h1[k] *= fw;
             outer_add(acc, h1, h2);
             // backward: [sum (1 + g_mu) c_{x+mu} (x) conj(d_x)]^dag = sum h+(d) (x) conj(h+(c))
             proj_mu<+1>(mu, cc, h1);
             proj_mu<+1>(mu, d, h2);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) h2[k] *= bw;
             outer_add(acc, h2, h1);
         }
         double* mine = red + ((size_t)ly * Ls + s) * 18;
@@ -131,19 +139,20 @@ int launch_force(mdwf_ctx* c, double* dSdU, const void* A_odd, const void* B_eve
     const int SB = (128 / g.Ls) < 1 ? 1 : 128 / g.Ls;
     dim3 block(g.Ls, SB), grid((unsigned)((g.Vh + SB - 1) / SB));
     const size_t smem = (size_t)SB * g.Ls * 18 * sizeof(double);
+    const double efwd = exp(c->chem), ebwd = exp(-c->chem);
     auto F = [&](const void* p) { return make_field<MDWF_F64>(const_cast<void*>(p), g, 1); };
     const double n5 = (double)g.Vh * g.Ls;
     int st;
     {
         LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, n5 * 192.0 * 10.0 + g.Vh * 4 * 144.0, n5 * 4 * 200.0);
         force_kernel<<<grid, block, smem, c->stream>>>((double2*)dSdU, F(C_even), F(D_odd), F(A_odd), F(B_even),
-                                                       (const int4*)c->nbr, g, 0, coef);
+                                                       (const int4*)c->nbr, g, 0, coef, efwd, ebwd);
     }
     if ((st = check_launch())) return st;
     {
         LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, n5 * 192.0 * 10.0 + g.Vh * 4 * 144.0, n5 * 4 * 200.0);
         force_kernel<<<grid, block, smem, c->stream>>>((double2*)dSdU, F(A_odd), F(B_even), F(C_even), F(D_odd),
-                                                       (const int4*)c->nbr, g, 1, coef);
+                                                       (const int4*)c->nbr, g, 1, coef, efwd, ebwd);
     }
     return check_launch();
 }
@@ -157,14 +166,6 @@ extern "C" int mdwf_force(mdwf_ctx* c, double* dSdU, double* dSdb5, double* dSdc
     NvtxRange nvtx_range("mdwf_force");
     if (!c || !phi || (where != MDWF_HOST && where != MDWF_DEVICE)) return MDWF_EINVAL;
     if (!c->have_gauge) return MDWF_ENOGAUGE;
-    if (c->sdep) {
-        set_error_message("mdwf_force supports constant b5, c5 only (per-slice coefficients are set)");
-        return MDWF_EINVAL;
-    }
-    if (c->chem != 0.0) {
-        set_error_message("the force is defined without a chemical potential");
-        return MDWF_EINVAL;
-    }
     mdwf_solve_params prm{};
     if (params) prm = *params;
     prm.guess = 0;  // the solves here start from zero
@@ -237,6 +238,44 @@ extern "C" int mdwf_force(mdwf_ctx* c, double* dSdU, double* dSdb5, double* dSdc
         if (where == MDWF_HOST &&
             (st = cuda_status(cudaMemcpyAsync(dSdU, stage_g, gb, cudaMemcpyDeviceToHost, c->stream))))
             return st;
+    }
+
+    if (!dSdb5 && !dSdc5) {
+        if ((st = cuda_status(cudaStreamSynchronize(c->stream)))) return st;
+        return res.status[0];
+    }
+    if (c->sdep) {
+        // Per slice s: b5(s) has E = w P_s, F = P_s and c5(s) has E = w P_s C,
+        // F = P_s C (P_s the projector on slice s). H_eo is diagonal in s, and
+        // gamma'^dag K E v = gamma^dag E v, so every term is a dot product
+        // restricted to slice s:
+        //   dS/db5(s) = 1/2 [-4 w <alpha, X - Y>_s + <gamma' - w gamma, v>_s + <gamma, H_eo X>_s]
+        //   dS/dc5(s) = the same with C (X - Y), C v and H_eo C X, v = A h1.
+        const int Ls = g.Ls;
+        std::vector<double> r1(Ls), r2(Ls), r3(Ls);
+        if ((st = m5(t1, Y, SOP_ID, 0, -1.0, X))) return st;       // t1 = X - Y
+        if ((st = m5(t2, h1, SOP_A, 0, 1.0, nullptr))) return st;  // t2 = v = A h1
+        if ((st = m5(t3, ga, SOP_ID, 0, -wgt, gp))) return st;     // t3 = gamma' - w gamma
+        for (int which = 0; which < 2; ++which) {
+            double* dst = which == 0 ? dSdb5 : dSdc5;
+            if (!dst) continue;
+            const void *a1 = t1, *a2 = t2, *a3 = X;
+            if (which == 1) {  // be, de are free after the link force: C (X - Y), C v, C X
+                if ((st = m5(de, t1, SOP_C, 0, 1.0, nullptr))) return st;
+                if ((st = slice_dot64(c, al, de, r1.data()))) return st;
+                if ((st = m5(de, t2, SOP_C, 0, 1.0, nullptr))) return st;
+                if ((st = slice_dot64(c, t3, de, r2.data()))) return st;
+                if ((st = m5(de, X, SOP_C, 0, 1.0, nullptr))) return st;
+                a3 = de;
+            } else {
+                if ((st = slice_dot64(c, al, a1, r1.data()))) return st;
+                if ((st = slice_dot64(c, t3, a2, r2.data()))) return st;
+            }
+            if ((st = hop(be, a3, 0, 0))) return st;  // H_eo X or H_eo C X
+            if ((st = slice_dot64(c, ga, be, r3.data()))) return st;
+            for (int k = 0; k < Ls; ++k) dst[k] = 0.5 * (-4.0 * wgt * r1[k] + r2[k] + r3[k]);
+        }
+        return res.status[0];
     }
 
     // dS/db5 (E = w 1, F = 1) and dS/dc5 (E = w C, F = C)

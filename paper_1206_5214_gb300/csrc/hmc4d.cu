@@ -65,10 +65,6 @@ extern "C" int mdwf_force4d(mdwf_ctx* c, double* dSdU, double* S_out, const doub
     if (!c || !phi || !S_out || (where != MDWF_HOST && where != MDWF_DEVICE)) return MDWF_EINVAL;
     if (!c->have_gauge) return MDWF_ENOGAUGE;
     if (c->mf == 1.0) return MDWF_EINVAL;
-    if (c->chem != 0.0) {
-        set_error_message("the force is defined without a chemical potential");
-        return MDWF_EINVAL;
-    }
     mdwf_solve_params prm{};
     if (params) prm = *params;
     prm.guess = 0;  // the solves here start from zero

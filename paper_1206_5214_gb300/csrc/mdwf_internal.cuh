@@ -783,6 +783,8 @@ struct NormalResult {
 int solve_normal(mdwf_ctx* c, int nrhs, void* xo, const void* src, const mdwf_solve_params& prm, NormalResult& res);
 // Re <a, b> of FP64 internal fields per right-hand side into host memory (synchronises)
 int field_dot64(mdwf_ctx* c, const void* a, const void* b, int nrhs, double* out_host);
+// out_host[s] = Re <a, b> restricted to slice s (one FP64 field); synchronises
+int slice_dot64(mdwf_ctx* c, const void* a, const void* b, double* out_host);
 
 // layout kernels (layout.cu)
 int launch_import_odd(mdwf_ctx* c, void* dst, const double* src_dev, int prec, int nrhs);

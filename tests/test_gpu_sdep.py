@@ -13,6 +13,7 @@ if not torch.cuda.is_available():
 import oracle
 import paper_1206_5214_gb300 as mdwf
 import synthetic as sy
+from _pins import dense_of
 from _gpu import Ctx, rel_err
 
 pytestmark = pytest.mark.gpu
@@ -148,20 +149,87 @@ def test_cgne_per_slice(inner):
     assert np.linalg.norm(r) / np.linalg.norm(b) <= 1e-7
 
 
-def test_force_and_noalloc_refuse_per_slice():
+def test_noalloc_refuses_per_slice():
     dims, Ls = (4, 4, 2, 2), 4
     U = sy.gauge_field(dims, 0.3, 1045)
     _, phi = oracle.split(sy.gaussian_field(dims, Ls, 2045), dims)
     with Ctx(dims, Ls, 1.8, 1.5, 0.5, 0.05, U) as c:
         mdwf.mdwf_set_s_coefficients(c.h, *cosine_profile(Ls))
-        G = torch.empty(U.shape, dtype=torch.complex128, device="cuda")
-        S, db, dc, st, info = mdwf.mdwf_force(c.h, G, torch.from_numpy(phi).cuda(), raise_on_error=False)
-        assert st == 1
         a = c.upload(phi, F32)
         out = c.alloc(F32)
         with pytest.raises(mdwf.MdwfError) as e:
             mdwf.mdwf_apply_noalloc(c.h, out, a, F32)
         assert e.value.status == 1
+
+
+def oracle_action(phi, U, p):
+    """S = phi^dag (M^dag M)^-1 phi with the oracle's M^dag M as a dense matrix."""
+    A = dense_of(lambda v: oracle.mdagm(v, U, p), phi.size, phi.shape)
+    return float(np.real(np.vdot(phi.reshape(-1), np.linalg.solve(A, phi.reshape(-1)))))
+
+
+def su3_direction(shape, seed):
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal(shape + (3, 3)) + 1j * rng.standard_normal(shape + (3, 3))
+    h = 0.5 * (a - np.conj(np.swapaxes(a, -1, -2)))
+    return h - np.trace(h, axis1=-2, axis2=-1)[..., None, None] / 3.0 * np.eye(3)
+
+
+def expm_ah(w):
+    lam, v = np.linalg.eigh(1j * w)
+    return np.einsum("...ij,...j,...kj->...ik", v, np.exp(-1j * lam), np.conj(v))
+
+
+def gpu_force(dims, Ls, mf, U, phi, prof):
+    with Ctx(dims, Ls, 1.8, 1.5, 0.5, mf, U) as c:
+        if prof is not None:
+            mdwf.mdwf_set_s_coefficients(c.h, *prof)
+        G = torch.empty(U.shape, dtype=torch.complex128, device="cuda")
+        S, db, dc, st, info = mdwf.mdwf_force(c.h, G, torch.from_numpy(phi).cuda(), tol=1e-13)
+        assert st == 0
+        return S, G.cpu().numpy(), db, dc
+
+
+def test_force_per_slice_against_oracle_action():
+    """4x2x2x2, Ls = 4, a generic profile: S, dS/dU along a random su(3) direction and
+    every dS/db5(s), dS/dc5(s) against central differences (h = 1e-5) of the oracle's
+    action S = phi^dag (M^dag M)^-1 phi (dense)."""
+    dims, Ls, mf = (4, 2, 2, 2), 4, 0.05
+    prof = generic_profile(Ls, 11)
+    U = sy.gauge_field(dims, 0.3, 1047)
+    _, phi = oracle.split(sy.gaussian_field(dims, Ls, 2047), dims)
+    p = oracle.Params(dims, Ls, 1.8, 1.5, 0.5, mf, b5s=tuple(prof[0]), c5s=tuple(prof[1]))
+    S, G, db, dc = gpu_force(dims, Ls, mf, U, phi, prof)
+    assert np.shape(db) == (Ls,) and np.shape(dc) == (Ls,)
+    assert S == pytest.approx(oracle_action(phi, U, p), rel=1e-10)
+    h = 1e-5
+    w = su3_direction(U.shape[:-2], 47)
+    fd = (oracle_action(phi, expm_ah(h * w) @ U, p) - oracle_action(phi, expm_ah(-h * w) @ U, p)) / (2 * h)
+    an = float(np.sum(np.real(np.conj(G) * (w @ U))))
+    assert an == pytest.approx(fd, rel=1e-6)
+    for which, got in (("b5s", db), ("c5s", dc)):
+        scale = np.abs(got).max()
+        for s in range(Ls):
+            up, dn = list(getattr(p, which)), list(getattr(p, which))
+            up[s] += h
+            dn[s] -= h
+            fd = (oracle_action(phi, U, p.with_(**{which: tuple(up)})) -
+                  oracle_action(phi, U, p.with_(**{which: tuple(dn)}))) / (2 * h)
+            assert abs(got[s] - fd) <= 1e-6 * scale, (which, s, got[s], fd)
+
+
+def test_force_per_slice_sums_to_constant_derivatives():
+    """A constant profile set per slice: dS/dU as with constant coefficients, and the
+    per-slice derivatives add up to dS/db5 and dS/dc5."""
+    dims, Ls, mf = (4, 4, 2, 2), 6, 0.05
+    U = sy.gauge_field(dims, 0.3, 1048)
+    _, phi = oracle.split(sy.gaussian_field(dims, Ls, 2048), dims)
+    S0, G0, db0, dc0 = gpu_force(dims, Ls, mf, U, phi, None)
+    S1, G1, db1, dc1 = gpu_force(dims, Ls, mf, U, phi, ([1.5] * Ls, [0.5] * Ls))
+    assert S1 == pytest.approx(S0, rel=1e-11)
+    assert np.abs(G1 - G0).max() <= 1e-9 * np.abs(G0).max()
+    assert float(np.sum(db1)) == pytest.approx(db0, rel=1e-9)
+    assert float(np.sum(dc1)) == pytest.approx(dc0, rel=1e-9)
 
 
 def test_apply_parity_full_16x16x16x32_per_slice():
