@@ -195,7 +195,7 @@ def run_reference(args) -> None:
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config("f64"),
+            "data": "synthetic", "config": workload_config(args.inner),
             "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": oracle.get_threads(), "kind": "oracle",
                              "sample": "each step: M then M^dag of the FP64 oracle on the full workload lattice"},
             "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
