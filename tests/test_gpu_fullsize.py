@@ -138,3 +138,30 @@ def test_cgne_32x32x32x64_Ls16_eight_masses_mixed_f16n(c5_links):
         normal, first = oracle_residuals(x[r], b[r], U, p)
         assert normal <= 1.05e-10, (r, normal)
         assert first <= 1e-8, (r, first)
+
+
+def test_cgne_16x16x16x32_Ls16_zolotarev_mixed_f32():
+    """The bench lattice (16^3 x 32, Ls = 16, links eps = 0.2) with per-slice Zolotarev
+    coefficients for |lambda| in [0.05, 0.756]: the fused iteration with dense
+    s-operators, mixed FP32/FP64 to 1e-10, checked through the oracle's residuals."""
+    from paper_1206_5214_gb300 import zolotarev
+    dims, Ls, mf = (16, 16, 16, 32), 16, 0.01
+    b5s, c5s = zolotarev.zolotarev_coefficients(Ls, 0.05, 0.756)
+    U = sy.gauge_field(dims, 0.2, sy.config_seed("gauge", 2))
+    b = sy.gaussian_field(dims, Ls, sy.config_seed("source", 2))
+    p = oracle.Params(dims, Ls, 1.8, 1.5, 0.5, mf, b5s=tuple(b5s), c5s=tuple(c5s))
+    h = mdwf.mdwf_create(dims, Ls, 1.8, 1.5, 0.5, mf)
+    try:
+        mdwf.mdwf_load_gauge(h, torch.from_numpy(U).cuda())
+        mdwf.mdwf_set_s_coefficients(h, list(b5s), list(c5s))
+        bd = torch.from_numpy(b).cuda()
+        xd = torch.zeros_like(bd)
+        st, info = mdwf.mdwf_cgne(h, xd, bd, tol=1e-10, inner_prec=F32)
+        x = xd.cpu().numpy()
+    finally:
+        mdwf.mdwf_destroy(h)
+    print("zolotarev", info[0].as_dict())
+    assert st == 0 and info[0].true_res <= 1e-10
+    normal, first = oracle_residuals(x, b, U, p)
+    assert normal <= 1.05e-10, normal
+    assert first <= 1e-8, first
