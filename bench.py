@@ -36,8 +36,8 @@ LS, M5, B5, C5, MF, EPS = 16, 1.8, 1.5, 0.5, 0.01, 0.2
 GAUGE_SEED, SOURCE_SEED = 1002, 2002
 FLOPS_PER_SITE = 3120.0      # per odd 5d site and M (or M^dag) application
 # DRAM bytes (read + write) per launch of a kernel in this workload's solve, from one
-# ncu capture of the kernels as they are now (profiles/hop_kernels_cgne_iteration_*);
-# a kernel that changes drops out of this table until it is captured again.
+# ncu capture of the kernels as they are now (summarised under profiles/); a kernel
+# that changes drops out of this table until it is captured again.
 NCU_TRAFFIC = {"hop_xpay_f32": 252.126720e6 + 167.469056e6}
 METRIC = "Moebius Dslash GFLOP/s in CGNE to 1e-10 (mixed FP32/FP64)"
 # spectrum bounds of the Zolotarev coefficients of the per-slice solve: the upper one is
