@@ -144,7 +144,7 @@ def gpu_identifier(torch) -> str | None:
 def cpu_baseline(dims, Ls) -> dict:
     """The FP64 oracle on this host's cores: a bounded sample of the same
     workload, six CG iterations' worth of operator work (M and M^dag six times,
-    about 10 s on the 16 cores of the GPU machine's host)."""
+    about 10 s on 16 Grace cores)."""
     import numpy as np
     import oracle
     import synthetic as sy
