@@ -12,11 +12,15 @@
 // Mat is an Ls x Ls real matrix per chirality (K = M_phi I^-1, I^-1, ...).
 //
 // Thread mapping: a block is Ls x SB threads: threadIdx.x = s, threadIdx.y =
-// one of SB 4d sites, blockIdx.y = right-hand side. The Ls threads of a
-// column load the same link (one L1 line, broadcast), so each link is read
-// from HBM once per hop and reused across all Ls slices. Spinor chunks of
-// consecutive s are contiguous, so every vector load of a warp is coalesced.
-// The s-mixing matrix is applied after the hop through shared memory.
+// one of SB 4d sites; blockIdx.x = (site block, right-hand side) with the
+// right-hand side fastest, so that the blocks running together share sites and
+// read their links from L2. The Ls threads of a column load the same link (one
+// L1 line, broadcast), so each link is read from HBM once per hop and reused
+// across all Ls slices. Spinor chunks of consecutive s are contiguous, so every
+// vector load of a warp is coalesced. The neighbour spinors are loaded into
+// registers when needed, or one term ahead into a second register buffer
+// (prefetch), or staged in shared memory (STAGE below). The s-mixing matrix is
+// applied after the hop through shared memory.
 #pragma once
 
 #include <atomic>
