@@ -502,6 +502,28 @@ __device__ __forceinline__ void hop_bulk(R* acc, const Field<P>& in, const Gauge
 //            residual field (precision PR) and the partial |r|^2 goes to part
 enum { FUSE_NONE = 0, FUSE_T = 1, FUSE_R = 2 };
 
+// The bidiagonal s-operators (M_phi = b5 + c5 C, C, I = M+ + M- C, and their
+// adjoints) for Ls = 16, where the 16 slices of a site fill one half-warp:
+// the s +- 1 neighbours of a column are lanes +- 1 of its 16-lane group, so
+// the column step needs shuffles and no shared memory. Chirality 0 (reals
+// 0..11) couples to s - 1 and chirality 1 to s + 1; the adjoint (swap)
+// exchanges them; the wrap-around term carries -m. Every lane of the warp
+// must take part.
+template <typename R>
+__device__ __forceinline__ void bidiag_shuffle16(const R* in, R* out, int s, int op, bool swap, const SCoef<R>& sc,
+                                                 R m) {
+    const R w0 = op == SOP_MPHI ? sc.b5 : op == SOP_MEE ? sc.Mp : R(0);
+    const R w1 = op == SOP_MPHI ? sc.c5 : op == SOP_MEE ? sc.Mm : R(1);
+    const int up = (s + 1) & 15, dn = (s + 15) & 15;
+    const int src0 = swap ? up : dn, src1 = swap ? dn : up;
+    const R f0 = w1 * ((swap ? s < 15 : s > 0) ? R(1) : -m);
+    const R f1 = w1 * ((swap ? s > 0 : s < 15) ? R(1) : -m);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) out[k] = w0 * in[k] + f0 * __shfl_sync(0xffffffffu, in[k], src0, 16);
+#pragma unroll
+    for (int k = 12; k < 24; ++k) out[k] = w0 * in[k] + f1 * __shfl_sync(0xffffffffu, in[k], src1, 16);
+}
+
 // res = Mat col for the thread's slice s: Mat is the [chir][s'][s] table of one
 // right-hand side in shared memory, col the block row of the thread's site.
 template <typename R>
@@ -549,6 +571,10 @@ constexpr int kHopHeader = 4 * sizeof(double) + 2 * sizeof(unsigned long long);
 #define MDWF_EPILOGUE_PREFETCH 1
 #endif
 constexpr bool kEpiloguePrefetch = MDWF_EPILOGUE_PREFETCH != 0;
+#ifndef MDWF_SHUFFLE_BIDIAG
+#define MDWF_SHUFFLE_BIDIAG 1
+#endif
+constexpr bool kShuffleBidiag = MDWF_SHUFFLE_BIDIAG != 0;
 
 #ifndef MDWF_MINB_STAGE
 #define MDWF_MINB_STAGE 6
@@ -651,15 +677,27 @@ __global__ void __launch_bounds__(128, STAGE == 1   ? MDWF_MINB_STAGE
     }
     const int sst = site_stride(Ls);
     R* mine = hs + (size_t)ly * sst + s * kRowStride;
-    row_store(mine, acc);
-    __syncthreads();
     R res[24];
-    if (dense) {
-        dense_columns(mat, hs + (size_t)ly * sst, s, Ls, res);
-    } else {
-        block_columns<LSR>(hs, blockDim.y, Ls, hp.sop, hp.swap != 0, hp.sc, mass, tid, nthr);
+    // bidiagonal operators at Ls = 16 by shuffles when every warp holds two
+    // whole columns (uniform over the block)
+    bool shuffled = false;
+    if constexpr (LSR == 16) {
+        if (kShuffleBidiag && !dense && (blockDim.y & 1) == 0 &&
+            (hp.sop == SOP_MPHI || hp.sop == SOP_C || hp.sop == SOP_MEE)) {
+            bidiag_shuffle16(acc, res, s, hp.sop, hp.swap != 0, hp.sc, mass);
+            shuffled = true;
+        }
+    }
+    if (!shuffled) {
+        row_store(mine, acc);
         __syncthreads();
-        row_load(mine, res);
+        if (dense) {
+            dense_columns(mat, hs + (size_t)ly * sst, s, Ls, res);
+        } else {
+            block_columns<LSR>(hs, blockDim.y, Ls, hp.sop, hp.swap != 0, hp.sc, mass, tid, nthr);
+            __syncthreads();
+            row_load(mine, res);
+        }
     }
     if (FUSE == FUSE_NONE && !active) return;
     const R cf = hp.coef * hp.gscale;

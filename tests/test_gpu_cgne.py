@@ -202,3 +202,16 @@ def test_cgne_nan_source_is_reported_per_rhs(inner):
     assert st == 5
     assert info[0].status == 0 and info[0].true_res <= 1e-10
     assert info[1].status == 5
+
+
+@pytest.mark.parametrize("inner", [F32, F16N], ids=["mixed-f32", "mixed-f16n"])
+def test_cgne_4x4x4x4_Ls16_matches_oracle(inner):
+    """Ls = 16 (the fused iteration's Ls-specialised kernels and the shuffled M_phi^dag of
+    its last hop) to 1e-10, checked through the oracle's residuals."""
+    dims, Ls, mf = (4, 4, 4, 4), 16, 0.01
+    U = sy.gauge_field(dims, 0.3, 1092)
+    b = sy.gaussian_field(dims, Ls, 2092)
+    p = oracle.Params(dims, Ls, 1.8, 1.5, 0.5, mf)
+    st, info, x = gpu_solve(dims, Ls, 1.5, 0.5, mf, U, b, inner)
+    assert st == 0 and info[0].true_res <= 1e-10
+    assert oracle_residual(x, b, U, p) <= 1.05e-10

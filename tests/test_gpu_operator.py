@@ -273,3 +273,23 @@ def test_apply_parity_Ls32(prec):
     with Ctx(dims, Ls, 1.8, 1.5, 0.5, 0.01, U) as c:
         for d in (False, True):
             check(c.apply(odd, prec, d)[0], oracle.m(odd, U, p, dagger=d), prec)
+
+
+@pytest.mark.parametrize("prec", [F32, F16N])
+def test_adjoint_Ls16_masses_and_block_shapes(prec):
+    """Ls = 16: the bidiagonal s-operator of M^dag runs on warp shuffles when every warp
+    holds two whole columns (an even number of sites per block) and through shared memory
+    otherwise; three masses in one launch (the wrap-around term carries each -m). Both
+    against the oracle, for 8, 2, 3 and 1 sites per block."""
+    dims, Ls = (4, 4, 2, 4), 16
+    masses = [0.01, 0.1, 0.7]
+    U = sy.gauge_field(dims, 0.3, 1091)
+    srcs = sy.gaussian_field(dims, Ls, 2091, nrhs=3)
+    odd = np.stack([oracle.split(srcs[r], dims)[1] for r in range(3)])
+    refs = [oracle.m(odd[r], U, oracle.Params(dims, Ls, 1.8, 1.5, 0.5, m), dagger=True) for r, m in enumerate(masses)]
+    with Ctx(dims, Ls, 1.8, 1.5, 0.5, 0.01, U) as c:
+        for sb in (8, 2, 3, 1):
+            mdwf.mdwf_set_tuning(c.h, prec, 3, sb)
+            got = c.apply(odd, prec, True, nrhs=3, masses=masses)
+            for r in range(3):
+                check(got[r], refs[r], prec)
