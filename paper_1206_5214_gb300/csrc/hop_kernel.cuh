@@ -701,13 +701,14 @@ __global__ void __launch_bounds__(128, STAGE == 1   ? MDWF_MINB_STAGE
     }
     if (FUSE == FUSE_NONE && !active) return;
     const R cf = hp.coef * hp.gscale;
-#pragma unroll
-    for (int k = 0; k < 24; ++k) res[k] *= cf;
-    if (XPAY && active) {
+    if (XPAY && active) {  // res = cf res + x as one fused multiply-add
         R xv[24];
         xf.load(rbase + site, s, xv);
 #pragma unroll
-        for (int k = 0; k < 24; ++k) res[k] += xv[k];
+        for (int k = 0; k < 24; ++k) res[k] = fma(cf, res[k], xv[k]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 24; ++k) res[k] *= cf;
     }
     if (FUSE == FUSE_NONE) {
         out.store(rbase + site, s, res);
