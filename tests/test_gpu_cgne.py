@@ -215,3 +215,26 @@ def test_cgne_4x4x4x4_Ls16_matches_oracle(inner):
     st, info, x = gpu_solve(dims, Ls, 1.5, 0.5, mf, U, b, inner)
     assert st == 0 and info[0].true_res <= 1e-10
     assert oracle_residual(x, b, U, p) <= 1.05e-10
+
+
+def test_cgne_max_batch():
+    """64 right-hand sides with 64 masses in one mixed FP32 solve (4x2x2x2, Ls = 4): every
+    slot reaches 1e-10 and solves D_DW(m_r) x = b_r by the oracle."""
+    dims, Ls, n = (4, 2, 2, 2), 4, 64
+    U = sy.gauge_field(dims, 0.3, 1094)
+    b = sy.gaussian_field(dims, Ls, 2094, nrhs=n)
+    masses = list(np.linspace(0.01, 0.5, n))
+    h = mdwf.mdwf_create(dims, Ls, 1.8, 1.5, 0.5, 0.01)
+    try:
+        mdwf.mdwf_load_gauge(h, torch.from_numpy(U).cuda())
+        bb = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+        x = torch.zeros_like(bb)
+        st, info = mdwf.mdwf_cgne(h, x, bb, nrhs=n, mf_per_rhs=masses, tol=1e-10, inner_prec=F32)
+        xs = x.cpu().numpy()
+    finally:
+        mdwf.mdwf_destroy(h)
+    assert st == 0 and all(i.true_res <= 1e-10 for i in info)
+    for r in range(0, n, 9):
+        p = oracle.Params(dims, Ls, 1.8, 1.5, 0.5, masses[r])
+        res = b[r] - oracle.ddw(xs[r], U, p)
+        assert np.linalg.norm(res) / np.linalg.norm(b[r]) <= 1e-7, r

@@ -65,11 +65,13 @@ def test_import_export_roundtrip(prec):
 
 # ------------------------------------------------------------- small lattice
 
-@pytest.mark.parametrize("b5,c5", [(1.0, 0.0), (1.5, 0.5), (2.5, 1.5)])
+@pytest.mark.parametrize("b5,c5", [(1.0, 0.0), (1.5, 0.5), (2.5, 1.5), (1.0, 1.0), (1.0, 3.0)],
+                         ids=["shamir", "moebius", "moebius-alpha4", "borici", "auto-dense"])
 @pytest.mark.parametrize("prec", [F64, F32, F16N])
 @pytest.mark.parametrize("dagger", [False, True])
 def test_apply_parity_4x4x4x4(b5, c5, prec, dagger):
-    """4^4 lattice, Ls = 8, mf = 0.01, eps = 0.3 (Shamir and Moebius)."""
+    """4^4 lattice, Ls = 8, mf = 0.01, eps = 0.3: Shamir, Moebius, Borici (b5 = c5) and
+    |M-/M+| > 0.9 (c5 = 3), where the context applies the s-operators as dense tables."""
     dims, Ls = (4, 4, 4, 4), 8
     U, odd, p = setup(dims, Ls, b5, c5, 0.01, 0.3, 1)
     ref = oracle.m(odd, U, p, dagger=dagger)
@@ -293,3 +295,21 @@ def test_adjoint_Ls16_masses_and_block_shapes(prec):
             got = c.apply(odd, prec, True, nrhs=3, masses=masses)
             for r in range(3):
                 check(got[r], refs[r], prec)
+
+
+def test_max_batch_of_right_hand_sides():
+    """The largest batch, 64 right-hand sides with 64 masses, in one launch (M and M^dag)
+    on a 4x2x2x2 lattice, Ls = 4: every slot against the oracle; 65 is refused."""
+    dims, Ls, n = (4, 2, 2, 2), 4, 64
+    U = sy.gauge_field(dims, 0.3, 1093)
+    srcs = sy.gaussian_field(dims, Ls, 2093, nrhs=n)
+    odd = np.stack([oracle.split(srcs[r], dims)[1] for r in range(n)])
+    masses = list(np.linspace(0.005, 0.5, n))
+    with Ctx(dims, Ls, 1.8, 1.5, 0.5, 0.01, U) as c:
+        for dagger in (False, True):
+            got = c.apply(odd, F32, dagger, nrhs=n, masses=masses)
+            for r in range(n):
+                ref = oracle.m(odd[r], U, oracle.Params(dims, Ls, 1.8, 1.5, 0.5, masses[r]), dagger=dagger)
+                check(got[r], ref, F32)
+        with pytest.raises(mdwf.MdwfError):
+            c.apply(np.concatenate([odd, odd[:1]]), F32, False, nrhs=n + 1)
