@@ -43,6 +43,8 @@ METRIC = "Moebius Dslash GFLOP/s in CGNE to 1e-10 (mixed FP32/FP64)"
 # spectrum bounds of the Zolotarev coefficients of the per-slice solve: the upper one is
 # lambda_max = (8 - M5) / (10 - M5) of the Shamir kernel at M5 = 1.8 (Sec. 2)
 ZOLO_RANGE = (0.05, 0.756)
+# the force workload: the same lattice and links, mf = 0.02, its own Gaussian phi
+FORCE_MF, FORCE_SEED = 0.02, 2004
 N5 = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2 * LS
 
 
@@ -454,6 +456,27 @@ def main() -> None:
             "lambda_range": list(ZOLO_RANGE)}
         mdwf.mdwf_set_s_coefficients(h, None, None)
 
+    # ---------------- the force on the same lattice at mf = 0.02 (dS/dU, dS/db5, dS/dc5; one solve)
+    force = None
+    if not args.no_extras:
+        # a Gaussian odd field (any field of the odd-field shape serves)
+        phi = np.ascontiguousarray(sy.gaussian_field(dims, Ls, FORCE_SEED).reshape(Ls, -1, 4, 3)[:, :Vh])
+        hf = mdwf.mdwf_create(dims, Ls, M5, B5, C5, FORCE_MF)
+        mdwf.mdwf_load_gauge(hf, Ud)
+        phid = torch.from_numpy(phi).cuda()
+        G = torch.empty(U.shape, dtype=torch.complex128, device="cuda")
+        mdwf.mdwf_force(hf, G, phid, tol=1e-10, inner_prec=inner)  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        S, db5, dc5, fst, finfo = mdwf.mdwf_force(hf, G, phid, tol=1e-10, inner_prec=inner)
+        e1.record()
+        torch.cuda.synchronize()
+        force = {"ms": e0.elapsed_time(e1), "mf": FORCE_MF, "tol": 1e-10, "inner": args.inner,
+                 "iters": finfo.iters, "true_res": finfo.true_res, "status": fst}
+        mdwf.mdwf_destroy(hf)
+        del G, phid
+
     # ---------------- end to end through the C ABI with host buffers
     e2e = None
     if not args.no_extras:
@@ -468,7 +491,7 @@ def main() -> None:
             "gpu_launches": launches1 - launches0,
             "applies_per_step": applies / args.steps,
             "roofline": roofline, "clocks": clocks.summary(), "e2e": e2e, "cpu_baseline": cpu,
-            "cgne": cg, "dslash": dslash, "batched_apply": batched, "kernels": kernels,
+            "cgne": cg, "dslash": dslash, "batched_apply": batched, "force": force, "kernels": kernels,
             "profiled_solve": {"iters": prof_info.iters, "true_res": prof_info.true_res}}
     print(json.dumps(line), flush=True)
     if dist:

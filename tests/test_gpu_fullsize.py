@@ -8,6 +8,10 @@ configuration the solver uses (one launch over all right-hand sides):
   apply (masses 0.001 .. 0.05 in one launch), and (opt-in, MDWF_SLOW=1) the
   8-source, 8-mass mixed FP16+norm CGNE with FP64 reliable updates.
 
+* 16^3 x 32, Ls = 16 (the bench lattice): the mixed solve with per-slice
+  Zolotarev coefficients, and the force at mf = 0.02 against central
+  differences of its action.
+
 The oracle checks sampled right-hand sides element by element (tolerances of
 the operator tests: F32 1e-5 of max |oracle|, F16N 3e-3 in the 2-norm) and the
 solves through its own FP64 residuals.
@@ -165,3 +169,41 @@ def test_cgne_16x16x16x32_Ls16_zolotarev_mixed_f32():
     normal, first = oracle_residuals(x, b, U, p)
     assert normal <= 1.05e-10, normal
     assert first <= 1e-8, first
+
+
+def test_force_16x16x16x32_Ls16_finite_differences():
+    """The force workload (16^3 x 32, Ls = 16, mf = 0.02, links eps = 0.2): dS/dU along a
+    random su(3) direction and dS/db5 against central differences (h = 1e-5) of S, with
+    FP64 solves to 1e-13 so that the difference quotients resolve the derivatives."""
+    dims, Ls, mf = (16, 16, 16, 32), 16, 0.02
+    U = sy.gauge_field(dims, 0.2, sy.config_seed("gauge", 4))
+    _, phi = oracle.split(sy.gaussian_field(dims, Ls, sy.config_seed("source", 4)), dims)
+    rng = np.random.default_rng(44)
+    a = rng.standard_normal(U.shape) + 1j * rng.standard_normal(U.shape)
+    w = 0.5 * (a - np.conj(np.swapaxes(a, -1, -2)))
+    w -= np.trace(w, axis1=-2, axis2=-1)[..., None, None] / 3.0 * np.eye(3)
+    lam, v = np.linalg.eigh(1j * w)
+
+    def expm(t):
+        return np.einsum("...ij,...j,...kj->...ik", v, np.exp(-1j * t * lam), np.conj(v))
+
+    phid = torch.from_numpy(phi).cuda()
+
+    def action(Ux, b5=1.5, derivs=False):
+        h = mdwf.mdwf_create(dims, Ls, 1.8, b5, 0.5, mf)
+        try:
+            mdwf.mdwf_load_gauge(h, torch.from_numpy(np.ascontiguousarray(Ux)).cuda())
+            G = torch.empty(U.shape, dtype=torch.complex128, device="cuda") if derivs else None
+            S, db5, dc5, st, info = mdwf.mdwf_force(h, G, phid, tol=1e-13)
+            assert st == 0, info.as_dict()
+            return S, (G.cpu().numpy() if derivs else None), db5
+        finally:
+            mdwf.mdwf_destroy(h)
+
+    S0, G, db5 = action(U, derivs=True)
+    eps = 1e-5
+    fd = (action(expm(eps) @ U)[0] - action(expm(-eps) @ U)[0]) / (2 * eps)
+    an = float(np.sum(np.real(np.conj(G) * (w @ U))))
+    assert an == pytest.approx(fd, rel=1e-4)
+    fd_b5 = (action(U, b5=1.5 + eps)[0] - action(U, b5=1.5 - eps)[0]) / (2 * eps)
+    assert db5 == pytest.approx(fd_b5, rel=1e-4)
