@@ -167,12 +167,101 @@ __device__ __forceinline__ R load_input(const Field<P>& in, long long sr, int s,
     return R(1);
 }
 
+// The forward and backward terms of one direction mu together (FP64 operator,
+// no gather, no chemical potential on mu): per output colour i,
+//   g_f = [U_mu(x) h_f]_i,  s = g_f + [U_mu(x-mu)^dag h_b]_i  (one FMA chain from g_f),
+//   upper += s,  lower += SF A_mu^dag (g_f - g_b) with g_f - g_b = 2 g_f - s,
+// since the backward term enters the lower half with the opposite sign. This
+// takes 12 of the 48 additions of the two reconstructions away (the FP64
+// operator is bound by the FP64 pipe). Links are read one row (U) or one
+// column (U^dag) at a time.
+template <int MU, bool DAG>
+__device__ __forceinline__ void hop_pair64(double* acc, const Field<MDWF_F64>& in, const Gauge<MDWF_F64>& U,
+                                           const HopParams<double>& hp, const int* nbi, long long site, int s,
+                                           long long rbase) {
+    constexpr int SF = DAG ? +1 : -1;
+    const long long jf = __ldg(nbi + MU), jb = __ldg(nbi + 4 + MU);
+    double hf[12], hb[12];
+    {
+        double w[24];
+        in.load(rbase + jf, s, w);
+        project<MU, SF>(w, hf);
+    }
+    {
+        double w[24];
+        in.load(rbase + jb, s, w);
+        project<MU, -SF>(w, hb);
+    }
+    const double2* uf = U.u + (((long long)hp.out_parity * 4 + MU) * hp.g.Vh + site) * 9;
+    const double2* ub = U.u + (((long long)(1 - hp.out_parity) * 4 + MU) * hp.g.Vh + jb) * 9;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        double2 rf[3], cb[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            rf[j] = __ldg(uf + 3 * i + j);  // U_f[i][j]
+            cb[j] = __ldg(ub + 3 * j + i);  // U_b[j][i]: (U_b^dag)[i][j] = conj
+        }
+        double sum[4], dif[4];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            double sr = 0, si = 0;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const double ur = rf[j].x, ui = rf[j].y, hr = hf[6 * a + 2 * j], hi = hf[6 * a + 2 * j + 1];
+                sr = fma(ur, hr, sr);
+                sr = fma(-ui, hi, sr);
+                si = fma(ur, hi, si);
+                si = fma(ui, hr, si);
+            }
+            const double fr = sr, fi = si;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const double ur = cb[j].x, ui = -cb[j].y, hr = hb[6 * a + 2 * j], hi = hb[6 * a + 2 * j + 1];
+                sr = fma(ur, hr, sr);
+                sr = fma(-ui, hi, sr);
+                si = fma(ur, hi, si);
+                si = fma(ui, hr, si);
+            }
+            sum[2 * a] = sr;
+            sum[2 * a + 1] = si;
+            dif[2 * a] = fma(2.0, fr, -sr);
+            dif[2 * a + 1] = fma(2.0, fi, -si);
+        }
+        acc[2 * i] += sum[0];
+        acc[2 * i + 1] += sum[1];
+        acc[6 + 2 * i] += sum[2];
+        acc[7 + 2 * i] += sum[3];
+        const double g0r = dif[0], g0i = dif[1], g1r = dif[2], g1i = dif[3];
+        double b0r, b0i, b1r, b1i;  // (A^dag d)_0, (A^dag d)_1
+        if (MU == 0) {
+            b0r = -g1i; b0i = g1r; b1r = -g0i; b1i = g0r;
+        } else if (MU == 1) {
+            b0r = g1r; b0i = g1i; b1r = -g0r; b1i = -g0i;
+        } else if (MU == 2) {
+            b0r = -g0i; b0i = g0r; b1r = g1i; b1i = -g1r;
+        } else {
+            b0r = g0r; b0i = g0i; b1r = g1r; b1i = g1i;
+        }
+        acc[12 + 2 * i] += SF * b0r;
+        acc[13 + 2 * i] += SF * b0i;
+        acc[18 + 2 * i] += SF * b1r;
+        acc[19 + 2 * i] += SF * b1i;
+    }
+}
+
 // nbi: the site's eight neighbour indices (x+mu, mu = 0..3, then x-mu), each
 // read just before its term so that none is held in a register across terms
 template <int P, int MU, bool GATHER, bool DAG, typename R>
 __device__ __forceinline__ void hop_dir(R* acc, const Field<P>& in, const Gauge<P>& U, const HopParams<R>& hp,
                                         const int* nbi, long long site, int s, long long rbase, R mass,
                                         R gown, R gfac) {
+    if constexpr (P == MDWF_F64 && !GATHER) {
+        if (!(MU == 3 && hp.chem)) {
+            hop_pair64<MU, DAG>(acc, in, U, hp, nbi, site, s, rbase);
+            return;
+        }
+    }
     const Geom& g = hp.g;
     constexpr int SF = DAG ? +1 : -1;  // forward projector 1 + SF g_mu
     constexpr bool SCALED = P == MDWF_F16N && !GATHER;
