@@ -38,7 +38,7 @@ FLOPS_PER_SITE = 3120.0      # per odd 5d site and M (or M^dag) application
 # DRAM bytes (read + write) per launch of a kernel in this workload's solve, from one
 # ncu capture of the kernels as they are now (summarised under profiles/); a kernel
 # that changes drops out of this table until it is captured again.
-NCU_TRAFFIC = {"hop_xpay_f32": 252.139008e6 + 166.769408e6}
+NCU_TRAFFIC = {"hop_xpay_f32": 252.167936e6 + 167.096064e6}
 METRIC = "Moebius Dslash GFLOP/s in CGNE to 1e-10 (mixed FP32/FP64)"
 # spectrum bounds of the Zolotarev coefficients of the per-slice solve: the upper one is
 # lambda_max = (8 - M5) / (10 - M5) of the Shamir kernel at M5 = 1.8 (Sec. 2)
