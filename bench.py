@@ -45,6 +45,8 @@ METRIC = "Moebius Dslash GFLOP/s in CGNE to 1e-10 (mixed FP32/FP64)"
 ZOLO_RANGE = (0.05, 0.756)
 # the force workload: the same lattice and links, mf = 0.02, its own Gaussian phi
 FORCE_MF, FORCE_SEED = 0.02, 2004
+# the 4d field of the overlap application and the wall force, and the chemical potential
+OVERLAP_SEED, CHEM_MU = 2005, 0.1
 N5 = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2 * LS
 
 
@@ -456,6 +458,38 @@ def main() -> None:
             "lambda_range": list(ZOLO_RANGE)}
         mdwf.mdwf_set_s_coefficients(h, None, None)
 
+    # ---------------- the constructions around the solve, mixed precision to 1e-10: D_ov(m) psi
+    # (one Pauli-Villars solve, Sec. 2.2), the wall-pseudofermion action and its force (two
+    # solves, Sec. 2.4), and the solve with a chemical potential on the time links (Sec. 6.6)
+    around = None
+    if not args.no_extras:
+        around = {}
+        psi4 = torch.from_numpy(np.ascontiguousarray(sy.gaussian_field(dims, 1, OVERLAP_SEED)[0])).cuda()
+        out4 = torch.empty_like(psi4)
+        G4 = torch.empty(U.shape, dtype=torch.complex128, device="cuda")
+
+        def timed(fn):
+            fn()  # warm-up
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            r = fn()
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1), r
+
+        ms, (st, infs) = timed(lambda: mdwf.mdwf_overlap_apply(h, out4, psi4, tol=1e-10, inner_prec=inner))
+        around["overlap_apply"] = {"ms": ms, "pv_iters": infs[0].iters, "status": st}
+        ms, (S4, st, inf4) = timed(lambda: mdwf.mdwf_force4d(h, G4, psi4, tol=1e-10, inner_prec=inner))
+        around["wall_force"] = {"ms": ms, "second_solve_iters": inf4.iters, "status": st}
+        mdwf.mdwf_set_chemical_potential(h, CHEM_MU)
+        ms, inf = timed(lambda: solve(inner))
+        around["mixed_" + args.inner + "_chemical_potential"] = {
+            "ms": ms, "mu": CHEM_MU, "iters": inf.iters, "reliable_updates": inf.reliable_updates,
+            "true_res": inf.true_res}
+        mdwf.mdwf_set_chemical_potential(h, 0.0)
+        del psi4, out4, G4
+
     # ---------------- the force on the same lattice at mf = 0.02 (dS/dU, dS/db5, dS/dc5; one solve)
     force = None
     if not args.no_extras:
@@ -491,7 +525,8 @@ def main() -> None:
             "gpu_launches": launches1 - launches0,
             "applies_per_step": applies / args.steps,
             "roofline": roofline, "clocks": clocks.summary(), "e2e": e2e, "cpu_baseline": cpu,
-            "cgne": cg, "dslash": dslash, "batched_apply": batched, "force": force, "kernels": kernels,
+            "cgne": cg, "dslash": dslash, "batched_apply": batched, "force": force, "around_the_solve": around,
+            "kernels": kernels,
             "profiled_solve": {"iters": prof_info.iters, "true_res": prof_info.true_res}}
     print(json.dumps(line), flush=True)
     if dist:

@@ -286,12 +286,12 @@ def mdwf_apply_full(ctx, out, inp, nrhs: int = 1, mf_per_rhs=None, dagger: bool 
            "mdwf_apply_full")
 
 
-def _pv_call(fn, name, ctx, out, psi, nrhs, mf_per_rhs, tol, maxiter, raise_on_error):
+def _pv_call(fn, name, ctx, out, psi, nrhs, mf_per_rhs, tol, maxiter, raise_on_error, inner_prec=MDWF_F64):
     po, wo = _ptr_where(out)
     pp, wp = _ptr_where(psi)
     if wo != wp:
         raise ValueError("both buffers must be host or both device")
-    prm = SolveParams(float(tol), int(maxiter), MDWF_F64, 0.0, 8, 1)
+    prm = SolveParams(float(tol), int(maxiter), int(inner_prec), 0.0, 8, 1)
     infos = (SolveInfo * int(nrhs))()
     st = fn(ctx, po, pp, int(nrhs), _masses(mf_per_rhs), wp, ctypes.byref(prm), infos)
     if raise_on_error and st != 0:
@@ -300,24 +300,24 @@ def _pv_call(fn, name, ctx, out, psi, nrhs, mf_per_rhs, tol, maxiter, raise_on_e
 
 
 def mdwf_overlap_apply(ctx, out4, psi4, nrhs: int = 1, mf_per_rhs=None, tol: float = 1e-12, maxiter: int = 20000,
-                       raise_on_error: bool = True):
+                       raise_on_error: bool = True, inner_prec: int = MDWF_F64):
     """out4 = D_ov(m) psi4 through a Pauli-Villars solve; returns (status, [SolveInfo])."""
     return _pv_call(load().mdwf_overlap_apply, "mdwf_overlap_apply", ctx, out4, psi4, nrhs, mf_per_rhs, tol,
-                    maxiter, raise_on_error)
+                    maxiter, raise_on_error, inner_prec)
 
 
 def mdwf_pv_reconstruct(ctx, Psi5, psi4, nrhs: int = 1, mf_per_rhs=None, tol: float = 1e-12, maxiter: int = 20000,
-                        raise_on_error: bool = True):
+                        raise_on_error: bool = True, inner_prec: int = MDWF_F64):
     """5d Psi (Sec. 2.3) from the 4d overlap solution psi4; returns (status, [SolveInfo])."""
     return _pv_call(load().mdwf_pv_reconstruct, "mdwf_pv_reconstruct", ctx, Psi5, psi4, nrhs, mf_per_rhs, tol,
-                    maxiter, raise_on_error)
+                    maxiter, raise_on_error, inner_prec)
 
 
 def mdwf_gw_violation(ctx, out4, psi4, nrhs: int = 1, mf_per_rhs=None, tol: float = 1e-12, maxiter: int = 20000,
-                      raise_on_error: bool = True):
+                      raise_on_error: bool = True, inner_prec: int = MDWF_F64):
     """out4 = Delta_Ls psi4 = (1 - eps^2) psi4 / 4 through two overlap applications."""
     return _pv_call(load().mdwf_gw_violation, "mdwf_gw_violation", ctx, out4, psi4, nrhs, mf_per_rhs, tol, maxiter,
-                    raise_on_error)
+                    raise_on_error, inner_prec)
 
 
 def mdwf_apply_noalloc(ctx, out, inp, prec: int, nrhs: int = 1, mf_per_rhs=None, dagger: bool = False) -> None:
@@ -357,7 +357,8 @@ def mdwf_force(ctx, dSdU, phi, tol: float = 1e-12, maxiter: int = 40000, inner_p
     return S.value, db5[0], dc5[0], st, info
 
 
-def mdwf_force4d(ctx, dSdU, phi4, tol: float = 1e-12, maxiter: int = 40000, raise_on_error: bool = True):
+def mdwf_force4d(ctx, dSdU, phi4, tol: float = 1e-12, maxiter: int = 40000, raise_on_error: bool = True,
+                 inner_prec: int = MDWF_F64):
     """S = |D(1)^dag D(m)^-dag P phi|^2 for a 4d wall pseudofermion and dS/dU (into dSdU, or
     None for S only). Returns (S, status, SolveInfo)."""
     pp, wp = _ptr_where(phi4)
@@ -366,7 +367,7 @@ def mdwf_force4d(ctx, dSdU, phi4, tol: float = 1e-12, maxiter: int = 40000, rais
         pg, wg = _ptr_where(dSdU)
         if wg != wp:
             raise ValueError("dSdU and phi must both be host or both be device buffers")
-    prm = SolveParams(float(tol), int(maxiter), MDWF_F64, 0.0, 8, 1)
+    prm = SolveParams(float(tol), int(maxiter), int(inner_prec), 0.0, 8, 1)
     info = SolveInfo()
     S = ctypes.c_double(0)
     st = load().mdwf_force4d(ctx, pg, ctypes.byref(S), pp, wp, ctypes.byref(prm), ctypes.byref(info))
