@@ -98,8 +98,11 @@ def test_overlap_apply_matches_dense_overlap(b5, c5):
         assert np.abs(out[r] - ref).max() <= 1e-9 * np.abs(ref).max()
 
 
-def test_overlap_apply_matches_oracle_route():
-    """4^4, Ls = 8, Moebius: [P^dag D(1)^-1 D(m) P psi~]_1 with the oracle's solve."""
+@pytest.mark.parametrize("inner,tol,bound", [(mdwf.MDWF_F64, 1e-12, 1e-9), (mdwf.MDWF_F32, 1e-10, 1e-8),
+                                             (mdwf.MDWF_F16N, 1e-10, 1e-8)], ids=["f64", "mixed-f32", "mixed-f16n"])
+def test_overlap_apply_matches_oracle_route(inner, tol, bound):
+    """4^4, Ls = 8, Moebius: [P^dag D(1)^-1 D(m) P psi~]_1 with the oracle's solve; the
+    Pauli-Villars solve in FP64, or mixed with FP32 or FP16+norm inner iterations."""
     dims, Ls, mf = (4, 4, 4, 4), 8, 0.02
     U = sy.gauge_field(dims, 0.3, 1053)
     psi = sy.gaussian_field(dims, 1, 2053)[0]
@@ -113,12 +116,12 @@ def test_overlap_apply_matches_oracle_route():
     h = ctx(dims, Ls, 1.5, 0.5, mf, U)
     try:
         out = torch.empty(psi.shape, dtype=torch.complex128, device="cuda")
-        st, info = mdwf.mdwf_overlap_apply(h, out, torch.from_numpy(psi).cuda(), tol=1e-12)
+        st, info = mdwf.mdwf_overlap_apply(h, out, torch.from_numpy(psi).cuda(), tol=tol, inner_prec=inner)
     finally:
         mdwf.mdwf_destroy(h)
     assert st == 0
     assert info[0].iters < 200  # the Pauli-Villars solve is cheap (Sec. 2.3)
-    assert np.abs(out.cpu().numpy() - ref).max() <= 1e-9 * np.abs(ref).max()
+    assert np.abs(out.cpu().numpy() - ref).max() <= bound * np.abs(ref).max()
 
 
 def test_pv_reconstruct_reproduces_bulk_solution():
