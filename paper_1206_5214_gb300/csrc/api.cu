@@ -105,6 +105,22 @@ static void kernel_name(int kind, char* out, size_t n) {
     snprintf(out, n, "%s_%s", base[kind / 3], prec[kind % 3]);
 }
 
+// With MDWF_CANARY=1 in the environment every allocation of the library is
+// filled with 0xFF bytes (a NaN in FP16, FP32 and FP64) before its first use,
+// so that a kernel reading memory nothing has written spreads NaN into its
+// results, which the parity tests then catch. Off by default.
+bool canary_on() {
+    static const bool on = [] {
+        const char* e = getenv("MDWF_CANARY");
+        return e && e[0] == '1';
+    }();
+    return on;
+}
+
+int canary_fill(void* p, size_t bytes) {
+    return canary_on() && p ? cuda_status(cudaMemset(p, 0xFF, bytes)) : MDWF_OK;
+}
+
 int ensure_workspace(Workspace& w, size_t bytes) {
     if (w.bytes >= bytes) return MDWF_OK;
     if (w.p) {
@@ -119,7 +135,7 @@ int ensure_workspace(Workspace& w, size_t bytes) {
         return cuda_status(e);
     }
     w.bytes = bytes;
-    return MDWF_OK;
+    return canary_fill(w.p, bytes);
 }
 
 // ----------------------------------------------------- Ls x Ls tables (host)
@@ -225,8 +241,12 @@ int ensure_tables(mdwf_ctx* c, int nrhs, const double* mf_per_rhs) {
         cudaFree(c->tab64); cudaFree(c->tab32); cudaFree(c->mass64); cudaFree(c->mass32);
         cudaFreeHost(c->tab_host);
         c->tab64 = nullptr; c->tab32 = nullptr; c->mass64 = nullptr; c->mass32 = nullptr; c->tab_host = nullptr;
-        if ((st = cuda_status(cudaMalloc(&c->tab64, total * sizeof(double))))) return st;
-        if ((st = cuda_status(cudaMalloc(&c->tab32, total * sizeof(float))))) return st;
+        if ((st = cuda_status(cudaMalloc(&c->tab64, total * sizeof(double)))) ||
+            (st = canary_fill(c->tab64, total * sizeof(double))))
+            return st;
+        if ((st = cuda_status(cudaMalloc(&c->tab32, total * sizeof(float)))) ||
+            (st = canary_fill(c->tab32, total * sizeof(float))))
+            return st;
         if ((st = cuda_status(cudaMalloc(&c->mass64, 64 * sizeof(double))))) return st;
         if ((st = cuda_status(cudaMalloc(&c->mass32, 64 * sizeof(float))))) return st;
         if ((st = cuda_status(cudaMallocHost(&c->tab_host, total * (sizeof(double) + sizeof(float)) + 64 * 12 + 16))))
@@ -505,8 +525,12 @@ int mdwf_set_s_coefficients(mdwf_ctx* c, const double* b5s, const double* c5s) {
     }
     for (int s = 0; s < Ls; ++s)
         if (!isfinite(b5s[s]) || !isfinite(c5s[s])) return MDWF_EINVAL;
-    if (!c->gs64 && (st = cuda_status(cudaMalloc(&c->gs64, 3 * 64 * sizeof(double))))) return st;
-    if (!c->gs32 && (st = cuda_status(cudaMalloc(&c->gs32, 3 * 64 * sizeof(float))))) return st;
+    if (!c->gs64 && ((st = cuda_status(cudaMalloc(&c->gs64, 3 * 64 * sizeof(double)))) ||
+                     (st = canary_fill(c->gs64, 3 * 64 * sizeof(double)))))
+        return st;
+    if (!c->gs32 && ((st = cuda_status(cudaMalloc(&c->gs32, 3 * 64 * sizeof(float)))) ||
+                     (st = canary_fill(c->gs32, 3 * 64 * sizeof(float)))))
+        return st;
     // gather factors of row s: M_phi psi at s = gscale (gown psi_s + gfac C psi)
     double h64[3 * 64] = {0};
     float h32[3 * 64] = {0};
@@ -577,7 +601,9 @@ int mdwf_load_gauge(mdwf_ctx* c, const double* U, int where) {
     const size_t nlink = (size_t)c->g.Vh * 2 * 4;
     const size_t bytes[2] = {nlink * link_store_bytes(MDWF_F64), nlink * link_store_bytes(MDWF_F32)};
     for (int k = 0; k < 2; ++k)
-        if (!c->gauge[k] && (st = cuda_status(cudaMalloc(&c->gauge[k], bytes[k])))) return st;
+        if (!c->gauge[k] && ((st = cuda_status(cudaMalloc(&c->gauge[k], bytes[k]))) ||
+                             (st = canary_fill(c->gauge[k], bytes[k]))))
+            return st;
     const double* src = U;
     void* stage = nullptr;
     if (where == MDWF_HOST) {

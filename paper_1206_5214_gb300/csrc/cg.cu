@@ -607,6 +607,7 @@ int field_dot64(mdwf_ctx* c, const void* a, const void* b, int nrhs, double* out
         c->red_partials = nullptr;
         c->red_partials_len = 0;
         int st = cuda_status(cudaMalloc(&c->red_partials, need * sizeof(double)));
+        if (!st) st = canary_fill(c->red_partials, need * sizeof(double));
         if (st) return st;
         c->red_partials_len = need;
     }
@@ -670,6 +671,7 @@ int slice_dot64(mdwf_ctx* c, const void* a, const void* b, double* out_host) {
         c->red_partials = nullptr;
         c->red_partials_len = 0;
         int st = cuda_status(cudaMalloc(&c->red_partials, need * sizeof(double)));
+        if (!st) st = canary_fill(c->red_partials, need * sizeof(double));
         if (st) return st;
         c->red_partials_len = need;
     }

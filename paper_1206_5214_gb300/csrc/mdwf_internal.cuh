@@ -689,6 +689,9 @@ int check_launch();
 // MDWF_ETIMEOUT if a bounded device-side wait gave up since the last call (synchronises)
 int device_wait_status(mdwf_ctx* c);
 int ensure_workspace(Workspace& w, size_t bytes);
+// NaN-canary mode (MDWF_CANARY=1): fill a fresh allocation with 0xFF bytes
+bool canary_on();
+int canary_fill(void* p, size_t bytes);
 int ensure_tables(mdwf_ctx* c, int nrhs, const double* mf_per_rhs);
 
 // table pointers for table t, precision
