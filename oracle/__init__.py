@@ -56,8 +56,7 @@ class Params:
     ``b5s`` / ``c5s`` (tuples of Ls values, or None) replace the constant b5 / c5
     by per-slice coefficients b5(s), c5(s): row s of Eq. (MoebiusOp) then uses
     D+ = b5(s) D_W + 1 and D- = c5(s) D_W - 1. ``mu`` is a chemical potential
-    on the time links (Sec. 6.6). The force supports constant coefficients and
-    mu = 0 only.
+    on the time links (Sec. 6.6).
     """
     dims: tuple
     Ls: int
@@ -277,20 +276,23 @@ def solve_dag(b: np.ndarray, U: np.ndarray, p: Params, tol: float = 1e-12, maxit
 
 
 def force(phi: np.ndarray, U: np.ndarray, p: Params, tol: float = 1e-12, maxiter: int = 20000):
-    """S = phi^dag (M^dag M)^-1 phi and dS/dU, dS/db5, dS/dc5.
+    """S = phi^dag (M^dag M)^-1 phi and dS/dU, dS/db5, dS/dc5 (with a chemical
+    potential when p.mu is set).
 
     dS/dU has the gauge field's shape; a variation dU changes S by
-    Re sum(conj(dSdU) * dU). Returns (S, dSdU, dSdb5, dSdc5, status, iters).
+    Re sum(conj(dSdU) * dU). With per-slice coefficients dSdb5 and dSdc5 are arrays of
+    Ls values, dS/db5(s) and dS/dc5(s). Returns (S, dSdU, dSdb5, dSdc5, status, iters).
     """
-    if p.s_dependent or p.mu != 0.0:
-        raise ValueError("the oracle force supports constant b5, c5 and mu = 0 only")
     phi, U = _c(phi), _c(U)
     G = np.zeros_like(U)
-    S, db5, dc5 = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+    n = p.Ls if p.s_dependent else 1
+    S, db5, dc5 = ctypes.c_double(0), (ctypes.c_double * n)(), (ctypes.c_double * n)()
     it = ctypes.c_int(0)
-    st = _load().or_force(_ptr(G), ctypes.byref(db5), ctypes.byref(dc5), ctypes.byref(S), _ptr(phi), _ptr(U),
+    st = _load().or_force(_ptr(G), db5, dc5, ctypes.byref(S), _ptr(phi), _ptr(U),
                           ctypes.byref(p.c()), float(tol), int(maxiter), ctypes.byref(it))
-    return float(S.value), G, float(db5.value), float(dc5.value), int(st), int(it.value)
+    if p.s_dependent:
+        return float(S.value), G, np.array(db5[:]), np.array(dc5[:]), int(st), int(it.value)
+    return float(S.value), G, float(db5[0]), float(dc5[0]), int(st), int(it.value)
 
 
 # ------------------------------------------------------------- layout helpers

@@ -832,6 +832,10 @@ static void acc_link_derivative(cplx *Gd, const cplx *c, const cplx *e, const or
         long i = half_to_lex(p->L, j, po);
         for (int mu = 0; mu < 4; ++mu) {
             long fw = shift(p->L, i, mu, +1), bw = shift(p->L, i, mu, -1);
+            /* the forward time hop of the (undaggered) block carries e^{+mu}, the
+               backward one e^{-mu} (Sec. 6.6) */
+            const double wf = (mu == 3 && p->mu != 0.0) ? exp(p->mu) : 1.0;
+            const double wb = (mu == 3 && p->mu != 0.0) ? exp(-p->mu) : 1.0;
             cplx Sm[4][4], Sp[4][4];
             one_pm_gamma(Sm, mu, -1.0);
             one_pm_gamma(Sp, mu, +1.0);
@@ -849,8 +853,8 @@ static void acc_link_derivative(cplx *Gd, const cplx *c, const cplx *e, const or
                             sf += pc[3 * sp + a] * conj(ef[3 * sp + b]);
                             sb += eb[3 * sp + a] * conj(qc[3 * sp + b]);
                         }
-                        gf[3 * a + b] += coef * (-0.5) * sf;
-                        gb[3 * a + b] += coef * (-0.5) * sb;
+                        gf[3 * a + b] += coef * (-0.5) * wf * sf;
+                        gb[3 * a + b] += coef * (-0.5) * wb * sb;
                     }
             }
         }
@@ -858,14 +862,15 @@ static void acc_link_derivative(cplx *Gd, const cplx *c, const cplx *e, const or
 }
 
 /*
- * d/d(theta) of M applied to X, for theta = b5 (which == 0) or c5 (which == 1):
+ * d/d(theta) of M applied to X, for theta = b5 (which == 0) or c5 (which == 1),
+ * constant over the slices (slice < 0) or the coefficient of row `slice` alone:
  *   M = 1 - A D_br A D_rb,  A = I^-1,  dA = -A dI A,
  *   dM X = -[dA D_br A D_rb X + A dD_br A D_rb X + A D_br dA D_rb X + A D_br A dD_rb X]
  * with dI the site-diagonal block whose D+ part is (4 - M5) (b5) or whose D-
  * part is (4 - M5) (c5), and dD the hopping block with D+ -> W (b5) or
  * D- -> W (c5); both follow from D+ = b5 D_W + 1, D- = c5 D_W - 1.
  */
-void or_dm_dparam(cplx *out, const cplx *X, const cplx *U, const or_params *p, int which)
+static void dm_dparam_rows(cplx *out, const cplx *X, const cplx *U, const or_params *p, int which, int slice)
 {
     long Vh = vol4(p->L) / 2, n = 12 * Vh * p->Ls;
     double w = 4.0 - p->M5;
@@ -882,6 +887,9 @@ void or_dm_dparam(cplx *out, const cplx *X, const cplx *U, const or_params *p, i
     or_mee_inv(u, t, Vh, p, 0);
     coefs cId = fill_const(p->Ls, dId), cIo = fill_const(p->Ls, dIo);
     coefs cHd = fill_const(p->Ls, dHd), cHo = fill_const(p->Ls, dHo);
+    if (slice >= 0)  /* only row `slice` of I and of the hopping block depends on theta */
+        for (int k = 0; k < p->Ls; ++k)
+            if (k != slice) cId.v[k] = cIo.v[k] = cHd.v[k] = cHo.v[k] = 0.0;
     rb_block(t, u, NULL, p, 1, 0, cId.v, cIo.v, 0);
     or_mee_inv(u, t, Vh, p, 0);
     for (long k = 0; k < n; ++k) out[k] -= -u[k];
@@ -904,6 +912,11 @@ void or_dm_dparam(cplx *out, const cplx *X, const cplx *U, const or_params *p, i
     free(e1); free(e2); free(t); free(u);
 }
 
+void or_dm_dparam(cplx *out, const cplx *X, const cplx *U, const or_params *p, int which)
+{
+    dm_dparam_rows(out, X, U, p, which, -1);
+}
+
 /*
  * Action S = phi^dag (M^dag M)^-1 phi and its derivatives. With X = (M^dag M)^-1 phi
  * and Y = M X, a variation of M gives dS = -2 Re(Y^dag dM X). M depends on the
@@ -920,7 +933,7 @@ void or_dm_dparam(cplx *out, const cplx *X, const cplx *U, const or_params *p, i
 int or_force(cplx *dSdU, double *dSdb5, double *dSdc5, double *S, const cplx *phi,
              const cplx *U, const or_params *p, double tol, int maxiter, int *iters)
 {
-    if (p->b5s || p->c5s || p->mu != 0.0) return -1;   /* the derivatives below: constant b5, c5, no mu */
+    const int per_slice = p->b5s || p->c5s;
     long V = vol4(p->L), Vh = V / 2, n = 12 * Vh * p->Ls;
     cplx *X = calloc((size_t)n, sizeof(cplx)), *Y = malloc(sizeof(cplx) * n);
     cplx *a = malloc(sizeof(cplx) * n), *b = malloc(sizeof(cplx) * n);
@@ -936,15 +949,24 @@ int or_force(cplx *dSdU, double *dSdb5, double *dSdc5, double *S, const cplx *ph
     or_dhop(t, a, U, p, 0, 1);
     or_mee_inv(c, t, Vh, p, 1);             /* c = A^dag D_br^dag a (even) */
     memset(dSdU, 0, sizeof(cplx) * 9 * 4 * V);
-    coefs cb5 = fill_const(p->Ls, p->b5), cc5 = fill_const(p->Ls, p->c5);
+    coefs cb5 = b5_s(p), cc5 = c5_s(p);
     rb_block(w, b, NULL, p, 0, 0, cb5.v, cc5.v, 0);   /* b~ (even) */
     acc_link_derivative(dSdU, a, w, p, 1, 2.0);    /* 2 Re(a^dag dD_br b) */
     rb_block(w, X, NULL, p, 1, 0, cb5.v, cc5.v, 0);   /* X~ (odd) */
     acc_link_derivative(dSdU, c, w, p, 0, 2.0);    /* 2 Re(c^dag dD_rb X) */
-    or_dm_dparam(t, X, U, p, 0);
-    *dSdb5 = -2.0 * creal(dotc(Y, t, n));
-    or_dm_dparam(t, X, U, p, 1);
-    *dSdc5 = -2.0 * creal(dotc(Y, t, n));
+    if (per_slice) {  /* dS/db5(s), dS/dc5(s): Ls values each */
+        for (int sl = 0; sl < p->Ls; ++sl) {
+            dm_dparam_rows(t, X, U, p, 0, sl);
+            dSdb5[sl] = -2.0 * creal(dotc(Y, t, n));
+            dm_dparam_rows(t, X, U, p, 1, sl);
+            dSdc5[sl] = -2.0 * creal(dotc(Y, t, n));
+        }
+    } else {
+        or_dm_dparam(t, X, U, p, 0);
+        *dSdb5 = -2.0 * creal(dotc(Y, t, n));
+        or_dm_dparam(t, X, U, p, 1);
+        *dSdc5 = -2.0 * creal(dotc(Y, t, n));
+    }
     free(X); free(Y); free(a); free(b); free(c); free(t); free(w);
     return st;
 }
