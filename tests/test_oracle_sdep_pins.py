@@ -200,9 +200,13 @@ def test_blocks_schur_complement_and_solve(orc, tiny):
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-10
 
 
-def test_force_refuses_s_dependent(orc, tiny):
+def test_force_per_slice_outputs(orc, tiny):
+    """With per-slice coefficients the force returns Ls values of dS/db5(s) and
+    dS/dc5(s) (their values are pinned in test_oracle_force_ext_pins.py)."""
     dims, U = tiny
     p = _params(orc, dims, GENERIC)
     _, phi = orc.split(sy.gaussian_field(dims, 4, 1), dims)
-    with pytest.raises(ValueError):
-        orc.force(phi, U, p)
+    S, G, db5, dc5, st, _ = orc.force(phi, U, p)
+    assert st == 0 and G.shape == U.shape
+    assert np.shape(db5) == (4,) and np.shape(dc5) == (4,)
+    assert np.all(np.isfinite(db5)) and np.all(np.isfinite(dc5))
