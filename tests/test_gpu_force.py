@@ -119,3 +119,26 @@ def test_autograd_backward_matches_force():
     assert float(S.detach()) == pytest.approx(S0, rel=1e-10)
     assert np.abs(U.grad.cpu().numpy() - G0).max() <= 1e-8 * np.abs(G0).max()
     assert b5c5.grad.cpu().numpy() == pytest.approx([db0, dc0], rel=1e-8)
+
+
+def test_autograd_per_slice_and_mu_match_oracle_force():
+    """mobius_action with per-slice b5(s), c5(s) (b5c5 of shape (2, Ls)) and mu = 0.3 on
+    4x2x2x2, Ls = 4: S, dS/dU and the (2, Ls) coefficient gradient against the oracle's force
+    with the same parameters (both solves to 1e-12)."""
+    dims, Ls, mf, mu = (4, 2, 2, 2), 4, 0.05, 0.3
+    prof = ([1.2, 1.9, 1.4, 2.3], [0.1, 0.8, 0.2, 1.0])
+    U = torch.from_numpy(sy.gauge_field(dims, 0.3, 1017)).cuda().requires_grad_(True)
+    _, phi_np = oracle.split(sy.gaussian_field(dims, Ls, 2017), dims)
+    phi = torch.from_numpy(phi_np).cuda()
+    bc = torch.tensor(prof, dtype=torch.float64, device="cuda", requires_grad=True)
+    S = mobius_action(U, bc, phi, dims, Ls, 1.8, mf, 1e-12, mu=mu)
+    S.backward()
+    p = oracle.Params(dims, Ls, 1.8, 1.5, 0.5, mf, b5s=tuple(prof[0]), c5s=tuple(prof[1]), mu=mu)
+    S0, G0, db0, dc0, st, _ = oracle.force(phi_np, U.detach().cpu().numpy(), p, tol=1e-12, maxiter=200000)
+    assert st == 0
+    assert float(S.detach()) == pytest.approx(S0, rel=1e-9)
+    assert np.abs(U.grad.cpu().numpy() - G0).max() <= 1e-7 * np.abs(G0).max()
+    g = bc.grad.cpu().numpy()
+    assert g.shape == (2, Ls)
+    ref = np.stack([db0, dc0])
+    assert np.abs(g - ref).max() <= 1e-7 * np.abs(ref).max()
