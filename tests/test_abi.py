@@ -64,3 +64,65 @@ def test_argument_validation_without_gpu(libpath):
     assert lib.mdwf_field_bytes(None, 0, 1) == 0
     assert m.mdwf_strerror(0) == "MDWF_OK"
     assert "invalid" in m.mdwf_strerror(1)
+
+
+def _argtype(decl):
+    decl = " ".join(decl.split())
+    if "*" in decl or "[" in decl:
+        return ctypes.c_void_p
+    if decl.startswith("double"):
+        return ctypes.c_double
+    if decl.startswith("int") or decl.startswith("const int"):
+        return ctypes.c_int
+    raise AssertionError(f"unexpected parameter type in the header: {decl}")
+
+
+def declared_signatures():
+    """name -> (return type text, [parameter declarations]) from include/*.h."""
+    sigs = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"^\s*([A-Za-z_][\w\s\*]*?)\b(mdwf_\w+)\s*\(([^)]*)\)\s*;", text, flags=re.M | re.S):
+            params = [p.strip() for p in m.group(3).split(",") if p.strip() and p.strip() != "void"]
+            sigs[m.group(2)] = (m.group(1).strip(), params)
+    return sigs
+
+
+def test_every_entry_point_refuses_a_null_context(libpath):
+    """Every call that takes a context returns MDWF_EINVAL for a NULL one (MDWF_OK for
+    mdwf_destroy, 0 bytes for mdwf_field_bytes), before any CUDA call: no GPU is needed."""
+    import paper_1206_5214_gb300 as m
+    lib = m.load()
+    checked = 0
+    for name, (ret, params) in declared_signatures().items():
+        if not params or not re.match(r"(const )?mdwf_ctx\s*\*\s*\w+$", params[0]):
+            continue
+        f = getattr(lib, name)
+        f.argtypes = [_argtype(p) for p in params]
+        f.restype = ctypes.c_size_t if ret == "size_t" else ctypes.c_int
+        args = [None if t is ctypes.c_void_p else t(0).value for t in f.argtypes]
+        got = f(*args)
+        expect = {"mdwf_destroy": 0, "mdwf_field_bytes": 0}.get(name, 1)
+        assert got == expect, (name, got)
+        checked += 1
+    assert checked >= 30
+
+
+def test_create_refuses_invalid_geometry(libpath):
+    import paper_1206_5214_gb300 as m
+    lib = m.load()
+    h = ctypes.c_void_p()
+    for dims, Ls in [((4, 4, 4, 0), 8), ((4, 4, 4, 4), 2 * 64 + 2), ((4, 4, 4, 4), -2), ((4, 4, 5, 4), 8)]:
+        d = (ctypes.c_int * 4)(*dims)
+        assert lib.mdwf_create(ctypes.byref(h), d, Ls, ctypes.c_double(1.8), ctypes.c_double(1.5),
+                               ctypes.c_double(0.5), ctypes.c_double(0.01), None) == 1, (dims, Ls)
+        assert not h.value
+
+
+def test_strerror_names_every_status(libpath):
+    import paper_1206_5214_gb300 as m
+    names = [m.mdwf_strerror(s) for s in range(0, 9)]
+    assert names[0] == "MDWF_OK"
+    assert all(n.startswith("MDWF_") for n in names[:8]), names
+    assert len(set(names[:8])) == 8
+    assert not names[8].startswith("MDWF_")
