@@ -90,9 +90,9 @@ def declared_signatures():
 
 def test_every_entry_point_refuses_a_null_context(libpath):
     """Every call that takes a context returns MDWF_EINVAL for a NULL one (MDWF_OK for
-    mdwf_destroy, 0 bytes for mdwf_field_bytes), before any CUDA call: no GPU is needed."""
-    import paper_1206_5214_gb300 as m
-    lib = m.load()
+    mdwf_destroy, 0 bytes for mdwf_field_bytes), before any CUDA call: no GPU is needed.
+    A separate handle of the library is used, so that the binding's signatures stay as set."""
+    lib = ctypes.CDLL(libpath)
     checked = 0
     for name, (ret, params) in declared_signatures().items():
         if not params or not re.match(r"(const )?mdwf_ctx\s*\*\s*\w+$", params[0]):
@@ -126,3 +126,30 @@ def test_strerror_names_every_status(libpath):
     assert all(n.startswith("MDWF_") for n in names[:8]), names
     assert len(set(names[:8])) == 8
     assert not names[8].startswith("MDWF_")
+
+
+def test_binding_signatures_match_the_header(libpath):
+    """The ctypes binding declares every header function with the header's number of
+    parameters, pointers where the header has pointers and doubles where it has doubles."""
+    import paper_1206_5214_gb300 as m
+    lib = m.load()
+    for name, (ret, params) in declared_signatures().items():
+        f = getattr(lib, name)
+        assert f.argtypes is not None, f"{name} has no argtypes in the binding"
+        assert len(f.argtypes) == len(params), (name, f.argtypes, params)
+        for t, p in zip(f.argtypes, params):
+            kind = _argtype(p)
+            if kind is ctypes.c_void_p:
+                assert t is ctypes.c_void_p or hasattr(t, "_type_") and t not in (ctypes.c_int, ctypes.c_double), \
+                    (name, p, t)
+            else:
+                assert t is kind, (name, p, t)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libmdwf.so the binding raises; it never falls back to the CPU."""
+    import paper_1206_5214_gb300 as m
+    monkeypatch.setattr(m, "_lib", None)
+    monkeypatch.setattr(m._build, "LIB", str(tmp_path / "libmdwf.so"))
+    with pytest.raises(OSError, match="not found"):
+        m.load(build_if_missing=False)
