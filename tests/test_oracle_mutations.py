@@ -48,6 +48,7 @@ PIN = {
     "blocks": lambda o: base.test_blocks_and_schur_complement(o, _tiny(), 1.5, 0.5),
     "solve": lambda o: base.test_solve_matches_dense_inverse(o, _tiny(), 1.5, 0.5),
     "force": lambda o: base.test_force_finite_differences(o),
+    "adjoint_solve": lambda o: base.test_adjoint_solve_inverts_the_adjoint(o, _tiny()),
     "sdep_dagger": lambda o: sdep.test_dagger_is_adjoint(o, _sdep_tiny(), sdep.GENERIC),
     "sdep_overlap": lambda o: sdep.test_transfer_matrix_overlap_identity(o, _sdep_tiny(), sdep.GENERIC),
     "sdep_blocks": lambda o: sdep.test_blocks_schur_complement_and_solve(o, _sdep_tiny()),
@@ -107,6 +108,20 @@ MUTATIONS = {
         "const double wf = (mu == 3 && p->mu != 0.0) ? exp(-p->mu) : 1.0;", ["force_chem"]),
     "force_per_slice_rows_inverted": (
         "if (k != slice) cId.v[k]", "if (k == slice) cId.v[k]", ["force_slices"]),
+    "force_action_from_wrong_vectors": (
+        "*S = creal(dotc(phi, X, n));", "*S = creal(dotc(X, X, n));", ["force"]),
+    "forward_link_at_neighbour": (
+        "acc_spin_colour(out, wf, Sf, U + 9 * (4 * i + mu), 0, ff);",
+        "acc_spin_colour(out, wf, Sf, U + 9 * (4 * fw + mu), 0, ff);", ["covariance", "dagger"]),
+    "chem_on_a_space_direction": (
+        "if (mu == 3 && chem != 0.0) {", "if (mu == 2 && chem != 0.0) {", ["chem_free"]),
+    "cg_beta_inverted": (
+        "double beta = rr_new / rr;\n            for (long i = 0; i < n; ++i) pp[i] = r[i] + beta * pp[i];\n"
+        "            rr = rr_new;\n        }\n    }",
+        "double beta = rr / rr_new;\n            for (long i = 0; i < n; ++i) pp[i] = r[i] + beta * pp[i];\n"
+        "            rr = rr_new;\n        }\n    }", ["solve"]),
+    "adjoint_solve_wrong_rhs": (
+        "or_ddw(rhs, b, U, p, 0);", "or_ddw(rhs, b, U, p, 1);", ["adjoint_solve"]),
 }
 
 
