@@ -81,3 +81,48 @@ def test_nonhermitian_kernel_overlap_identity(orc, b5, c5):
     Dov = 0.5 * (1 + m) * one + 0.5 * (1 - m) * g5 @ eps
     assert np.allclose(K[:n, :n], Dov, atol=1e-11)
     assert np.allclose(K[:, n:], np.eye(Ls * n)[:, n:], atol=1e-11)
+
+
+def test_per_slice_profile_with_chemical_potential(orc):
+    """Per-slice b5(s), c5(s) together with mu = 0.3 (2^4, Ls = 4): the first column of
+    P^dag D(1)^-1 D(m) P is (1+m)/2 + (1-m)/2 gamma5 (T^-Ls - 1)(T^-Ls + 1)^-1 with
+    T^-Ls = T_1^-1 ... T_Ls^-1, T_s^-1 = (1 + H_s)(1 - H_s)^-1 and the non-Hermitian
+    H_s = gamma5 (b5(s) + c5(s)) D_W(mu) (2 + (b5(s) - c5(s)) D_W(mu))^-1 (App. A with the
+    links of Sec. 6.6); the other columns are the identity and D^dag is the conjugate transpose."""
+    dims, Ls, M5, m, mu = (2, 2, 2, 2), 4, 1.8, 0.1, 0.3
+    b5s, c5s = (1.2, 1.9, 1.4, 2.3), (0.1, 0.8, 0.2, 1.0)
+    U = sy.gauge_field(dims, 0.3, 33)
+    V = 16
+    n = 12 * V
+    p = orc.Params(dims, Ls, M5, 1.5, 0.5, m, b5s=b5s, c5s=c5s, mu=mu)
+    shape = (Ls, 2, 2, 2, 2, 4, 3)
+    Dm = dense_of(lambda v: orc.ddw(v, U, p), Ls * n, shape)
+    D1 = dense_of(lambda v: orc.ddw(v, U, p.with_(mf=1.0)), Ls * n, shape)
+    assert np.allclose(dense_of(lambda v: orc.ddw(v, U, p, dagger=True), Ls * n, shape), Dm.conj().T, atol=1e-13)
+    Pp = np.kron(np.eye(V), np.kron(np.diag([1, 1, 0, 0]), np.eye(3)))
+    Pm = np.kron(np.eye(V), np.kron(np.diag([0, 0, 1, 1]), np.eye(3)))
+    P = np.zeros((Ls * n, Ls * n), complex)
+    for s in range(Ls):
+        P[s * n:(s + 1) * n, s * n:(s + 1) * n] += Pm
+        sp = (s + 1) % Ls
+        P[s * n:(s + 1) * n, sp * n:(sp + 1) * n] += Pp
+    K = P.conj().T @ np.linalg.solve(D1, Dm) @ P
+    DW = _dense_dw(orc, U, dims, M5, mu)
+    g5 = np.kron(np.eye(V), np.kron(np.diag([1, 1, -1, -1]), np.eye(3))).astype(complex)
+    one = np.eye(n)
+    Tinv = one.astype(complex)
+    for b, c in zip(b5s, c5s):
+        Hs = g5 @ ((b + c) * DW) @ np.linalg.inv(2 * one + (b - c) * DW)
+        Tinv = Tinv @ ((one + Hs) @ np.linalg.inv(one - Hs))
+    eps = (Tinv - one) @ np.linalg.inv(Tinv + one)
+    Dov = 0.5 * (1 + m) * one + 0.5 * (1 - m) * g5 @ eps
+    assert np.allclose(K[:n, :n], Dov, atol=1e-11)
+    assert np.allclose(K[:, n:], np.eye(Ls * n)[:, n:], atol=1e-11)
+    # and the same identity fails if the links carry no mu (the pin sees the phases)
+    DW0 = _dense_dw(orc, U, dims, M5, 0.0)
+    T0 = one.astype(complex)
+    for b, c in zip(b5s, c5s):
+        Hs = g5 @ ((b + c) * DW0) @ np.linalg.inv(2 * one + (b - c) * DW0)
+        T0 = T0 @ ((one + Hs) @ np.linalg.inv(one - Hs))
+    Dov0 = 0.5 * (1 + m) * one + 0.5 * (1 - m) * g5 @ ((T0 - one) @ np.linalg.inv(T0 + one))
+    assert not np.allclose(K[:n, :n], Dov0, atol=1e-6)
