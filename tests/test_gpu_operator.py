@@ -18,6 +18,7 @@ import oracle
 import paper_1206_5214_gb300 as mdwf
 import synthetic as sy
 from _gpu import Ctx, rel_err
+from _pins import gauge_rotate, rotate_field
 
 pytestmark = pytest.mark.gpu
 
@@ -133,6 +134,28 @@ def test_adjoint_identity_f64():
         mdx = c.apply(x, F64, dagger=True)[0]
     lhs, rhs = np.vdot(x, my), np.vdot(mdx, y)
     assert abs(lhs - rhs) <= 1e-13 * abs(lhs)
+
+
+@pytest.mark.parametrize("prec", [F64, F32])
+def test_gauge_covariance(prec):
+    """M[U^Omega](Omega psi) = Omega M[U] psi and likewise for M^dag, with a random SU(3)
+    Omega(x) per site and U^Omega_mu(x) = Omega(x) U_mu(x) Omega(x+mu)^dag, on an
+    anisotropic 4x4x2x6 lattice (Ls = 6) so that forward and backward neighbours differ."""
+    dims, Ls = (4, 4, 2, 6), 6
+    U, odd, p = setup(dims, Ls, 1.5, 0.5, 0.02, 0.3, 5)
+    Om = sy.gauge_transform(dims, 3005)
+    UO = gauge_rotate(U, Om)
+
+    def rot(f):
+        return oracle.split(rotate_field(oracle.join(np.zeros_like(f), f, dims), Om), dims)[1]
+
+    with Ctx(dims, Ls, 1.8, 1.5, 0.5, 0.02, U) as c:
+        a, ad = c.apply(odd, prec)[0], c.apply(odd, prec, dagger=True)[0]
+    with Ctx(dims, Ls, 1.8, 1.5, 0.5, 0.02, UO) as c:
+        b, bd = c.apply(rot(odd), prec)[0], c.apply(rot(odd), prec, dagger=True)[0]
+    tol = 2 * TOL_MAX[prec]          # two GPU results, each within TOL_MAX of the exact one
+    assert rel_err(b, rot(a))[0] <= tol
+    assert rel_err(bd, rot(ad))[0] <= tol
 
 
 def test_linearity_and_zero():
