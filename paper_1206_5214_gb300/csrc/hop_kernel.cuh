@@ -639,12 +639,22 @@ template <int P> struct FuseArgs {
     const double* sc;                  // CG scalars [slot][kMaxRhs]
 };
 
-__device__ __forceinline__ double block_sum128(double v, double* red) {
+// Block sum of the epilogue's squared norms: the lanes of a warp add in the
+// precision A of their partial (a fixed shuffle tree), each warp's sum goes
+// to FP64, and thread 0 adds the warps in FP64 in a fixed order. For the FP32
+// and FP16+norm operators A is FP32: a lane sums its 24 squares and the warp
+// tree 32 lanes, so the rounding is bounded by about 28 ulp of the warp sum
+// (2e-6 relative), the FP32 rounding of the vectors themselves; the sums over
+// warps and blocks, which the CG scalars take, stay in FP64. Squares and
+// conversions in FP64 per element would put 48 FP64 instructions per thread
+// on a pipe that runs at 1/64 of the FP32 rate.
+template <typename A>
+__device__ __forceinline__ double block_sum128(A v, double* red) {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nthr = blockDim.x * blockDim.y;
-    if ((tid & 31) == 0) red[tid >> 5] = v;
+    if ((tid & 31) == 0) red[tid >> 5] = (double)v;
     __syncthreads();
     double tot = 0;
     if (tid == 0)
@@ -803,12 +813,12 @@ __global__ void __launch_bounds__(128, STAGE == 1   ? MDWF_MINB_STAGE
         out.store(rbase + site, s, res);
         return;
     }
-    double sq = 0;
+    R sq = 0;  // squared norm partial in the operator's arithmetic precision
     if (FUSE == FUSE_T) {
         if (active) {
             out.store(rbase + site, s, res);
 #pragma unroll
-            for (int k = 0; k < 24; ++k) sq += (double)res[k] * (double)res[k];
+            for (int k = 0; k < 24; ++k) sq = fma(res[k], res[k], sq);
         }
         // v = A^dag t through the same column machinery
         __syncthreads();
@@ -839,7 +849,7 @@ __global__ void __launch_bounds__(128, STAGE == 1   ? MDWF_MINB_STAGE
 #pragma unroll
             for (int k = 0; k < 24; ++k) {
                 rv[k] -= alpha * (RR)res[k];
-                sq += (double)rv[k] * (double)rv[k];
+                sq = fma((R)rv[k], (R)rv[k], sq);
             }
             fa.rf.store(rbase + site, s, rv);
         }
