@@ -183,7 +183,10 @@ int mdwf_apply_dag(mdwf_ctx *ctx, void *out, const void *in, int prec, int nrhs,
  * process exits: at most 8 MiB per intermediate field, i.e.
  * mdwf_field_bytes(ctx, prec, nrhs) <= 8 MiB (MDWF_EINVAL with a message in
  * mdwf_last_error() otherwise; also MDWF_EINVAL for a context created with
- * dense_s = 1). The per-rhs masses are copied into a fixed array as well.
+ * dense_s = 1, for a mass that is not finite, and for a mass at which
+ * I = M+ + M- C is singular, as mdwf_apply reports it). The per-rhs masses
+ * are passed by value to a kernel that writes them into a fixed device array;
+ * the caller's mf_per_rhs buffer is not read after the call returns.
  * The first call on a device looks up the scratch's device address (once
  * per device); make that first call before any stream capture.
  * All calls share the scratch and keep the last call's contents (every call

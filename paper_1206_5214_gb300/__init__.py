@@ -25,12 +25,13 @@ __all__ = [
     "mdwf_strerror", "mdwf_force", "mdwf_apply_noalloc", "mdwf_autotune", "mdwf_set_tuning",
     "mdwf_get_tuning", "mdwf_set_staging", "mdwf_get_staging", "mdwf_device_status", "mdwf_selftest_wait",
     "mdwf_profile_enable", "mdwf_profile_read", "mdwf_counters", "SolveParams", "SolveInfo", "KernelStat",
-    "MDWF_OK", "MDWF_ETIMEOUT", "STAGE_AUTO", "STAGE_CP_ASYNC", "STAGE_BULK", "STAGE_PREFETCH", "STAGE_REGISTERS",
+    "MDWF_OK", "MDWF_EINVAL", "MDWF_ENOMEM", "MDWF_ECUDA", "MDWF_ENOCONV", "MDWF_EBREAKDOWN", "MDWF_ETIMEOUT",
+    "MDWF_ENOGAUGE", "STAGE_AUTO", "STAGE_CP_ASYNC", "STAGE_BULK", "STAGE_PREFETCH", "STAGE_REGISTERS",
 ]
 
 MDWF_F64, MDWF_F32, MDWF_F16N = 0, 1, 2
 MDWF_HOST, MDWF_DEVICE = 0, 1
-MDWF_OK, MDWF_ETIMEOUT = 0, 6
+MDWF_OK, MDWF_EINVAL, MDWF_ENOMEM, MDWF_ECUDA, MDWF_ENOCONV, MDWF_EBREAKDOWN, MDWF_ETIMEOUT, MDWF_ENOGAUGE = range(8)
 _lib = None
 
 

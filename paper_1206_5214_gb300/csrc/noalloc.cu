@@ -12,6 +12,10 @@
 // arrays that every GPU loading this library holds until the process exits.
 // Host code cannot use those array names as device addresses: the device
 // address of each is fetched once per device with cudaGetSymbolAddress.
+// The masses of a call travel as kernel arguments (by value) to a one-block
+// kernel that writes them into their fixed arrays, stream-ordered before the
+// operator's kernels: no host buffer has to outlive the call.
+#include <math.h>
 #include <stdio.h>
 
 #include <mutex>
@@ -57,6 +61,21 @@ static int noalloc_setup(int device, NoAllocAddrs** out) {
     return MDWF_OK;
 }
 
+// The masses of one call, passed by value.
+struct NoAllocMasses {
+    double m64[64];
+    float m32[64];
+    int n;
+};
+
+__global__ void k_noalloc_masses(NoAllocMasses m) {
+    const int r = threadIdx.x;
+    if (r < m.n) {
+        g_noalloc_mass64[r] = m.m64[r];
+        g_noalloc_mass32[r] = m.m32[r];
+    }
+}
+
 }  // namespace mdwf
 
 using namespace mdwf;
@@ -81,22 +100,41 @@ extern "C" int mdwf_apply_noalloc(mdwf_ctx* c, void* out, const void* in, int pr
         set_error_message(msg);
         return MDWF_EINVAL;
     }
+    // the masses: finite, and I = M+ + M- C invertible for each. The closed form
+    // (Sec. 3) divides by M+ (1 + m (-r)^Ls), r = M-/M+, the determinant of one
+    // chirality's I over M+^Ls; the same test as the dense tables' inversion.
+    {
+        const double Mp = c->b5 * (4.0 - c->M5) + 1.0, Mm = c->c5 * (4.0 - c->M5) - 1.0;
+        const double scale = 1.0 + fabs(4.0 - c->M5) * fmax(fabs(c->b5), fabs(c->c5));
+        for (int r = 0; r < nrhs; ++r) {
+            const double m = mf_per_rhs ? mf_per_rhs[r] : c->mf;
+            if (!isfinite(m)) {
+                set_error_message("mdwf_apply_noalloc: a mass is not finite");
+                return MDWF_EINVAL;
+            }
+            const double rr = Mm / Mp;
+            double pw = 1.0;
+            for (int s = 0; s < c->g.Ls; ++s) pw *= -rr;
+            const double den = Mp * (1.0 + m * pw);
+            if (!isfinite(den) || fabs(den) <= 1e-12 * scale) {
+                set_error_message("the Ls x Ls matrix I = M+ + M- C is singular for these coefficients");
+                return MDWF_EINVAL;
+            }
+        }
+    }
     int st;
     if ((st = cuda_status(cudaSetDevice(c->device)))) return st;
     NoAllocAddrs* a = nullptr;
     if ((st = noalloc_setup(c->device, &a))) return st;
     // masses of this call into the fixed arrays (stream-ordered before the kernels)
-    double m64[64];
-    float m32[64];
+    NoAllocMasses ms{};
+    ms.n = nrhs;
     for (int r = 0; r < nrhs; ++r) {
-        m64[r] = mf_per_rhs ? mf_per_rhs[r] : c->mf;
-        m32[r] = (float)m64[r];
+        ms.m64[r] = mf_per_rhs ? mf_per_rhs[r] : c->mf;
+        ms.m32[r] = (float)ms.m64[r];
     }
-    if ((st = cuda_status(cudaMemcpyAsync(a->mass64, m64, sizeof(double) * nrhs, cudaMemcpyHostToDevice, c->stream))))
-        return st;
-    if ((st = cuda_status(cudaMemcpyAsync(a->mass32, m32, sizeof(float) * nrhs, cudaMemcpyHostToDevice, c->stream))))
-        return st;
-    // the host arrays above are pageable: the copies have consumed them when cudaMemcpyAsync returns
+    k_noalloc_masses<<<1, 64, 0, c->stream>>>(ms);
+    if ((st = check_launch())) return st;
     void* z = a->scratch;
     void* v = a->scratch + kNoAllocFieldBytes;
     const void* mass = prec == MDWF_F64 ? (const void*)a->mass64 : (const void*)a->mass32;
