@@ -32,6 +32,8 @@ __all__ = [
     "gaussian_field",
     "point_sources",
     "unit_gauge",
+    "gaussian_field_device",
+    "point_sources_device",
 ]
 
 
@@ -115,4 +117,32 @@ def point_sources(dims, Ls: int, origin=(0, 0, 0, 0)) -> np.ndarray:
             k = 3 * spin + col
             s = 0 if spin >= 2 else Ls - 1
             b[k, s, ot, oz, oy, ox, spin, col] = 1.0
+    return b
+
+
+def gaussian_field_device(dims, Ls: int, seed: int, nrhs: int, device="cuda"):
+    """A batch of ``nrhs`` Gaussian 5d fields drawn on ``device`` by torch's
+    seeded generator (every real component N(0, 1)), for workloads whose
+    host-side draw would take minutes (tens of GB). Same shape and
+    distribution as :func:`gaussian_field`, a different stream of numbers.
+    Shape (nrhs, Ls, T, Z, Y, X, 4, 3), complex128.
+    """
+    import torch
+    x, y, z, t = (int(d) for d in dims)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    re_im = torch.randn((nrhs, Ls, t, z, y, x, 4, 3, 2), dtype=torch.float64, device=device, generator=g)
+    return torch.view_as_complex(re_im)
+
+
+def point_sources_device(dims, Ls: int, origin=(0, 0, 0, 0), device="cuda"):
+    """:func:`point_sources` built directly in device memory (a torch tensor)."""
+    import torch
+    x, y, z, t = (int(d) for d in dims)
+    ox, oy, oz, ot = origin
+    b = torch.zeros((12, Ls, t, z, y, x, 4, 3), dtype=torch.complex128, device=device)
+    for spin in range(4):
+        for col in range(3):
+            s = 0 if spin >= 2 else Ls - 1
+            b[3 * spin + col, s, ot, oz, oy, ox, spin, col] = 1.0
     return b

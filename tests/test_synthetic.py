@@ -72,3 +72,18 @@ def test_unit_gauge_and_transform():
     g = sy.gauge_transform((2, 2, 2, 2), 3001).reshape(-1, 3, 3)
     assert np.abs(np.einsum("nij,nkj->nik", g, np.conj(g)) - np.eye(3)).max() < 1e-13
     assert np.abs(np.linalg.det(g) - 1.0).max() < 1e-13
+
+
+def test_device_generators_match_the_host_recipe():
+    """The torch-side draws used for the largest batched workloads: the same
+    shapes and distribution as the host recipe, reproducible by seed, and the
+    same placement of the point sources."""
+    torch = __import__("pytest").importorskip("torch")
+    f = sy.gaussian_field_device((8, 8, 4, 4), 8, 2005, nrhs=2, device="cpu")
+    assert f.shape == (2, 8, 4, 4, 8, 8, 4, 3) and f.dtype == torch.complex128
+    x = torch.cat([f.real.ravel(), f.imag.ravel()]).numpy()
+    assert abs(x.mean()) < 0.02 and abs(x.var() - 1.0) < 0.02
+    assert torch.equal(f, sy.gaussian_field_device((8, 8, 4, 4), 8, 2005, nrhs=2, device="cpu"))
+    assert not torch.equal(f, sy.gaussian_field_device((8, 8, 4, 4), 8, 2006, nrhs=2, device="cpu"))
+    b = sy.point_sources_device((4, 2, 2, 2), 6, origin=(1, 0, 1, 0), device="cpu")
+    assert np.array_equal(b.numpy(), sy.point_sources((4, 2, 2, 2), 6, origin=(1, 0, 1, 0)))
