@@ -94,6 +94,54 @@ typedef struct {
 int mdwf_create(mdwf_ctx **out, const int dims[4], int Ls, double M5, double b5, double c5,
                 double mf, const mdwf_opts *opts);
 
+/*
+ * Domain decomposition along t (Sec. 3: the Ls x Ls factors are site-local,
+ * so only the 4d hopping term couples sub-lattices; the fifth dimension is
+ * never split). The lattice {X, Y, Z, T} is cut into n slabs of T/n
+ * t-slices each, slab r holding global t = r T/n .. (r+1) T/n - 1; T/n must be
+ * even (so that every slab keeps the global even/odd parity) and >= 2.
+ *
+ * mdwf_create_slab creates the context of one slab: local_dims = {X, Y, Z, T/n},
+ * other arguments as for mdwf_create. Load the slab's own links with
+ * mdwf_load_gauge (the gauge field restricted to its t-slices, user layout)
+ * and import its fields with mdwf_field_import (its odd sites in user order:
+ * the contiguous block of the global odd sites that lie in the slab). A slab
+ * context applies its operator only through mdwf_slab_stage; every other
+ * operator, solve or force call on it returns MDWF_EINVAL.
+ */
+int mdwf_create_slab(mdwf_ctx **out, const int local_dims[4], int Ls, double M5, double b5, double c5,
+                     double mf, const mdwf_opts *opts);
+
+/*
+ * Bytes of one face buffer of a slab: both faces, [face 0 | face 1], each
+ * [rhs][site of one parity in a t-slice][half spinor, 12 reals][s] in the
+ * precision's reals (FP64 or FP32). 0 for a context that is not a slab or
+ * for MDWF_F16N.
+ */
+size_t mdwf_slab_face_bytes(const mdwf_ctx *ctx, int prec, int nrhs);
+
+/*
+ * One stage of out = M in (dagger = 0) or M^dag in (dagger = 1) on a slab,
+ * for nrhs internal odd fields of precision MDWF_F64 or MDWF_F32 (device).
+ * The three stages run in order with the same prec, nrhs, mf_per_rhs and
+ * dagger; between them the caller delivers the faces:
+ *   stage 0: reads in; writes the faces of the first factor's output into send;
+ *   stage 1: reads recv (the neighbours' stage-0 faces); first hop; writes the
+ *            faces of its output into send;
+ *   stage 2: reads recv (the neighbours' stage-1 faces) and in; writes out.
+ * send and recv are caller-owned device buffers of mdwf_slab_face_bytes bytes.
+ * Delivery: face 0 of slab r's send goes to face 0 of slab r-1's recv, face 1
+ * of slab r's send to face 1 of slab r+1's recv (periodic in r); face 0 holds
+ * the t' = 0 slice projected with the forward t-projector of the receiving
+ * hop, face 1 the t' = T/n - 1 slice projected with the backward one and
+ * multiplied by the sender's U_t^dag. The slab keeps its intermediate fields
+ * between the stages (do not interleave other operator calls on it).
+ * Errors: MDWF_EINVAL (not a slab, F16N, bad stage or pointer, per-slice
+ * coefficients), MDWF_ENOGAUGE, MDWF_ENOMEM, MDWF_ECUDA.
+ */
+int mdwf_slab_stage(mdwf_ctx *ctx, int stage, void *out, const void *in, int prec, int nrhs,
+                    const double *mf_per_rhs, int dagger, void *send, const void *recv);
+
 /* Frees the context and its workspace (synchronises the context's stream). NULL is accepted. */
 int mdwf_destroy(mdwf_ctx *ctx);
 

@@ -17,7 +17,7 @@ from . import build as _build
 
 __all__ = [
     "MDWF_F64", "MDWF_F32", "MDWF_F16N", "MdwfError", "lib_path", "load",
-    "mdwf_create", "mdwf_destroy", "mdwf_set_stream", "mdwf_set_s_coefficients", "mdwf_get_s_coefficients",
+    "mdwf_create", "mdwf_destroy", "mdwf_create_slab", "mdwf_slab_face_bytes", "mdwf_slab_stage", "mdwf_set_stream", "mdwf_set_s_coefficients", "mdwf_get_s_coefficients",
     "mdwf_set_chemical_potential",
     "mdwf_load_gauge", "mdwf_field_bytes",
     "mdwf_field_import", "mdwf_field_export", "mdwf_apply", "mdwf_apply_dag", "mdwf_cgne",
@@ -89,6 +89,10 @@ def load(build_if_missing: bool = True):
         "mdwf_create": (ip, [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), ip, ctypes.c_double,
                              ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_Opts)]),
         "mdwf_destroy": (ip, [vp]),
+        "mdwf_create_slab": (ip, [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), ip, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_Opts)]),
+        "mdwf_slab_face_bytes": (sz, [vp, ip, ip]),
+        "mdwf_slab_stage": (ip, [vp, ip, vp, vp, ip, ip, dp, ip, vp, vp]),
         "mdwf_set_stream": (ip, [vp, vp]),
         "mdwf_set_s_coefficients": (ip, [vp, dp, dp]),
         "mdwf_set_chemical_potential": (ip, [vp, ctypes.c_double]),
@@ -177,6 +181,30 @@ def _stream_handle(stream) -> int | None:
     if hasattr(stream, "cuda_stream"):
         return stream.cuda_stream
     return int(stream)
+
+
+def mdwf_create_slab(local_dims, Ls: int, M5: float, b5: float, c5: float, mf: float, stream=None,
+                     device: int = -1, dense_s: bool = False):
+    """Context of one t-slab of a lattice split along t (local_dims = (X, Y, Z, T/n))."""
+    lib = load()
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int * 4)(*[int(x) for x in local_dims])
+    opts = _Opts(_stream_handle(stream), int(device), int(bool(dense_s)), 0)
+    _check(lib.mdwf_create_slab(ctypes.byref(h), d, int(Ls), float(M5), float(b5), float(c5), float(mf),
+                                ctypes.byref(opts)), "mdwf_create_slab")
+    return h.value
+
+
+def mdwf_slab_face_bytes(ctx, prec: int, nrhs: int = 1) -> int:
+    return int(load().mdwf_slab_face_bytes(ctx, int(prec), int(nrhs)))
+
+
+def mdwf_slab_stage(ctx, stage: int, out, inp, prec: int, nrhs: int = 1, mf_per_rhs=None, dagger: bool = False,
+                    send=None, recv=None) -> None:
+    """One of the three stages of M (or M^dag) on a t-slab; send / recv: face buffers (device)."""
+    ptr = lambda t: None if t is None else _ptr_where(t)[0]
+    _check(load().mdwf_slab_stage(ctx, int(stage), ptr(out), ptr(inp), int(prec), int(nrhs), _masses(mf_per_rhs),
+                                  int(bool(dagger)), ptr(send), ptr(recv)), "mdwf_slab_stage")
 
 
 def mdwf_destroy(ctx) -> None:

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmdwf.so")
-SOURCES = ["api.cu", "dslash.cu", "dslash_f64.cu", "dslash_f32.cu", "dslash_f16n.cu", "m5.cu", "layout.cu", "cg.cu", "force.cu", "noalloc.cu", "overlap.cu", "hmc4d.cu"]
+SOURCES = ["api.cu", "dslash.cu", "dslash_f64.cu", "dslash_f32.cu", "dslash_f16n.cu", "m5.cu", "layout.cu", "cg.cu", "force.cu", "noalloc.cu", "overlap.cu", "hmc4d.cu", "slab.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

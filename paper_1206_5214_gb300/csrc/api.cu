@@ -424,26 +424,11 @@ int device_wait_status(mdwf_ctx* c) {
 
 }  // namespace mdwf
 
-extern "C" {
+namespace mdwf {
 
-const char* mdwf_strerror(int status) {
-    switch (status) {
-        case MDWF_OK: return "MDWF_OK";
-        case MDWF_EINVAL: return "MDWF_EINVAL: invalid argument";
-        case MDWF_ENOMEM: return "MDWF_ENOMEM: out of memory";
-        case MDWF_ECUDA: return "MDWF_ECUDA: CUDA runtime error";
-        case MDWF_ENOCONV: return "MDWF_ENOCONV: solver did not converge";
-        case MDWF_EBREAKDOWN: return "MDWF_EBREAKDOWN: CG breakdown";
-        case MDWF_ETIMEOUT: return "MDWF_ETIMEOUT: device wait limit reached";
-        case MDWF_ENOGAUGE: return "MDWF_ENOGAUGE: no gauge field loaded";
-    }
-    return "unknown mdwf status";
-}
-
-const char* mdwf_last_error(void) { return g_last_error; }
-
-int mdwf_create(mdwf_ctx** out, const int dims[4], int Ls, double M5, double b5, double c5, double mf,
-                const mdwf_opts* opts) {
+// Context creation; slab: a t-slab of a lattice split along t (mdwf_create_slab).
+static int create_context(mdwf_ctx** out, const int dims[4], int Ls, double M5, double b5, double c5, double mf,
+                         const mdwf_opts* opts, bool slab) {
     if (!out || !dims) return MDWF_EINVAL;
     *out = nullptr;
     for (int mu = 0; mu < 4; ++mu)
@@ -471,6 +456,7 @@ int mdwf_create(mdwf_ctx** out, const int dims[4], int Ls, double M5, double b5,
         c->dense_s_base = c->dense_s;
     }
     c->autotune = opts && opts->autotune;
+    c->slab = slab;
     // the default mass tables, so that an apply needs no host round trip
     if ((st = ensure_tables(c, 1, nullptr)) ||
         (st = cuda_status(cudaMalloc(&c->nbr, sizeof(int) * 16 * (size_t)c->g.Vh))) ||
@@ -482,6 +468,36 @@ int mdwf_create(mdwf_ctx** out, const int dims[4], int Ls, double M5, double b5,
     }
     *out = c;
     return MDWF_OK;
+}
+
+}  // namespace mdwf
+
+extern "C" {
+
+const char* mdwf_strerror(int status) {
+    switch (status) {
+        case MDWF_OK: return "MDWF_OK";
+        case MDWF_EINVAL: return "MDWF_EINVAL: invalid argument";
+        case MDWF_ENOMEM: return "MDWF_ENOMEM: out of memory";
+        case MDWF_ECUDA: return "MDWF_ECUDA: CUDA runtime error";
+        case MDWF_ENOCONV: return "MDWF_ENOCONV: solver did not converge";
+        case MDWF_EBREAKDOWN: return "MDWF_EBREAKDOWN: CG breakdown";
+        case MDWF_ETIMEOUT: return "MDWF_ETIMEOUT: device wait limit reached";
+        case MDWF_ENOGAUGE: return "MDWF_ENOGAUGE: no gauge field loaded";
+    }
+    return "unknown mdwf status";
+}
+
+const char* mdwf_last_error(void) { return g_last_error; }
+
+int mdwf_create(mdwf_ctx** out, const int dims[4], int Ls, double M5, double b5, double c5, double mf,
+                const mdwf_opts* opts) {
+    return mdwf::create_context(out, dims, Ls, M5, b5, c5, mf, opts, false);
+}
+
+int mdwf_create_slab(mdwf_ctx** out, const int local_dims[4], int Ls, double M5, double b5, double c5, double mf,
+                     const mdwf_opts* opts) {
+    return mdwf::create_context(out, local_dims, Ls, M5, b5, c5, mf, opts, true);
 }
 
 int mdwf_destroy(mdwf_ctx* c) {

@@ -338,12 +338,16 @@ static int init_w(Solver& S, void* w, const void* p) {
 //   z = K H_eo M_phi p;  t = p - 1/4 A H_oe z, v = A^dag t, |t|^2 (-> alpha);
 //   z = K^dag H'_eo v;   r -= alpha (t - 1/4 M_phi^dag H'_oe z), |r|^2 (-> beta);
 //   x += alpha p, p = r + beta p.
+//   Where the closed-form s-operators run by shuffles (Ls = 16), t is not
+//   stored: K2' forms it again as t = I^dag v from v = A^dag t, a bidiagonal
+//   s-operator, which saves one field write per iteration.
 template <int PR, int PP>
 static int cg_iteration_fused(Solver& S, void* x, void* r, void* p, void* t, void* w) {
     mdwf_ctx* c = S.c;
     int st;
     note_apply(c, PP);
     note_apply(c, PP);
+    const bool no_t = hop_no_t_ok(c, PP, S.nrhs);
     HopLaunch h{};
     h.nrhs = S.nrhs;
     h.b5 = c->b5;
@@ -361,17 +365,19 @@ static int cg_iteration_fused(Solver& S, void* x, void* r, void* p, void* t, voi
         set_sop(c, PP, SOP_A, 1, a);
         h.mat2 = a.mat;
     }
-    h.fuse = 1; h.out2 = c->tmp[1].p; h.part = S.hpart; h.sc = S.sc;
+    h.fuse = 1; h.out2 = c->tmp[1].p; h.part = S.hpart; h.sc = S.sc; h.no_t = no_t;
     if ((st = launch_hop(c, PP, h))) return st;
     h.mat2 = nullptr;
+    h.no_t = 0;
     if ((st = S.fin_hop(FIN_ALPHA))) return st;
     h.out = c->tmp[0].p; h.in = c->tmp[1].p; h.x = nullptr; h.coef = 1.0; h.out_parity = 0; h.dagger = 1;
     set_sop(c, PP, SOP_K, 1, h);
     h.fuse = 0;
     if ((st = launch_hop(c, PP, h))) return st;
-    h.out = c->tmp[1].p; h.in = c->tmp[0].p; h.x = t; h.coef = -0.25; h.out_parity = 1; h.dagger = 1;
+    h.out = c->tmp[1].p; h.in = c->tmp[0].p; h.x = no_t ? c->tmp[1].p : t; h.coef = -0.25; h.out_parity = 1;
+    h.dagger = 1;
     set_sop(c, PP, SOP_MPHI, 1, h);
-    h.fuse = 2; h.rfield = r; h.part = S.hpart; h.sc = S.sc;
+    h.fuse = 2; h.rfield = r; h.part = S.hpart; h.sc = S.sc; h.no_t = no_t;
     if ((st = launch_hop(c, PP, h))) return st;
     if ((st = S.fin_hop(FIN_BETA))) return st;
     return launch_pupd_w<PR, PP>(S, x, r, p, w);

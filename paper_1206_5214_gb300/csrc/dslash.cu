@@ -18,6 +18,18 @@ int hop_sites_per_block(const mdwf_ctx* c, int prec, int nrhs) {
     return sb < 1 ? 1 : sb;
 }
 
+// The fused iteration drops its t field when the FUSE_R epilogue can rebuild
+// t = I^dag v by shuffles: FP32 or FP16+norm operators at Ls = 16 with the
+// closed-form s-operators, whole s-columns in every warp (an even number of
+// sites per block) and a load strategy whose kernels fix Ls = 16 at compile
+// time (not the two shared-memory staging modes).
+bool hop_no_t_ok(const mdwf_ctx* c, int prec, int nrhs) {
+    if (prec == MDWF_F64 || c->g.Ls != 16 || c->dense_s || c->sdep) return false;
+    if (hop_sites_per_block(c, prec, nrhs) & 1) return false;
+    const int mode = c->hop_stage[prec];
+    return mode != 1 && mode != 2;
+}
+
 int hop_blocks(const mdwf_ctx* c, int prec, int nrhs) {
     const int SB = hop_sites_per_block(c, prec, nrhs);
     return (int)((c->g.Vh + SB - 1) / SB);

@@ -136,6 +136,7 @@ int launch_force(mdwf_ctx* c, double* dSdU, const void* A_odd, const void* B_eve
     // even x: forward (gamma_x, delta_{x+mu}), backward (alpha_{x+mu}, beta_x)
     // odd x : forward (alpha_x, beta_{x+mu}), backward (gamma_{x+mu}, delta_x)
     const Geom& g = c->g;
+    if (c->slab) return MDWF_EINVAL;  // the neighbour table of a t-slab points into halos
     const int SB = (128 / g.Ls) < 1 ? 1 : 128 / g.Ls;
     dim3 block(g.Ls, SB), grid((unsigned)((g.Vh + SB - 1) / SB));
     const size_t smem = (size_t)SB * g.Ls * 18 * sizeof(double);

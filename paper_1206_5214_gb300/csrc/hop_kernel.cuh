@@ -54,7 +54,40 @@ template <typename R> struct HopParams {
     bool chem;
     R efwd, ebwd;
     int* err;        // device error word (bounded waits of the bulk variant)
+    // the fused iteration without a t field (Ls = 16, bidiagonal shuffles):
+    // FUSE_T does not store t; FUSE_R forms its addend t = I^dag v from x = v
+    bool no_t;
+    // t-slab (domain decomposition along t): the t-direction neighbours across
+    // the slab's faces are read from halo = [dir][rhs][face site][6 / 3 chunks][s]
+    // half spinors (dir 0: the forward term's projected neighbour, dir 1: the
+    // backward term's neighbour projected and transported by the sending slab);
+    // the neighbour table marks them as -1 - face site
+    const void* halo;
+    long long face;  // 4d sites of one parity in one t-slice
 };
+
+// One half spinor (12 reals) of a slab halo: chunk k of (dir, rhs, face site f,
+// slice s), in the layout of the precision's field chunks.
+template <int P, typename R>
+__device__ __forceinline__ void halo_load(const HopParams<R>& hp, int dir, long long rf, int s, R* h) {
+    const int Ls = hp.g.Ls;
+    const long long base = ((long long)dir * hp.nrhs * hp.face + rf) * (P == MDWF_F64 ? 6 : 3) * Ls + s;
+    if constexpr (P == MDWF_F64) {
+        const double2* q = reinterpret_cast<const double2*>(hp.halo) + base;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const double2 d = __ldg(q + (long long)k * Ls);
+            h[2 * k] = d.x; h[2 * k + 1] = d.y;
+        }
+    } else {
+        const float4* q = reinterpret_cast<const float4*>(hp.halo) + base;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float4 d = __ldg(q + (long long)k * Ls);
+            h[4 * k] = d.x; h[4 * k + 1] = d.y; h[4 * k + 2] = d.z; h[4 * k + 3] = d.w;
+        }
+    }
+}
 
 // --------------------------------------------------------- spin structure
 //
@@ -132,6 +165,19 @@ __device__ __forceinline__ void transport_add(R* acc, const R* U, const R* h, R 
         acc[13 + 2 * i] += S * b0i;
         acc[18 + 2 * i] += S * b1r;
         acc[19 + 2 * i] += S * b1i;
+    }
+}
+
+// Reconstruction alone, for a half spinor g already transported (the backward
+// t-direction term of a slab face, whose link lives on the sending slab):
+// upper half += f g, lower half += f S A_mu^dag g.
+template <int MU, int S, typename R>
+__device__ __forceinline__ void reconstruct_add(R* acc, const R* g, R f) {
+    static_assert(MU == 3, "slab faces are t-faces (A_4 = 1)");
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+        acc[k] = fma(f, g[k], acc[k]);
+        acc[12 + k] = fma(S * f, g[k], acc[12 + k]);
     }
 }
 
@@ -252,12 +298,12 @@ __device__ __forceinline__ void hop_pair64(double* acc, const Field<MDWF_F64>& i
 
 // nbi: the site's eight neighbour indices (x+mu, mu = 0..3, then x-mu), each
 // read just before its term so that none is held in a register across terms
-template <int P, int MU, bool GATHER, bool DAG, typename R>
+template <int P, int MU, bool GATHER, bool DAG, bool DD = false, typename R>
 __device__ __forceinline__ void hop_dir(R* acc, const Field<P>& in, const Gauge<P>& U, const HopParams<R>& hp,
                                         const int* nbi, long long site, int s, long long rbase, R mass,
-                                        R gown, R gfac) {
+                                        R gown, R gfac, int rhs = 0) {
     if constexpr (P == MDWF_F64 && !GATHER) {
-        if (!(MU == 3 && hp.chem)) {
+        if (!(MU == 3 && (hp.chem || DD))) {
             hop_pair64<MU, DAG>(acc, in, U, hp, nbi, site, s, rbase);
             return;
         }
@@ -265,6 +311,39 @@ __device__ __forceinline__ void hop_dir(R* acc, const Field<P>& in, const Gauge<
     const Geom& g = hp.g;
     constexpr int SF = DAG ? +1 : -1;  // forward projector 1 + SF g_mu
     constexpr bool SCALED = P == MDWF_F16N && !GATHER;
+    if constexpr (DD && MU == 3) {
+        // slab faces: the neighbour across a face comes from the halo
+        const int jf = __ldg(nbi + 3), jb = __ldg(nbi + 7);
+        if (jf < 0) {
+            R h[12], u[18];
+            halo_load<P>(hp, 0, (long long)rhs * hp.face + (-1 - jf), s, h);
+            U.load(((long long)hp.out_parity * 4 + 3) * g.Vh + site, u);
+            transport_add<false, 3, SF>(acc, u, h, hp.efwd, hp.chem);
+        }
+        if (jb < 0) {
+            R h[12];
+            halo_load<P>(hp, 1, (long long)rhs * hp.face + (-1 - jb), s, h);
+            reconstruct_add<3, -SF>(acc, h, hp.chem ? hp.ebwd : R(1));
+        }
+        if (jf < 0 && jb < 0) return;
+        if (jf < 0 || jb < 0) {
+            // the other term of this direction lies inside the slab
+            const bool fwd = jb < 0;
+            const long long j = fwd ? jf : jb;
+            R w[24], h[12], u[18];
+            const R f = load_input<P, GATHER>(in, rbase + j, s, g.Ls, gown, gfac, mass, w);
+            if (fwd) {
+                project<3, SF>(w, h);
+                U.load(((long long)hp.out_parity * 4 + 3) * g.Vh + site, u);
+                transport_add<false, 3, SF>(acc, u, h, hp.chem ? f * hp.efwd : f, SCALED || hp.chem);
+            } else {
+                project<3, -SF>(w, h);
+                U.load(((long long)(1 - hp.out_parity) * 4 + 3) * g.Vh + j, u);
+                transport_add<true, 3, -SF>(acc, u, h, hp.chem ? f * hp.ebwd : f, SCALED || hp.chem);
+            }
+            return;
+        }
+    }
     {
         const long long jf = __ldg(nbi + MU);
         R w[24], h[12], u[18];
@@ -685,13 +764,14 @@ constexpr bool kShuffleBidiag = MDWF_SHUFFLE_BIDIAG != 0;
 // launcher picks it when Ls matches), or -1 for the run-time choice; one
 // fixed length leaves the other lengths' code and its register demand out of
 // the kernel.
-template <int P, bool GATHER, bool DAG, bool XPAY, int FUSE, int STAGE, int LSR>
+template <int P, bool GATHER, bool DAG, bool XPAY, int FUSE, int STAGE, int LSR, bool DD = false>
 __global__ void __launch_bounds__(128, STAGE == 1   ? MDWF_MINB_STAGE
                                       : STAGE == 3 ? kPrefetchMinBlocks
                                                    : PrecTraits<P>::min_blocks - (GATHER ? 1 : 0))
     hop_kernel(Field<P> out, Field<P> in, Field<P> xf, Gauge<P> U, HopParams<typename PrecTraits<P>::real> hp,
                FuseArgs<P> fa) {
     static_assert(!STAGE || (!GATHER && P != MDWF_F64), "staged loads: FP32 / FP16 operators without gather");
+    static_assert(!DD || (STAGE == 0 && !GATHER && FUSE == FUSE_NONE), "slab halos: plain loads, unfused");
     typedef typename PrecTraits<P>::real R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Ls = hp.g.Ls;
@@ -757,10 +837,10 @@ __global__ void __launch_bounds__(128, STAGE == 1   ? MDWF_MINB_STAGE
             hop_staged<P, DAG>(acc, in, U, hp, st, f, b, site, s, rbase);
         } else {
             const int* nbi = reinterpret_cast<const int*>(nb);
-            hop_dir<P, 0, GATHER, DAG>(acc, in, U, hp, nbi, site, s, rbase, mass, gown, gfac);
-            hop_dir<P, 1, GATHER, DAG>(acc, in, U, hp, nbi, site, s, rbase, mass, gown, gfac);
-            hop_dir<P, 2, GATHER, DAG>(acc, in, U, hp, nbi, site, s, rbase, mass, gown, gfac);
-            hop_dir<P, 3, GATHER, DAG>(acc, in, U, hp, nbi, site, s, rbase, mass, gown, gfac);
+            hop_dir<P, 0, GATHER, DAG, DD>(acc, in, U, hp, nbi, site, s, rbase, mass, gown, gfac, rhs);
+            hop_dir<P, 1, GATHER, DAG, DD>(acc, in, U, hp, nbi, site, s, rbase, mass, gown, gfac, rhs);
+            hop_dir<P, 2, GATHER, DAG, DD>(acc, in, U, hp, nbi, site, s, rbase, mass, gown, gfac, rhs);
+            hop_dir<P, 3, GATHER, DAG, DD>(acc, in, U, hp, nbi, site, s, rbase, mass, gown, gfac, rhs);
         }
     }
     if constexpr (STAGE == 1 || STAGE == 2) __syncthreads();
@@ -800,7 +880,27 @@ __global__ void __launch_bounds__(128, STAGE == 1   ? MDWF_MINB_STAGE
     }
     if (FUSE == FUSE_NONE && !active) return;
     const R cf = hp.coef * hp.gscale;
-    if (XPAY && active) {  // res = cf res + x as one fused multiply-add
+    bool xdone = false;
+    if constexpr (XPAY && FUSE == FUSE_R && LSR == 16) {
+        // x holds v = A^dag t: the addend t = I^dag v, I^dag = M+ + M- C^dag
+        // bidiagonal, by shuffles (every lane takes part; the launcher admits
+        // no_t only where the shuffled s-operators run)
+        if (hp.no_t) {
+            R xv[24], tv[24];
+            if (active) {
+                xf.load(rbase + site, s, xv);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 24; ++k) xv[k] = R(0);
+            }
+            bidiag_shuffle16(xv, tv, s, SOP_MEE, true, hp.sc, mass);
+#pragma unroll
+            for (int k = 0; k < 24; ++k) res[k] = fma(cf, res[k], tv[k]);
+            xdone = true;
+        }
+    }
+    if (xdone) {
+    } else if (XPAY && active) {  // res = cf res + x as one fused multiply-add
         R xv[24];
         xf.load(rbase + site, s, xv);
 #pragma unroll
@@ -816,7 +916,7 @@ __global__ void __launch_bounds__(128, STAGE == 1   ? MDWF_MINB_STAGE
     R sq = 0;  // squared norm partial in the operator's arithmetic precision
     if (FUSE == FUSE_T) {
         if (active) {
-            out.store(rbase + site, s, res);
+            if (!hp.no_t) out.store(rbase + site, s, res);
 #pragma unroll
             for (int k = 0; k < 24; ++k) sq = fma(res[k], res[k], sq);
         }
@@ -860,7 +960,7 @@ __global__ void __launch_bounds__(128, STAGE == 1   ? MDWF_MINB_STAGE
 
 // ---------------------------------------------------------------- launcher
 
-template <int P, bool G, bool D, bool X, int FU, int ST, int LSR>
+template <int P, bool G, bool D, bool X, int FU, int ST, int LSR, bool DD = false>
 static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<typename PrecTraits<P>::real>& hp) {
     typedef typename PrecTraits<P>::real R;
     const Geom& g = c->g;
@@ -871,7 +971,7 @@ static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<t
                          : ST == 2 ? (size_t)2 * BulkBytes<P>::value * g.Ls * SB : 0;
     const int ntab = hp.sop == SOP_DENSE ? (FU == FUSE_T ? 2 : 1) : 0;
     size_t smem = kHopHeader + (size_t)ntab * 2 * g.Ls * g.Ls * sizeof(R) + (rows > stage ? rows : stage);
-    auto kern = hop_kernel<P, G, D, X, FU, ST, LSR>;
+    auto kern = hop_kernel<P, G, D, X, FU, ST, LSR, DD>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_status(e);
@@ -904,7 +1004,7 @@ static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<t
     // fields moved: in, out (+x), and for the fused epilogues v (FUSE_T) or r read+write instead of out (FUSE_R)
     const double sp = site_bytes(P), sr = site_bytes(ResPrec<P>::value);
     double fields = sp + sp + (X ? sp : 0.0);
-    if (FU == FUSE_T) fields += sp;
+    if (FU == FUSE_T && !hp.no_t) fields += sp;  // t (out) and v (out2); no_t stores only v
     if (FU == FUSE_R) fields += 2.0 * sr - sp;
     const double bytes = n5 * fields + 8.0 * g.Vh * link_bytes(P);
     const double flops = n5 * (1320.0 + (G ? 72.0 : 0.0) + 144.0 + (X ? 48.0 : 0.0) + (FU ? 144.0 : 0.0));
@@ -920,6 +1020,10 @@ static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<t
 // Mode 4 uses the plain loads everywhere.
 template <int P, bool G, bool D, bool X, int FU>
 static int launch_hop_pick(mdwf_ctx* c, const HopLaunch& h, const HopParams<typename PrecTraits<P>::real>& hp) {
+    if constexpr (!G && FU == FUSE_NONE && P != MDWF_F16N) {
+        if (h.halo) return launch_hop_variant<P, G, D, X, FU, 0, -1, true>(c, h, hp);
+    }
+    if (h.halo) return MDWF_EINVAL;
     if constexpr (!G && P != MDWF_F64) {
         const int mode = c->hop_stage[P];
         if (mode == 1) return launch_hop_variant<P, G, D, X, FU, 1, -1>(c, h, hp);
@@ -973,7 +1077,19 @@ int launch_hop_t(mdwf_ctx* c, const HopLaunch& h) {
     hp.efwd = (R)exp(h.dagger ? -c->chem : c->chem);
     hp.ebwd = (R)exp(h.dagger ? c->chem : -c->chem);
     hp.err = c->dev_err;
+    hp.no_t = h.no_t != 0;
+    hp.halo = h.halo;
+    hp.face = (long long)c->g.X * c->g.Y * c->g.Z / 2;
+    // a t-slab context reads its t-faces from halos: every hop on it needs them
+    if (c->slab != (h.halo != nullptr)) {
+        set_error_message("a t-slab context applies its hops only through mdwf_slab_stage, with halos");
+        return MDWF_EINVAL;
+    }
     const bool X = h.x != nullptr;
+    if (hp.no_t) {
+        if (!hop_no_t_ok(c, P, h.nrhs) || h.fuse == FUSE_NONE || h.sop == SOP_DENSE) return MDWF_EINVAL;
+        if (h.fuse == FUSE_R && h.sop != SOP_MPHI) return MDWF_EINVAL;
+    }
     if (h.fuse != FUSE_NONE) {
         // fused CG epilogues: t = M p with v = A^dag t, or Ap = M^dag t folded into r
         // (structured s-operators or dense tables)

@@ -95,7 +95,10 @@ __global__ void gauge_pack_kernel(double2* u64, float* u32, const double2* __res
     }
 }
 
-__global__ void neighbour_kernel(int* nbr, Geom g) {
+// On a t-slab (slab != 0) the t-neighbours across the two faces are marked
+// -1 - f, f the site's index within its t-slice (the index of the same
+// (x, y, z) in the neighbouring slab's face), so the hops read them from halos.
+__global__ void neighbour_kernel(int* nbr, Geom g, int slab) {
     const long long n = 2 * g.Vh;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
         const int par = (int)(i / g.Vh);
@@ -110,6 +113,11 @@ __global__ void neighbour_kernel(int* nbr, Geom g) {
             b[mu] = c[mu] == 0 ? L[mu] - 1 : c[mu] - 1;
             o[mu] = (int)cb_index(g, f[0], f[1], f[2], f[3]);
             o[4 + mu] = (int)cb_index(g, b[0], b[1], b[2], b[3]);
+        }
+        if (slab) {
+            const long long face = (long long)g.X * g.Y * g.Z / 2;
+            if (c[3] == g.T - 1) o[3] = -1 - (int)(j % face);
+            if (c[3] == 0) o[7] = -1 - (int)(j % face);
         }
     }
 }
@@ -200,7 +208,7 @@ namespace mdwf {
 int launch_build_neighbours(mdwf_ctx* c) {
     const long long n = 2 * c->g.Vh;
     LaunchScope scope(c, KB_LAYOUT * 3 + MDWF_F64, n * 32.0, 0.0);
-    neighbour_kernel<<<grid_for(n, 256), 256, 0, c->stream>>>(c->nbr, c->g);
+    neighbour_kernel<<<grid_for(n, 256), 256, 0, c->stream>>>(c->nbr, c->g, c->slab ? 1 : 0);
     return check_launch();
 }
 }  // namespace mdwf

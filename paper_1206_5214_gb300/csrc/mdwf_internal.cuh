@@ -657,6 +657,9 @@ struct mdwf_ctx {
     // device word set by a bounded device-side wait that gave up (0 = none)
     int* dev_err = nullptr;
     bool autotune = false;
+    // a t-slab of a lattice split along t (domain decomposition): the t-neighbours
+    // across its two faces are remote and come in as halos (mdwf_slab_stage)
+    bool slab = false;
     // content of the CUDA graph being captured (added once per replay)
     long long cap_launches = 0;
     long long cap_applies[3] = {0, 0, 0};
@@ -736,10 +739,19 @@ struct HopLaunch {
     int fuse;
     void* out2;
     void* rfield;         // FP64 field for FP64 operators, FP32 otherwise
+    // fused CG iteration without the t field (Ls = 16, structured s-operators):
+    // FUSE_T stores only v = A^dag t, not t; FUSE_R takes its xpay addend t as
+    // I^dag v, formed from v (its x) by shuffles across the 16 slices
+    int no_t;
+    // t-slab contexts: the received faces [dir][rhs][face site][half spinor][s]
+    // (HopParams::halo); null on ordinary contexts
+    const void* halo;
     double* part;         // [rhs][hop_blocks] partial sums
     const double* sc;     // CG scalars
 };
 int launch_hop(mdwf_ctx* c, int prec, const HopLaunch& h);
+// whether the fused CG iteration can run without its t field (HopLaunch::no_t)
+bool hop_no_t_ok(const mdwf_ctx* c, int prec, int nrhs);
 int hop_sites_per_block(const mdwf_ctx* c, int prec, int nrhs);
 int hop_blocks(const mdwf_ctx* c, int prec, int nrhs);
 

@@ -90,7 +90,7 @@ def declared_signatures():
 
 def test_every_entry_point_refuses_a_null_context(libpath):
     """Every call that takes a context returns MDWF_EINVAL for a NULL one (MDWF_OK for
-    mdwf_destroy, 0 bytes for mdwf_field_bytes), before any CUDA call: no GPU is needed.
+    mdwf_destroy, 0 bytes for mdwf_field_bytes and mdwf_slab_face_bytes), before any CUDA call: no GPU is needed.
     A separate handle of the library is used, so that the binding's signatures stay as set."""
     lib = ctypes.CDLL(libpath)
     checked = 0
@@ -102,7 +102,7 @@ def test_every_entry_point_refuses_a_null_context(libpath):
         f.restype = ctypes.c_size_t if ret == "size_t" else ctypes.c_int
         args = [None if t is ctypes.c_void_p else t(0).value for t in f.argtypes]
         got = f(*args)
-        expect = {"mdwf_destroy": 0, "mdwf_field_bytes": 0}.get(name, 1)
+        expect = {"mdwf_destroy": 0, "mdwf_field_bytes": 0, "mdwf_slab_face_bytes": 0}.get(name, 1)
         assert got == expect, (name, got)
         checked += 1
     assert checked >= 30

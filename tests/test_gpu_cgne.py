@@ -204,17 +204,35 @@ def test_cgne_nan_source_is_reported_per_rhs(inner):
     assert info[1].status == 5
 
 
+@pytest.mark.parametrize("staged", [0, 1], ids=["no-t-field", "t-field"])
+@pytest.mark.parametrize("b5,c5", [(1.0, 0.0), (1.5, 0.5)], ids=["shamir", "moebius"])
 @pytest.mark.parametrize("inner", [F32, F16N], ids=["mixed-f32", "mixed-f16n"])
-def test_cgne_4x4x4x4_Ls16_matches_oracle(inner):
+def test_cgne_4x4x4x4_Ls16_matches_oracle(inner, b5, c5, staged):
     """Ls = 16 (the fused iteration's Ls-specialised kernels and the shuffled M_phi^dag of
-    its last hop) to 1e-10, checked through the oracle's residuals."""
+    its last hop) to 1e-10, checked through the oracle's residuals. With the default load
+    strategy the iteration keeps no t field (its last hop forms t = I^dag v by shuffles);
+    the cp.async staging keeps and reads t, so both forms are checked."""
     dims, Ls, mf = (4, 4, 4, 4), 16, 0.01
     U = sy.gauge_field(dims, 0.3, 1092)
     b = sy.gaussian_field(dims, Ls, 2092)
-    p = oracle.Params(dims, Ls, 1.8, 1.5, 0.5, mf)
-    st, info, x = gpu_solve(dims, Ls, 1.5, 0.5, mf, U, b, inner)
+    p = oracle.Params(dims, Ls, 1.8, b5, c5, mf)
+    st, info, x = gpu_solve(dims, Ls, b5, c5, mf, U, b, inner, staged=staged)
     assert st == 0 and info[0].true_res <= 1e-10
     assert oracle_residual(x, b, U, p) <= 1.05e-10
+
+
+def test_cgne_Ls16_multi_mass_without_t_field():
+    """Three masses in one Ls = 16 mixed FP32 solve with the t field dropped: each
+    right-hand side's I^dag takes its own mass in the wrap-around term."""
+    dims, Ls = (4, 4, 4, 4), 16
+    masses = [0.005, 0.05, 0.3]
+    U = sy.gauge_field(dims, 0.3, 1095)
+    b = sy.gaussian_field(dims, Ls, 2095, nrhs=3)
+    st, info, x = gpu_solve(dims, Ls, 1.5, 0.5, 0.01, U, b, F32, nrhs=3, masses=masses)
+    assert st == 0 and all(i.true_res <= 1e-10 for i in info)
+    for r, m in enumerate(masses):
+        p = oracle.Params(dims, Ls, 1.8, 1.5, 0.5, m)
+        assert oracle_residual(x[r], b[r], U, p) <= 1.05e-10, r
 
 
 def test_cgne_max_batch():
