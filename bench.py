@@ -35,10 +35,13 @@ DIMS = (16, 16, 16, 32)
 LS, M5, B5, C5, MF, EPS = 16, 1.8, 1.5, 0.5, 0.01, 0.2
 GAUGE_SEED, SOURCE_SEED = 1002, 2002
 FLOPS_PER_SITE = 3120.0      # per odd 5d site and M (or M^dag) application
-# DRAM bytes (read + write) per launch of a kernel in this workload's solve, from one
-# ncu capture of the kernels as they are now (summarised under profiles/); a kernel
-# that changes drops out of this table until it is captured again.
-NCU_TRAFFIC = {"hop_xpay_f32": 252.167936e6 + 167.096064e6}
+# DRAM bytes (read + write) per launch of a kernel in this workload's solve come from one
+# ncu capture, recorded (a JSON block) in profiles/dram_traffic.md with the SHA-256 of the
+# kernel's sources at capture time; a record whose hash differs from the sources as they
+# are now is stale and is not reported.
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.md")
+KERNEL_SOURCES = ("paper_1206_5214_gb300/csrc/hop_kernel.cuh", "paper_1206_5214_gb300/csrc/mdwf_internal.cuh",
+                  "paper_1206_5214_gb300/csrc/mbarrier.cuh")
 METRIC = "Moebius Dslash GFLOP/s in CGNE to 1e-10 (mixed FP32/FP64)"
 # spectrum bounds of the Zolotarev coefficients of the per-slice solve: the upper one is
 # lambda_max = (8 - M5) / (10 - M5) of the Shamir kernel at M5 = 1.8 (Sec. 2)
@@ -48,6 +51,17 @@ FORCE_MF, FORCE_SEED = 0.02, 2004
 # the 4d field of the overlap application and the wall force, and the chemical potential
 OVERLAP_SEED, CHEM_MU = 2005, 0.1
 N5 = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3] // 2 * LS
+# the batched workloads: 12 spin-colour point sources on 24^3 x 64, Ls = 12 (mixed FP32), and
+# 8 Gaussian sources at 8 masses on 32^3 x 64, Ls = 16 (mixed FP16+norm, autotuned tiles)
+BATCHED = {
+    "c3_12_point_sources": {"dims": (24, 24, 24, 64), "Ls": 12, "mf": [0.005] * 12, "eps": 0.2, "cfg": 3,
+                            "inner": "f32", "sources": "point", "autotune": False, "buffers": "device"},
+    # 8 x 6.4 GB sources and solutions do not fit in HBM beside the solver's FP64 fields:
+    # they stay in host memory and the library moves them (timed)
+    "c5_8_masses": {"dims": (32, 32, 32, 64), "Ls": 16,
+                    "mf": [0.001, 0.002, 0.005, 0.01, 0.02, 0.03, 0.04, 0.05], "eps": 0.15, "cfg": 5,
+                    "inner": "f16n", "sources": "gaussian", "autotune": True, "buffers": "host"},
+}
 
 
 def workload_config(inner: str) -> dict:
@@ -55,6 +69,33 @@ def workload_config(inner: str) -> dict:
             "lattice": list(DIMS), "Ls": LS, "M5": M5, "b5": B5, "c5": C5, "mf": MF, "eps": EPS,
             "nrhs": 1, "tol": 1e-10, "inner": inner,
             "l2": "256 MB buffer written between timed steps (L2 129 MB); each step streams > 1 GB"}
+
+
+def kernel_sources_sha256(files=KERNEL_SOURCES, root=ROOT) -> str:
+    """SHA-256 over the hop kernels' source files, in a fixed order."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(root, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read() + b"\0")
+    return h.hexdigest()
+
+
+def recorded_traffic(name: str, path: str = TRAFFIC_FILE, current_sha: str | None = None) -> tuple:
+    """(DRAM bytes per launch, note) of kernel `name` from the capture record, or
+    (None, why) when there is no record or the sources changed since the capture."""
+    try:
+        text = open(path).read()
+        block = text.split("```json", 1)[1].split("```", 1)[0]
+        rec = json.loads(block)["kernels"].get(name)
+    except (OSError, ValueError, KeyError, IndexError):
+        return None, "no capture record"
+    if not rec:
+        return None, f"no capture of {name}"
+    sha = current_sha or kernel_sources_sha256()
+    if rec.get("sources_sha256") != sha:
+        return None, "stale: the kernel sources changed since the capture"
+    return rec["dram_read_bytes"] + rec["dram_write_bytes"], f"ncu capture, {rec.get('summary', '')}"
 
 
 def parse():
@@ -71,6 +112,9 @@ def parse():
                     help="only the warm-up and timed solves (a short, fixed launch sequence for ncu)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the per-precision Dslash loops, the second inner precision and the e2e leg")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the full-size batched solves (12 point sources at 24^3x64 Ls=12, 8 masses at "
+                         "32^3x64 Ls=16)")
     ap.add_argument("--apply-only", choices=["f64", "f32", "f16n"], default=None,
                     help="only time M applications in this precision (a fixed launch sequence for ncu)")
     return ap.parse_args()
@@ -349,12 +393,27 @@ def main() -> None:
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     achieved = top["bytes"] / top["launches"] / (top["ms"] / top["launches"] * 1e-3) / 1e9
+    traffic, traffic_note = recorded_traffic(top["name"])
     roofline = {"kernel": top["name"], "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "peak_source": peak_src,
-                "traffic": NCU_TRAFFIC.get(top["name"]),
+                "traffic": traffic, "traffic_source": traffic_note,
                 "launches": top["launches"], "avg_us": 1e3 * top["ms"] / top["launches"],
                 "share_of_solve_kernel_time": top["ms"] / total_ms,
                 "algorithmic_bytes_per_launch": top["bytes"] / top["launches"]}
+    # the FP64 operator of the reliable updates, preparation and reconstruction is bound by
+    # the FP64 pipe (GB300 runs FP64 at 1/64 of the FP32 rate): its roofline is the FP64
+    # peak measured here by cuBLAS DGEMM
+    f64 = [st for st in stats if st["name"].startswith("hop") and st["name"].endswith("_f64")]
+    peak64 = fp64_peak_tflops()
+    roofline_fp64 = None
+    if f64 and peak64:
+        fl, tm = sum(st["flops"] for st in f64), sum(st["ms"] for st in f64)
+        ach = fl / (tm * 1e-3) / 1e12
+        roofline_fp64 = {"kernels": [st["name"] for st in f64], "bound": "fp64_alu", "achieved": ach,
+                         "peak": peak64, "unit": "TFLOP/s", "frac": ach / peak64,
+                         "peak_source": "measured in this run: cuBLAS DGEMM 4096^3 through torch, best of 5",
+                         "flops_model": "1320 per 5d site and hop + the s-operator and xpay terms",
+                         "share_of_solve_kernel_time": tm / total_ms}
     kernels = [{"name": s["name"], "launches": s["launches"], "ms": round(s["ms"], 3),
                 "share": round(s["ms"] / total_ms, 4),
                 "GBps": round(s["bytes"] / (s["ms"] * 1e-3) / 1e9, 1) if s["ms"] > 0 else None}
@@ -516,6 +575,12 @@ def main() -> None:
     if not args.no_extras:
         e2e = end_to_end(args, h, b, inner, n5, flush)
 
+    batched_solves = None
+    if not args.no_extras and not args.no_batched and not args.quick:
+        del flush
+        torch.cuda.empty_cache()
+        batched_solves = {name: batched_solve(name, cfg) for name, cfg in BATCHED.items()}
+
     cpu = None if args.no_cpu else cpu_baseline(dims, Ls)
 
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -524,8 +589,9 @@ def main() -> None:
             "data": "synthetic", "config": workload_config(args.inner),
             "gpu_launches": launches1 - launches0,
             "applies_per_step": applies / args.steps,
-            "roofline": roofline, "clocks": clocks.summary(), "e2e": e2e, "cpu_baseline": cpu,
-            "cgne": cg, "dslash": dslash, "batched_apply": batched, "force": force, "around_the_solve": around,
+            "roofline": roofline, "roofline_fp64": roofline_fp64, "clocks": clocks.summary(), "e2e": e2e, "cpu_baseline": cpu,
+            "cgne": cg, "dslash": dslash, "batched_apply": batched, "batched_solves": batched_solves,
+            "force": force, "around_the_solve": around,
             "kernels": kernels,
             "profiled_solve": {"iters": prof_info.iters, "true_res": prof_info.true_res}}
     print(json.dumps(line), flush=True)
@@ -533,6 +599,118 @@ def main() -> None:
         dist.barrier()
         dist.destroy_process_group()
     mdwf.mdwf_destroy(h)
+
+
+def fp64_peak_tflops(n: int = 4096, reps: int = 5) -> float | None:
+    """FP64 throughput of cuBLAS DGEMM (2 n^3 flops per product), best of reps."""
+    import torch
+    try:
+        a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+        b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+        c = torch.matmul(a, b)
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        del a, b, c
+        return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+    except RuntimeError:
+        return None
+
+
+def batched_solve(name: str, cfg: dict) -> dict:
+    """Time to solution of one batched workload: all right-hand sides in one solve
+    (one launch per kernel over the batch), FP64 reliable updates, to a true FP64
+    residual of 1e-10 per right-hand side; the wall time of the mdwf_cgne call,
+    which synchronises. The sources and solutions are device buffers where they fit
+    beside the solver's fields and host buffers otherwise (the library's copies are
+    then inside the timed call). The plain FP64
+    solve of the same batch would take minutes, so its time is extrapolated: the
+    time per FP64 CG iteration (the difference of two capped FP64 solves of the
+    whole batch, or of a quarter of it when the whole batch does not fit beside
+    its workspace, then scaled by the batch size, since the FP64 operator is
+    bound by the FP64 pipe and its time grows in proportion) times the
+    iterations of the mixed solve, plus the capped solve's fixed costs."""
+    import torch
+    import paper_1206_5214_gb300 as mdwf
+    import synthetic as sy
+    dims, Ls, mf = cfg["dims"], cfg["Ls"], cfg["mf"]
+    nrhs = len(mf)
+    inner = mdwf.MDWF_F32 if cfg["inner"] == "f32" else mdwf.MDWF_F16N
+    out = {"lattice": list(dims), "Ls": Ls, "nrhs": nrhs, "masses": mf, "b5": B5, "c5": C5, "M5": M5,
+           "eps": cfg["eps"], "inner": cfg["inner"], "sources": cfg["sources"], "tol": 1e-10,
+           "autotune": cfg["autotune"], "buffers": cfg["buffers"]}
+    t0 = time.perf_counter()
+    U = sy.gauge_field(dims, cfg["eps"], sy.config_seed("gauge", cfg["cfg"]))
+    if cfg["sources"] == "point":
+        b = sy.point_sources_device(dims, Ls)
+    else:
+        b = sy.gaussian_field_device(dims, Ls, sy.config_seed("source", cfg["cfg"]), nrhs)
+    if cfg["buffers"] == "host":
+        bh = torch.empty(b.shape, dtype=b.dtype)
+        bh.copy_(b)
+        del b
+        torch.cuda.empty_cache()
+        b = bh
+    x = torch.zeros_like(b)
+    out["input_setup_s"] = round(time.perf_counter() - t0, 1)
+    Ud = torch.from_numpy(U).cuda()
+    del U
+    n5 = dims[0] * dims[1] * dims[2] * dims[3] // 2 * Ls
+
+    def run(h, prec, maxiter, sub=None):
+        bb, xx, mm = (b, x, mf) if sub is None else (b[:sub], x[:sub], mf[:sub])
+        xx.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        st, info = mdwf.mdwf_cgne(h, xx, bb, nrhs=len(mm), mf_per_rhs=mm, tol=1e-10, inner_prec=prec,
+                                  maxiter=maxiter, raise_on_error=False)
+        torch.cuda.synchronize()
+        return 1e3 * (time.perf_counter() - t), st, info
+
+    h = mdwf.mdwf_create(dims, Ls, M5, B5, C5, mf[0], autotune=cfg["autotune"])
+    try:
+        mdwf.mdwf_load_gauge(h, Ud)
+        run(h, inner, 16)  # warm-up: tables, autotuned tiles, the iteration's CUDA graph
+        a0 = sum(mdwf.mdwf_counters(h)[1])
+        ms, st, info = run(h, inner, 40000)
+        a1 = sum(mdwf.mdwf_counters(h)[1])
+    finally:
+        mdwf.mdwf_destroy(h)
+    iters = [i.iters for i in info]
+    out["mixed"] = {"ms": ms, "status": st, "iters": iters, "reliable_updates": [i.reliable_updates for i in info],
+                    "true_res": [i.true_res for i in info], "res_m": [i.res_m for i in info],
+                    "GFLOPs": (a1 - a0) * nrhs * FLOPS_PER_SITE * n5 / (ms * 1e-3) / 1e9}
+    # plain FP64: per-iteration time from two capped solves
+    m1, m2 = 4, 12
+    est = None
+    for sub in (None, max(1, nrhs // 4)):
+        h = mdwf.mdwf_create(dims, Ls, M5, B5, C5, mf[0])
+        try:
+            mdwf.mdwf_load_gauge(h, Ud)
+            t1, s1, _ = run(h, mdwf.MDWF_F64, m1, sub)
+            t2, s2, _ = run(h, mdwf.MDWF_F64, m2, sub)
+        finally:
+            mdwf.mdwf_destroy(h)
+        if s1 in (0, 4) and s2 in (0, 4):  # MDWF_OK or MDWF_ENOCONV (capped)
+            scale = nrhs / (sub or nrhs)
+            per_iter = (t2 - t1) / (m2 - m1) * scale
+            est = {"ms_per_iter": per_iter, "measured_nrhs": sub or nrhs, "capped_at": [m1, m2],
+                   "capped_ms": [t1, t2], "iters_assumed": max(iters),
+                   "ms_estimated": t1 * scale + per_iter * (max(iters) - m1)}
+            break
+        torch.cuda.empty_cache()
+    out["f64_extrapolated"] = est
+    if est:
+        out["mixed_speedup_over_f64"] = est["ms_estimated"] / ms
+    del b, x, Ud
+    torch.cuda.empty_cache()
+    return out
 
 
 def end_to_end(args, h, b, inner, n5, flush) -> dict:
