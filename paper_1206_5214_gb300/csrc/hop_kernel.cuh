@@ -820,6 +820,19 @@ __global__ void __launch_bounds__(128, STAGE == 1   ? MDWF_MINB_STAGE
         hop_bulk<P, DAG>(acc, in, U, hp, bk, bars, active, site, s, ly, tid, rbase);
     } else if (active) {
         const int4* nb = hp.nbr + ((long long)hp.out_parity * hp.g.Vh + site) * 2;
+        // the site's eight links into L1 before the terms need them (the links come from
+        // L2, and a link load that waits for L2 inside a term stalls its chain): thread s
+        // of the column asks for the lines of link s / 2 (forward links at the site,
+        // backward ones at the neighbour), two lines per 80-byte FP32 link
+        if constexpr (P != MDWF_F64) {
+            if (s < 16) {
+                const int t = s >> 1, mu = t & 3;
+                const bool fwd = t < 4;
+                const long long j = fwd ? site : (long long)__ldg(reinterpret_cast<const int*>(nb) + 4 + mu);
+                const long long li = ((long long)(fwd ? hp.out_parity : 1 - hp.out_parity) * 4 + mu) * hp.g.Vh + j;
+                if (j >= 0) prefetch_l1(reinterpret_cast<const char*>(U.u + li * 5) + (s & 1) * 64);  // halo: none
+            }
+        }
         if constexpr (STAGE == 3) {
             hop_prefetch<P, DAG>(acc, in, U, hp, reinterpret_cast<const int*>(nb), site, s, rbase);
         } else if constexpr (STAGE == 1) {
@@ -998,6 +1011,7 @@ static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<t
     fa.sc = h.sc;
     Gauge<P> U;
     U.u = reinterpret_cast<decltype(U.u)>(c->gauge[link_copy(P)]);
+    U.bnd = make_bounds(8 * g.Vh);
     const int base = D ? (X ? KB_HOP_DAG_XPAY : KB_HOP_DAG)
                        : G ? (X ? KB_HOP_GATHER_XPAY : KB_HOP_GATHER) : (X ? KB_HOP_XPAY : KB_HOP);
     const double n5 = (double)g.Vh * g.Ls * h.nrhs;
