@@ -142,6 +142,19 @@ size_t mdwf_slab_face_bytes(const mdwf_ctx *ctx, int prec, int nrhs);
 int mdwf_slab_stage(mdwf_ctx *ctx, int stage, void *out, const void *in, int prec, int nrhs,
                     const double *mf_per_rhs, int dagger, void *send, const void *recv);
 
+/*
+ * Bounds checks of the debug build. A library compiled with
+ * -DMDWF_BOUNDS_CHECK=1 (build(debug_bounds=True): _build_bounds/libmdwf.so)
+ * checks every field and link index its kernels compute against the extent
+ * of the buffer view, skips an access out of range and records it in a
+ * device word of the current device. No paper counterpart: it stands in for
+ * a device memory checker. *checked = 1 for that build, 0 for the release
+ * build (no checks; *violations = 0). *violations = 1 if an access was out
+ * of range since the last reset (synchronises the device). reset != 0 clears
+ * the word. Errors: MDWF_EINVAL (NULL pointer), MDWF_ECUDA.
+ */
+int mdwf_bounds_status(int *checked, int *violations, int reset);
+
 /* Frees the context and its workspace (synchronises the context's stream). NULL is accepted. */
 int mdwf_destroy(mdwf_ctx *ctx);
 

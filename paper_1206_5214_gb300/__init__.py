@@ -17,7 +17,8 @@ from . import build as _build
 
 __all__ = [
     "MDWF_F64", "MDWF_F32", "MDWF_F16N", "MdwfError", "lib_path", "load",
-    "mdwf_create", "mdwf_destroy", "mdwf_create_slab", "mdwf_slab_face_bytes", "mdwf_slab_stage", "mdwf_set_stream", "mdwf_set_s_coefficients", "mdwf_get_s_coefficients",
+    "mdwf_create", "mdwf_destroy", "mdwf_create_slab", "mdwf_slab_face_bytes", "mdwf_slab_stage",
+    "mdwf_bounds_status", "mdwf_set_stream", "mdwf_set_s_coefficients", "mdwf_get_s_coefficients",
     "mdwf_set_chemical_potential",
     "mdwf_load_gauge", "mdwf_field_bytes",
     "mdwf_field_import", "mdwf_field_export", "mdwf_apply", "mdwf_apply_dag", "mdwf_cgne",
@@ -92,6 +93,7 @@ def load(build_if_missing: bool = True):
         "mdwf_create_slab": (ip, [ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), ip, ctypes.c_double,
                                   ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.POINTER(_Opts)]),
         "mdwf_slab_face_bytes": (sz, [vp, ip, ip]),
+        "mdwf_bounds_status": (ip, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ip]),
         "mdwf_slab_stage": (ip, [vp, ip, vp, vp, ip, ip, dp, ip, vp, vp]),
         "mdwf_set_stream": (ip, [vp, vp]),
         "mdwf_set_s_coefficients": (ip, [vp, dp, dp]),
@@ -205,6 +207,15 @@ def mdwf_slab_stage(ctx, stage: int, out, inp, prec: int, nrhs: int = 1, mf_per_
     ptr = lambda t: None if t is None else _ptr_where(t)[0]
     _check(load().mdwf_slab_stage(ctx, int(stage), ptr(out), ptr(inp), int(prec), int(nrhs), _masses(mf_per_rhs),
                                   int(bool(dagger)), ptr(send), ptr(recv)), "mdwf_slab_stage")
+
+
+def mdwf_bounds_status(reset: bool = False) -> tuple[bool, bool]:
+    """(checked, violated): whether the loaded library is the bounds-checked debug build,
+    and whether one of its kernels computed an index out of range since the last reset."""
+    checked, bad = ctypes.c_int(), ctypes.c_int()
+    _check(load().mdwf_bounds_status(ctypes.byref(checked), ctypes.byref(bad), int(bool(reset))),
+           "mdwf_bounds_status")
+    return bool(checked.value), bool(bad.value)
 
 
 def mdwf_destroy(ctx) -> None:

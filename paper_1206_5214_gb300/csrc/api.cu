@@ -20,6 +20,8 @@
 
 #include <vector>
 
+#include <mutex>
+
 #include "mdwf_internal.cuh"
 
 namespace {
@@ -81,6 +83,24 @@ LaunchScope::~LaunchScope() {
             c_->ev_pool.push_back(a_);
         }
     }
+}
+
+// The bounds word of the debug build, one per device (allocated on first use).
+int* bounds_word() {
+#if MDWF_BOUNDS_CHECK
+    static int* words[64] = {};
+    static std::mutex m;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(m);
+    if (!words[dev]) {
+        if (cudaMalloc(&words[dev], sizeof(int)) != cudaSuccess) return nullptr;
+        cudaMemset(words[dev], 0, sizeof(int));
+    }
+    return words[dev];
+#else
+    return nullptr;
+#endif
 }
 
 void note_apply(mdwf_ctx* c, int prec) {
@@ -775,6 +795,23 @@ int mdwf_set_staging(mdwf_ctx* c, int prec, int staged) {
 int mdwf_get_staging(const mdwf_ctx* c, int prec, int* staged) {
     if (!c || !valid_prec(prec) || !staged) return MDWF_EINVAL;
     *staged = c->hop_stage[prec];
+    return MDWF_OK;
+}
+
+int mdwf_bounds_status(int* checked, int* violations, int reset) {
+    if (!checked || !violations) return MDWF_EINVAL;
+    *checked = MDWF_BOUNDS_CHECK ? 1 : 0;
+    *violations = 0;
+#if MDWF_BOUNDS_CHECK
+    int* w = bounds_word();
+    if (!w) return MDWF_ECUDA;
+    int st;
+    if ((st = cuda_status(cudaDeviceSynchronize()))) return st;
+    if ((st = cuda_status(cudaMemcpy(violations, w, sizeof(int), cudaMemcpyDeviceToHost)))) return st;
+    if (reset && (st = cuda_status(cudaMemset(w, 0, sizeof(int))))) return st;
+#else
+    (void)reset;
+#endif
     return MDWF_OK;
 }
 

@@ -133,6 +133,31 @@ __device__ __forceinline__ void prefetch_l1(const void* p) {
     asm volatile("prefetch.global.L1 [%0];\n" ::"l"(p));
 }
 
+// Bounds-checked debug build (-DMDWF_BOUNDS_CHECK=1, a separate library): every
+// field access checks 0 <= sr < (sites x right-hand sides of the view) and
+// 0 <= s < Ls, and every link access 0 <= index < 8 Vh; an access out of range
+// is skipped (a load returns zeros), and the device's bounds word records it
+// (mdwf_bounds_status). It stands in for a memory checker; the release build
+// compiles no checks.
+#ifndef MDWF_BOUNDS_CHECK
+#define MDWF_BOUNDS_CHECK 0
+#endif
+int* bounds_word();  // device address of the current device's bounds word (debug build; else null)
+
+struct Bounds {
+#if MDWF_BOUNDS_CHECK
+    long long n = 0;   // valid indices of the view
+    int* err = nullptr;
+    __device__ __forceinline__ bool bad(long long i, int s, int Ls) const {
+        if (i >= 0 && i < n && s >= 0 && s < Ls) return false;
+        atomicOr(err, 1);
+        return true;
+    }
+#else
+    __device__ __forceinline__ static constexpr bool bad(long long, int, int) { return false; }
+#endif
+};
+
 // Device view of an internal field. `sr` below is rhs * Vh + site.
 // prefetch(sr, s) asks L1 for the lines that load(sr, s) will read.
 template <int P> struct Field;
@@ -140,7 +165,9 @@ template <int P> struct Field;
 template <> struct Field<MDWF_F64> {
     double2* v;
     int Ls;
+    Bounds bnd;
     __device__ __forceinline__ void load(long long sr, int s, double* o) const {
+        if (bnd.bad(sr, s, Ls)) { for (int k = 0; k < 24; ++k) o[k] = 0; return; }
         const double2* p = v + sr * 12 * Ls + s;
 #pragma unroll
         for (int k = 0; k < 12; ++k) {
@@ -151,6 +178,7 @@ template <> struct Field<MDWF_F64> {
     }
     // half = 0: spins 0, 1 (reals 0..11); half = 1: spins 2, 3 (reals 12..23)
     __device__ __forceinline__ void load_half(long long sr, int s, int half, double* o) const {
+        if (bnd.bad(sr, s, Ls)) { for (int k = 0; k < 12; ++k) o[k] = 0; return; }
         const double2* p = v + sr * 12 * Ls + (long long)(6 * half) * Ls + s;
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
@@ -160,11 +188,13 @@ template <> struct Field<MDWF_F64> {
         }
     }
     __device__ __forceinline__ void prefetch(long long sr, int s) const {
+        if (bnd.bad(sr, s, Ls)) return;
         const double2* p = v + sr * 12 * Ls + s;
 #pragma unroll
         for (int k = 0; k < 12; ++k) prefetch_l1(p + (long long)k * Ls);
     }
     __device__ __forceinline__ void store(long long sr, int s, const double* i) const {
+        if (bnd.bad(sr, s, Ls)) return;
         double2* p = v + sr * 12 * Ls + s;
 #pragma unroll
         for (int k = 0; k < 12; ++k) p[(long long)k * Ls] = make_double2(i[2 * k], i[2 * k + 1]);
@@ -174,7 +204,9 @@ template <> struct Field<MDWF_F64> {
 template <> struct Field<MDWF_F32> {
     float4* v;
     int Ls;
+    Bounds bnd;
     __device__ __forceinline__ void load(long long sr, int s, float* o) const {
+        if (bnd.bad(sr, s, Ls)) { for (int k = 0; k < 24; ++k) o[k] = 0; return; }
         const float4* p = v + sr * 6 * Ls + s;
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
@@ -183,6 +215,7 @@ template <> struct Field<MDWF_F32> {
         }
     }
     __device__ __forceinline__ void load_half(long long sr, int s, int half, float* o) const {
+        if (bnd.bad(sr, s, Ls)) { for (int k = 0; k < 12; ++k) o[k] = 0; return; }
         const float4* p = v + sr * 6 * Ls + (long long)(3 * half) * Ls + s;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -191,11 +224,13 @@ template <> struct Field<MDWF_F32> {
         }
     }
     __device__ __forceinline__ void prefetch(long long sr, int s) const {
+        if (bnd.bad(sr, s, Ls)) return;
         const float4* p = v + sr * 6 * Ls + s;
 #pragma unroll
         for (int k = 0; k < 6; ++k) prefetch_l1(p + (long long)k * Ls);
     }
     __device__ __forceinline__ void store(long long sr, int s, const float* i) const {
+        if (bnd.bad(sr, s, Ls)) return;
         float4* p = v + sr * 6 * Ls + s;
 #pragma unroll
         for (int k = 0; k < 6; ++k)
@@ -207,6 +242,7 @@ template <> struct Field<MDWF_F16N> {
     uint2* v;     // 4 halves per chunk
     float* norm;  // [rhs][site][s]
     int Ls;
+    Bounds bnd;
     __device__ __forceinline__ static void unpack(uint2 d, float nrm, float* o) {
         __half2 a = *reinterpret_cast<__half2*>(&d.x);
         __half2 b = *reinterpret_cast<__half2*>(&d.y);
@@ -220,6 +256,7 @@ template <> struct Field<MDWF_F16N> {
         o[0] = fa.x; o[1] = fa.y; o[2] = fb.x; o[3] = fb.y;
     }
     __device__ __forceinline__ void load(long long sr, int s, float* o) const {
+        if (bnd.bad(sr, s, Ls)) { for (int k = 0; k < 24; ++k) o[k] = 0; return; }
         const uint2* p = v + sr * 6 * Ls + s;
         float nrm = __ldg(norm + sr * Ls + s);
 #pragma unroll
@@ -227,6 +264,7 @@ template <> struct Field<MDWF_F16N> {
     }
     // values without the norm; returns the norm (its factor is applied later)
     __device__ __forceinline__ float load_raw(long long sr, int s, float* o) const {
+        if (bnd.bad(sr, s, Ls)) { for (int k = 0; k < 24; ++k) o[k] = 0; return 0.f; }
         const uint2* p = v + sr * 6 * Ls + s;
         const float nrm = __ldg(norm + sr * Ls + s);
 #pragma unroll
@@ -234,18 +272,21 @@ template <> struct Field<MDWF_F16N> {
         return nrm;
     }
     __device__ __forceinline__ void load_half(long long sr, int s, int half, float* o) const {
+        if (bnd.bad(sr, s, Ls)) { for (int k = 0; k < 12; ++k) o[k] = 0; return; }
         const uint2* p = v + sr * 6 * Ls + (long long)(3 * half) * Ls + s;
         float nrm = __ldg(norm + sr * Ls + s);
 #pragma unroll
         for (int k = 0; k < 3; ++k) unpack(__ldg(p + (long long)k * Ls), nrm, o + 4 * k);
     }
     __device__ __forceinline__ void prefetch(long long sr, int s) const {
+        if (bnd.bad(sr, s, Ls)) return;
         const uint2* p = v + sr * 6 * Ls + s;
 #pragma unroll
         for (int k = 0; k < 6; ++k) prefetch_l1(p + (long long)k * Ls);
         prefetch_l1(norm + sr * Ls + s);
     }
     __device__ __forceinline__ void store(long long sr, int s, const float* i) const {
+        if (bnd.bad(sr, s, Ls)) return;
         float mx = 0.f;
 #pragma unroll
         for (int k = 0; k < 24; ++k) mx = fmaxf(mx, fabsf(i[k]));
@@ -266,17 +307,28 @@ template <> struct Field<MDWF_F16N> {
 
 // Host-side construction of a field view from a base pointer.
 template <int P> inline Field<P> make_field(void* base, const Geom& g, int nrhs);
-template <> inline Field<MDWF_F64> make_field<MDWF_F64>(void* base, const Geom& g, int) {
-    Field<MDWF_F64> f; f.v = (double2*)base; f.Ls = g.Ls; return f;
+inline Bounds make_bounds(long long n) {
+    Bounds b;
+#if MDWF_BOUNDS_CHECK
+    b.n = n;
+    b.err = bounds_word();
+#else
+    (void)n;
+#endif
+    return b;
 }
-template <> inline Field<MDWF_F32> make_field<MDWF_F32>(void* base, const Geom& g, int) {
-    Field<MDWF_F32> f; f.v = (float4*)base; f.Ls = g.Ls; return f;
+template <> inline Field<MDWF_F64> make_field<MDWF_F64>(void* base, const Geom& g, int nrhs) {
+    Field<MDWF_F64> f; f.v = (double2*)base; f.Ls = g.Ls; f.bnd = make_bounds(g.Vh * nrhs); return f;
+}
+template <> inline Field<MDWF_F32> make_field<MDWF_F32>(void* base, const Geom& g, int nrhs) {
+    Field<MDWF_F32> f; f.v = (float4*)base; f.Ls = g.Ls; f.bnd = make_bounds(g.Vh * nrhs); return f;
 }
 template <> inline Field<MDWF_F16N> make_field<MDWF_F16N>(void* base, const Geom& g, int nrhs) {
     Field<MDWF_F16N> f;
     f.v = (uint2*)base;
     f.norm = (float*)((char*)base + (size_t)g.Vh * g.Ls * nrhs * 48);
     f.Ls = g.Ls;
+    f.bnd = make_bounds(g.Vh * nrhs);
     return f;
 }
 
@@ -285,7 +337,9 @@ template <> inline Field<MDWF_F16N> make_field<MDWF_F16N>(void* base, const Geom
 template <int P> struct Gauge;
 template <> struct Gauge<MDWF_F64> {
     const double2* u;  // [parity][mu][site][9] complex
+    Bounds bnd;        // links: 8 Vh
     __device__ __forceinline__ void load(long long idx, double* o) const {
+        if (bnd.bad(idx, 0, 1)) { for (int k = 0; k < 18; ++k) o[k] = 0; return; }
         const double2* p = u + idx * 9;
 #pragma unroll
         for (int k = 0; k < 9; ++k) { double2 d = __ldg(p + k); o[2 * k] = d.x; o[2 * k + 1] = d.y; }
@@ -295,7 +349,9 @@ template <> struct Gauge<MDWF_F64> {
 // halves (three 16-byte loads); the padding is never read into arithmetic.
 template <> struct Gauge<MDWF_F32> {
     const float4* u;
+    Bounds bnd;        // links: 8 Vh
     __device__ __forceinline__ void load(long long idx, float* o) const {
+        if (bnd.bad(idx, 0, 1)) { for (int k = 0; k < 18; ++k) o[k] = 0; return; }
         const float4* p = u + idx * 5;
         float t[20];
 #pragma unroll

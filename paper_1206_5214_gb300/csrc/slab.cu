@@ -97,6 +97,7 @@ static int launch_pack(mdwf_ctx* c, void* send, const void* in, int in_parity, i
     if (blocks > 152LL * 32) blocks = 152LL * 32;
     Gauge<P> U;
     U.u = reinterpret_cast<decltype(U.u)>(c->gauge[link_copy(P)]);
+    U.bnd = make_bounds(8 * c->g.Vh);
     const double real = P == MDWF_F64 ? 8.0 : 4.0;
     LaunchScope scope(c, KB_LAYOUT * 3 + P, (double)n * (site_bytes(P) + 12.0 * real), (double)n * 12.0);
     Field<P> f = make_field<P>(const_cast<void*>(in), c->g, nrhs);
