@@ -419,13 +419,11 @@ int mdwf_get_tuning(const mdwf_ctx *ctx, int prec, int nrhs, int *sites_per_bloc
  * the paper; a GPU implementation choice), for the kernels without the input
  * gather. staged = 0 (default) prefetches the next neighbour spinor into a
  * second register buffer while the current one is transported, in every such
- * kernel but the fused residual update of the CG iteration, which loads into
- * registers when needed. 1 copies each neighbour spinor into shared memory with
+ * kernel. 1 copies each neighbour spinor into shared memory with
  * per-thread asynchronous copies one neighbour ahead of its use; 2 has the copy
  * engine (bulk copies, TMA) move whole neighbour s-columns of the block's sites
- * into shared memory, two hopping terms ahead, behind mbarriers; 3 prefetches
- * into registers in every kernel; 4 loads into registers when needed in every
- * kernel. Results are identical (the same arithmetic in the same order).
+ * into shared memory, two hopping terms ahead, behind mbarriers; 3 is the
+ * same as 0; 4 loads into registers when needed in every kernel. Results are identical (the same arithmetic in the same order).
  * prec MDWF_F64 accepts 0 only; staged = 2 with MDWF_F16N needs Ls % 4 == 0
  * (MDWF_EINVAL otherwise). The waits of mode 2 are bounded: one that gives up
  * marks the context, and the next mdwf_cgne or mdwf_device_status returns

@@ -1028,10 +1028,9 @@ static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<t
 }
 
 // Load strategy per launch (mdwf_set_staging). The FP32 and FP16 operators
-// without the input gather have the staged variants; by default (mode 0) they
-// prefetch the next neighbour into registers, except the FUSE_R epilogue,
-// whose residual update runs best at the occupancy of the plain loads.
-// Mode 4 uses the plain loads everywhere.
+// without the input gather have the staged variants; by default (mode 0, and
+// mode 3) they prefetch the next neighbour into registers. Mode 4 uses the
+// plain loads everywhere.
 template <int P, bool G, bool D, bool X, int FU>
 static int launch_hop_pick(mdwf_ctx* c, const HopLaunch& h, const HopParams<typename PrecTraits<P>::real>& hp) {
     if constexpr (!G && FU == FUSE_NONE && P != MDWF_F16N) {
@@ -1042,7 +1041,7 @@ static int launch_hop_pick(mdwf_ctx* c, const HopLaunch& h, const HopParams<type
         const int mode = c->hop_stage[P];
         if (mode == 1) return launch_hop_variant<P, G, D, X, FU, 1, -1>(c, h, hp);
         if (mode == 2) return launch_hop_variant<P, G, D, X, FU, 2, -1>(c, h, hp);
-        if (mode == 3 || (mode == 0 && FU != FUSE_R)) {
+        if (mode == 3 || mode == 0) {
             if (c->g.Ls == 16) return launch_hop_variant<P, G, D, X, FU, 3, 16>(c, h, hp);
             return launch_hop_variant<P, G, D, X, FU, 3, -1>(c, h, hp);
         }

@@ -706,9 +706,9 @@ struct mdwf_ctx {
     long long applies[3] = {0, 0, 0};
     // autotuned 4d sites per hop block, [precision][nrhs] (0 = default)
     int sb_tune[3][65] = {};
-    // load strategy of the FP32 / FP16 hops, [precision]: 0 default (prefetch
-    // except the FUSE_R epilogue), 1 cp.async per thread, 2 bulk copies of whole
-    // neighbour columns (TMA), 3 register prefetch everywhere, 4 plain loads
+    // load strategy of the FP32 / FP16 hops, [precision]: 0 default (register
+    // prefetch), 1 cp.async per thread, 2 bulk copies of whole neighbour columns
+    // (TMA), 3 register prefetch (as 0), 4 plain loads
     int hop_stage[3] = {0, 0, 0};
     // device word set by a bounded device-side wait that gave up (0 = none)
     int* dev_err = nullptr;
