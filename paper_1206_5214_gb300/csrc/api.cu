@@ -311,7 +311,7 @@ int ensure_tables(mdwf_ctx* c, int nrhs, const double* mf_per_rhs) {
 
 // ------------------------------------------------------------ operator chain
 
-int apply_op(mdwf_ctx* c, void* out, const void* in, int prec, int nrhs, int dagger, int rhs0) {
+int apply_op(mdwf_ctx* c, void* out, const void* in, int prec, int nrhs, int dagger, int rhs0, const double* mask) {
     const size_t fb = field_bytes(prec, c->g, nrhs);
     int st;
     note_apply(c, prec);
@@ -323,11 +323,12 @@ int apply_op(mdwf_ctx* c, void* out, const void* in, int prec, int nrhs, int dag
     h.b5 = c->b5;
     h.c5 = c->c5;
     h.mass = mass;
+    h.mask = mask;
     if (!dagger) {
         // w_o = M_phi psi_o by one site-local pass, so that the first hop loads w
         // without the gather along s (and the FP32 / FP16 hops can prefetch)
         M5Launch m{};
-        m.out = c->tmp[1].p; m.in = in; m.x = nullptr; m.coef = 1.0; m.nrhs = nrhs;
+        m.out = c->tmp[1].p; m.in = in; m.x = nullptr; m.coef = 1.0; m.nrhs = nrhs; m.mask = mask;
         set_sop(c, prec, SOP_MPHI, 0, m);
         offset_rhs(c, prec, rhs0, m);
         if ((st = launch_m5(c, prec, m))) return st;
@@ -347,7 +348,7 @@ int apply_op(mdwf_ctx* c, void* out, const void* in, int prec, int nrhs, int dag
     }
     // v_o = A^dag psi_o
     M5Launch m{};
-    m.out = c->tmp[1].p; m.in = in; m.x = nullptr; m.coef = 1.0; m.nrhs = nrhs;
+    m.out = c->tmp[1].p; m.in = in; m.x = nullptr; m.coef = 1.0; m.nrhs = nrhs; m.mask = mask;
     set_sop(c, prec, SOP_A, 1, m);
     offset_rhs(c, prec, rhs0, m);
     if ((st = launch_m5(c, prec, m))) return st;

@@ -175,13 +175,14 @@ __global__ void __launch_bounds__(kRedThreads) k_copy(Field<PD> d, Field<PS> src
     }
 }
 
-// y += x; x = 0 (active right-hand sides)
+// y += x; x = 0 (the right-hand sides whose flag in slot `slot` is set)
 template <int PY, int PX>
-__global__ void __launch_bounds__(kRedThreads) k_accum_zero(Field<PY> y, Field<PX> x, const double* sc, Geom g) {
+__global__ void __launch_bounds__(kRedThreads) k_accum_zero(Field<PY> y, Field<PX> x, const double* sc, int slot,
+                                                            Geom g) {
     typedef typename PrecTraits<PY>::real RY;
     typedef typename PrecTraits<PX>::real RX;
     const int rhs = blockIdx.y;
-    if (SC(S_ACTIVE, rhs) == 0.0) return;
+    if (SC(slot, rhs) == 0.0) return;
     SITE_LOOP(g) {
         const int s = (int)(i % g.Ls);
         const long long sr = rhs * g.Vh + i / g.Ls;
@@ -199,15 +200,16 @@ __global__ void __launch_bounds__(kRedThreads) k_accum_zero(Field<PY> y, Field<P
     }
 }
 
-// r = a - b (FP64), optional low-precision copy rs = r; partial |r|^2
+// r = a - b (FP64), optional low-precision copy rs = r; partial |r|^2 (the
+// right-hand sides whose flag in slot `slot` is set, or all when sc is null)
 template <int PS, bool COPY>
 __global__ void __launch_bounds__(kRedThreads) k_residual(Field<MDWF_F64> r, Field<PS> rs, Field<MDWF_F64> a,
                                                          Field<MDWF_F64> b, double* part, const double* sc,
-                                                         Geom g) {
+                                                         int slot, Geom g) {
     typedef typename PrecTraits<PS>::real RS;
     const int rhs = blockIdx.y;
     double acc = 0;
-    if (!sc || SC(S_ACTIVE, rhs) != 0.0) {
+    if (!sc || SC(slot, rhs) != 0.0) {
         SITE_LOOP(g) {
             const int s = (int)(i % g.Ls);
             const long long sr = rhs * g.Vh + i / g.Ls;
@@ -392,17 +394,21 @@ static int iterate(Solver& S, Fields& F, void* x, void* r) {
 // M^dag M x is formed in r itself (each element is read before it is
 // overwritten by the same thread), so no further FP64 field is needed; r of
 // an inactive right-hand side is left holding M^dag M x and is not used again.
+// only_updating: just the right-hand sides flagged in S_UPD (the operator's
+// blocks of the others do nothing, and their r and r_s stay as they are).
 template <int PS, bool COPY>
-static int true_residual(Solver& S, void* r, void* rs, const void* src, const void* x, void* t64, bool masked) {
+static int true_residual(Solver& S, void* r, void* rs, const void* src, const void* x, void* t64, bool masked,
+                         bool only_updating = false) {
     int st;
-    if ((st = apply_op(S.c, t64, x, MDWF_F64, S.nrhs, 0))) return st;
-    if ((st = apply_op(S.c, r, t64, MDWF_F64, S.nrhs, 1))) return st;
+    const double* mask = only_updating ? S.sc + S_UPD * kMaxRhs : nullptr;
+    if ((st = apply_op(S.c, t64, x, MDWF_F64, S.nrhs, 0, 0, mask))) return st;
+    if ((st = apply_op(S.c, r, t64, MDWF_F64, S.nrhs, 1, 0, mask))) return st;
     {
     LaunchScope scope(S.c, KB_BLAS * 3 + MDWF_F64, S.n5() * (3.0 * 192.0 + (COPY ? site_bytes(PS) : 0.0)), S.n5() * 48.0);
     k_residual<PS, COPY><<<S.grid(), kRedThreads, 0, S.c->stream>>>(
         make_field<MDWF_F64>(r, S.g, S.nrhs), make_field<PS>(rs ? rs : r, S.g, S.nrhs),
         make_field<MDWF_F64>(const_cast<void*>(src), S.g, S.nrhs), make_field<MDWF_F64>(r, S.g, S.nrhs), S.part,
-        masked ? S.sc : nullptr, S.g);
+        (masked || only_updating) ? S.sc : nullptr, only_updating ? S_UPD : S_ACTIVE, S.g);
     }
     if ((st = check_launch())) return st;
     return S.fin(FIN_STORE, S_AUX);
@@ -477,30 +483,40 @@ static int run_mixed(Solver& S, Fields& F, const mdwf_solve_params& prm, double 
         }
         it += steps;
         if ((st = S.pull())) return st;
+        // a right-hand side takes its FP64 reliable update when its inner residual has
+        // fallen by delta since its last one (or the inner estimate says it has
+        // converged, or the iterations run out); the others go on untouched, so in a
+        // batch of masses each pays only for its own updates
         bool any_active = false, need_update = false;
         for (int r = 0; r < nrhs; ++r) {
+            S.hsc[S_UPD * kMaxRhs + r] = 0.0;
             if (S.hsc[S_ACTIVE * kMaxRhs + r] == 0.0) continue;
             any_active = true;
             const double rr = S.hsc[S_RR * kMaxRhs + r];
             const double src2 = S.hsc[S_SRC2 * kMaxRhs + r];
             const double rn = sqrt(rr);
-            if (rn < delta * maxr[r] || rr <= tol * tol * src2 || it >= maxiter) need_update = true;
+            if (rn < delta * maxr[r] || rr <= tol * tol * src2 || it >= maxiter) {
+                S.hsc[S_UPD * kMaxRhs + r] = 1.0;
+                need_update = true;
+            }
             if (rn > maxr[r]) maxr[r] = rn;
         }
         if (!any_active) break;
         if (!need_update) continue;
-        // reliable update: x += x_s, x_s = 0, r = src - M^dag M x (FP64), r_s = r
+        // reliable update of the flagged right-hand sides: x += x_s, x_s = 0,
+        // r = src - M^dag M x (FP64), r_s = r
         NvtxRange nvtx_update("reliable update");
+        if ((st = S.push())) return st;
         {
             LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, S.n5() * (2.0 * 192.0 + 2.0 * 96.0), S.n5() * 24.0);
             k_accum_zero<MDWF_F64, MDWF_F32><<<S.grid(), kRedThreads, 0, c->stream>>>(
-                make_field<MDWF_F64>(F.xo, S.g, nrhs), make_field<MDWF_F32>(F.xs, S.g, nrhs), S.sc, S.g);
+                make_field<MDWF_F64>(F.xo, S.g, nrhs), make_field<MDWF_F32>(F.xs, S.g, nrhs), S.sc, S_UPD, S.g);
         }
         if ((st = check_launch())) return st;
-        if ((st = true_residual<MDWF_F32, true>(S, F.r, F.rs, F.src, F.xo, F.t64, true))) return st;
+        if ((st = true_residual<MDWF_F32, true>(S, F.r, F.rs, F.src, F.xo, F.t64, true, true))) return st;
         if ((st = S.pull())) return st;
         for (int r = 0; r < nrhs; ++r) {
-            if (S.hsc[S_ACTIVE * kMaxRhs + r] == 0.0) continue;
+            if (S.hsc[S_ACTIVE * kMaxRhs + r] == 0.0 || S.hsc[S_UPD * kMaxRhs + r] == 0.0) continue;
             rupd[r] += 1;
             const double rr = S.hsc[S_AUX * kMaxRhs + r];
             const double src2 = S.hsc[S_SRC2 * kMaxRhs + r];

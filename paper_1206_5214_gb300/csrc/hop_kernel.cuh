@@ -64,6 +64,7 @@ template <typename R> struct HopParams {
     // the neighbour table marks them as -1 - face site
     const void* halo;
     long long face;  // 4d sites of one parity in one t-slice
+    const double* mask;  // per-rhs flags (null: every right-hand side); 0 skips the blocks
 };
 
 // One half spinor (12 reals) of a slab halo: chunk k of (dir, rhs, face site f,
@@ -783,6 +784,8 @@ __global__ void __launch_bounds__(128, STAGE == 1   ? MDWF_MINB_STAGE
     R* hs = mat2 + (dense && FUSE == FUSE_T ? 2 * Ls * Ls : 0);   // [SB][site_stride], rows of kRowStride
     const int s = threadIdx.x, ly = threadIdx.y;
     const int rhs = blockIdx.x % hp.nrhs;
+    // a right-hand side left out of this launch (block-uniform: before any barrier)
+    if (hp.mask && hp.mask[rhs] == 0.0) return;
     const long long sblk = blockIdx.x / hp.nrhs;
     const int tid = ly * blockDim.x + s, nthr = blockDim.x * blockDim.y;
     if (dense) {
@@ -1092,6 +1095,8 @@ int launch_hop_t(mdwf_ctx* c, const HopLaunch& h) {
     hp.err = c->dev_err;
     hp.no_t = h.no_t != 0;
     hp.halo = h.halo;
+    hp.mask = h.mask;
+    if (h.mask && h.fuse != FUSE_NONE) return MDWF_EINVAL;  // the fused reductions cover every block
     hp.face = (long long)c->g.X * c->g.Y * c->g.Z / 2;
     // a t-slab context reads its t-faces from halos: every hop on it needs them
     if (c->slab != (h.halo != nullptr)) {

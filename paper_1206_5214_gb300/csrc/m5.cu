@@ -12,7 +12,7 @@ __global__ void __launch_bounds__(256) m5_kernel(Field<P> out, Field<P> in, Fiel
                                                  const typename PrecTraits<P>::real* tab,
                                                  const typename PrecTraits<P>::real* mass,
                                                  typename PrecTraits<P>::real coef, Geom g, int sop, int swap,
-                                                 SCoef<typename PrecTraits<P>::real> sc) {
+                                                 SCoef<typename PrecTraits<P>::real> sc, const double* mask) {
     typedef typename PrecTraits<P>::real R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Ls = g.Ls;
@@ -21,6 +21,7 @@ __global__ void __launch_bounds__(256) m5_kernel(Field<P> out, Field<P> in, Fiel
     R* cs = mat + (dense ? 2 * Ls * Ls : 0);
     const int nrhs = (int)(gridDim.x / ((g.Vh + blockDim.y - 1) / blockDim.y));
     const int s = threadIdx.x, ly = threadIdx.y, rhs = blockIdx.x % nrhs;
+    if (mask && mask[rhs] == 0.0) return;  // block-uniform, before any barrier
     const long long sblk = blockIdx.x / nrhs;
     const int tid = ly * blockDim.x + s, nthr = blockDim.x * blockDim.y;
     if (dense) {
@@ -98,11 +99,11 @@ static int launch_m5_t(mdwf_ctx* c, const M5Launch& m) {
     if (m.x) {
         auto k = m5_kernel<P, true>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<grid, block, smem, c->stream>>>(out, in, xf, tab, mass, (R)m.coef, g, m.sop, m.swap, sc);
+        k<<<grid, block, smem, c->stream>>>(out, in, xf, tab, mass, (R)m.coef, g, m.sop, m.swap, sc, m.mask);
     } else {
         auto k = m5_kernel<P, false>;
         if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k<<<grid, block, smem, c->stream>>>(out, in, xf, tab, mass, (R)m.coef, g, m.sop, m.swap, sc);
+        k<<<grid, block, smem, c->stream>>>(out, in, xf, tab, mass, (R)m.coef, g, m.sop, m.swap, sc, m.mask);
     }
     return check_launch();
 }

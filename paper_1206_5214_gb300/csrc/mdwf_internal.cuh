@@ -52,8 +52,9 @@ constexpr int kMaxRhs = 64;  // right-hand sides per call
 
 // CG scalars per right-hand side, stored [slot][kMaxRhs] in device memory:
 // |r|^2, <p, M^dag M p>, alpha, beta, |src|^2, active flag, status, scratch,
-// iteration count.
-enum CgSlot { S_RR = 0, S_PAP, S_ALPHA, S_BETA, S_SRC2, S_ACTIVE, S_STATUS, S_AUX, S_ITERS, S_NUM };
+// iteration count, and the flag of a right-hand side whose FP64 reliable
+// update runs now.
+enum CgSlot { S_RR = 0, S_PAP, S_ALPHA, S_BETA, S_SRC2, S_ACTIVE, S_STATUS, S_AUX, S_ITERS, S_UPD, S_NUM };
 // What a finished reduction v does: store it in a slot, or form alpha from
 // v = <p, M^dag M p>, or beta from v = |r_new|^2 (and count the iteration).
 enum FinMode { FIN_STORE = 0, FIN_ALPHA = 1, FIN_BETA = 2 };
@@ -790,6 +791,7 @@ struct HopLaunch {
     const void* mass;     // per-rhs masses (double for F64, float otherwise)
     double b5, c5;
     int nrhs;
+    const double* mask;   // per-rhs flags, or null: the blocks of a right-hand side whose flag is 0 do nothing
     // fused CG epilogues (0: none; 1: also v = A^dag out into out2 and |out|^2
     // partials; 2: r -= alpha out into rfield with |r|^2 partials, out not stored)
     int fuse;
@@ -821,6 +823,7 @@ struct M5Launch {
     int swap;
     int nrhs;
     const void* mass; // per-rhs masses in this precision; nullptr = the context's
+    const double* mask;  // per-rhs flags, or null (as HopLaunch::mask)
 };
 int launch_m5(mdwf_ctx* c, int prec, const M5Launch& m);
 
@@ -843,7 +846,8 @@ int launch_force(mdwf_ctx* c, double* dSdU, const void* A_odd, const void* B_eve
 
 // operator chains (api.cu); rhs0: the fields are right-hand sides rhs0 ..
 // rhs0 + nrhs - 1 of the batch the tables were built for
-int apply_op(mdwf_ctx* c, void* out, const void* in, int prec, int nrhs, int dagger, int rhs0 = 0);
+int apply_op(mdwf_ctx* c, void* out, const void* in, int prec, int nrhs, int dagger, int rhs0 = 0,
+             const double* mask = nullptr);
 int tune_hop(mdwf_ctx* c, int prec, int nrhs, int* chosen);
 
 // solver (cg.cu)

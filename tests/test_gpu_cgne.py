@@ -256,3 +256,26 @@ def test_cgne_max_batch():
         p = oracle.Params(dims, Ls, 1.8, 1.5, 0.5, masses[r])
         res = b[r] - oracle.ddw(xs[r], U, p)
         assert np.linalg.norm(res) / np.linalg.norm(b[r]) <= 1e-7, r
+
+
+@pytest.mark.parametrize("inner", [F32, F16N], ids=["mixed-f32", "mixed-f16n"])
+def test_reliable_updates_per_rhs(inner):
+    """In a batch of masses each right-hand side takes its own FP64 reliable
+    updates, when its own inner residual asks for one, while the others' inner
+    iterations go on untouched: every right-hand side of the batch takes the
+    same iterations and reliable updates as its solve alone (the batched
+    kernels and the fixed-order reductions compute each right-hand side as the
+    single solve does), and solves its system."""
+    dims, Ls = (4, 4, 4, 4), 8
+    masses = [0.005, 0.05, 0.8]
+    U = sy.gauge_field(dims, 0.3, 1096)
+    b = sy.gaussian_field(dims, Ls, 2096, nrhs=3)
+    st, info, x = gpu_solve(dims, Ls, 1.5, 0.5, 0.01, U, b, inner, nrhs=3, masses=masses)
+    assert st == 0 and all(i.true_res <= 1e-10 for i in info), [i.as_dict() for i in info]
+    for r, m in enumerate(masses):
+        st1, info1, _ = gpu_solve(dims, Ls, 1.5, 0.5, m, U, b[r], inner)
+        assert st1 == 0
+        assert (info[r].iters, info[r].reliable_updates) == (info1[0].iters, info1[0].reliable_updates), \
+            (r, info[r].as_dict(), info1[0].as_dict())
+        p = oracle.Params(dims, Ls, 1.8, 1.5, 0.5, m)
+        assert oracle_residual(x[r], b[r], U, p) <= 1.05e-10, r
