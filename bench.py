@@ -209,9 +209,20 @@ def cpu_baseline(dims, Ls) -> dict:
     dt = time.perf_counter() - t0
     n5 = int(np.prod(dims)) // 2 * Ls
     gf = 2 * reps * FLOPS_PER_SITE * n5 / dt / 1e9
-    return {"value": gf, "unit": "GFLOP/s", "cores": oracle.get_threads(), "kind": "oracle",
+    cores = oracle.get_threads()
+    # one host thread: one M application
+    oracle.set_threads(1)
+    try:
+        t1 = time.perf_counter()
+        v = oracle.m(xo, U, p)
+        dt1 = time.perf_counter() - t1
+    finally:
+        oracle.set_threads(cores)
+    return {"value": gf, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
             "sample": f"{2 * reps} applications (M, M^dag alternating) of the FP64 oracle on the full "
-                      f"workload lattice, {dt:.1f} s"}
+                      f"workload lattice, {dt:.1f} s",
+            "single_thread": {"value": FLOPS_PER_SITE * n5 / dt1 / 1e9, "unit": "GFLOP/s", "cores": 1,
+                              "sample": f"one M application on the same lattice, {dt1:.1f} s"}}
 
 
 def run_reference(args) -> None:
@@ -400,6 +411,15 @@ def main() -> None:
                 "launches": top["launches"], "avg_us": 1e3 * top["ms"] / top["launches"],
                 "share_of_solve_kernel_time": top["ms"] / total_ms,
                 "algorithmic_bytes_per_launch": top["bytes"] / top["launches"]}
+    # the whole inner iteration (its four hops, the vector update and the scalar
+    # reductions, in the inner precision): algorithmic bytes over device time
+    inner_tag = "_" + args.inner
+    it = [st for st in stats if st["name"].endswith(inner_tag)]
+    it_bytes, it_ms = sum(st["bytes"] for st in it), sum(st["ms"] for st in it)
+    roofline_iteration = {"kernels": [st["name"] for st in it], "bound": "hbm",
+                          "achieved": it_bytes / (it_ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                          "frac": it_bytes / (it_ms * 1e-3) / 1e9 / hbm_peak,
+                          "share_of_solve_kernel_time": it_ms / total_ms} if it and it_ms > 0 else None
     # the FP64 operator of the reliable updates, preparation and reconstruction is bound by
     # the FP64 pipe (GB300 runs FP64 at 1/64 of the FP32 rate): its roofline is the FP64
     # peak measured here by cuBLAS DGEMM
@@ -589,7 +609,8 @@ def main() -> None:
             "data": "synthetic", "config": workload_config(args.inner),
             "gpu_launches": launches1 - launches0,
             "applies_per_step": applies / args.steps,
-            "roofline": roofline, "roofline_fp64": roofline_fp64, "clocks": clocks.summary(), "e2e": e2e, "cpu_baseline": cpu,
+            "roofline": roofline, "roofline_iteration": roofline_iteration, "roofline_fp64": roofline_fp64,
+            "clocks": clocks.summary(), "e2e": e2e, "cpu_baseline": cpu,
             "cgne": cg, "dslash": dslash, "batched_apply": batched, "batched_solves": batched_solves,
             "force": force, "around_the_solve": around,
             "kernels": kernels,
