@@ -36,10 +36,10 @@ LS, M5, B5, C5, MF, EPS = 16, 1.8, 1.5, 0.5, 0.01, 0.2
 GAUGE_SEED, SOURCE_SEED = 1002, 2002
 FLOPS_PER_SITE = 3120.0      # per odd 5d site and M (or M^dag) application
 # DRAM bytes (read + write) per launch of a kernel in this workload's solve come from one
-# ncu capture, recorded (a JSON block) in profiles/dram_traffic.md with the SHA-256 of the
+# ncu capture, recorded (a JSON block) in a text file under profiles/ with the SHA-256 of the
 # kernel's sources at capture time; a record whose hash differs from the sources as they
 # are now is stale and is not reported.
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.md")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_cgne_f32_16x16x16x32_Ls16.txt")
 KERNEL_SOURCES = ("paper_1206_5214_gb300/csrc/hop_kernel.cuh", "paper_1206_5214_gb300/csrc/mdwf_internal.cuh",
                   "paper_1206_5214_gb300/csrc/mbarrier.cuh")
 METRIC = "Moebius Dslash GFLOP/s in CGNE to 1e-10 (mixed FP32/FP64)"

@@ -69,7 +69,7 @@ def test_traffic_record_is_keyed_by_the_kernel_sources(tmp_path):
     src.write_text("kernel A")
     sha_a = bench.kernel_sources_sha256(files=("k.cuh",), root=str(tmp_path))
     assert re.fullmatch(r"[0-9a-f]{64}", sha_a)
-    rec = tmp_path / "t.md"
+    rec = tmp_path / "t.txt"
     rec.write_text('x\n```json\n{"kernels": {"hop_xpay_f32": {"dram_read_bytes": 3e8, "dram_write_bytes": 1e8, '
                    f'"sources_sha256": "{sha_a}"}}}}}}\n```\n')
     assert bench.recorded_traffic("hop_xpay_f32", str(rec), sha_a)[0] == 4e8
