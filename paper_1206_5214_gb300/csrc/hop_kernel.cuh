@@ -870,6 +870,37 @@ __global__ void __launch_bounds__(128, STAGE == 1   ? MDWF_MINB_STAGE
 #pragma unroll
         for (int k = 0; k < 24; ++k) acc[k] *= gpre;
     }
+    if constexpr (FUSE == FUSE_T && XPAY && LSR == 16) {
+        // t not stored (closed form, Ls = 16, two columns per warp): the rows go
+        // to the column pass as y = cf acc + I p (I = M+ + M- C bidiagonal, by
+        // shuffles), so that one pass forms t = A y = cf A acc + p, adds |t|^2
+        // and turns t into v = A^dag t: one shared-memory round trip, not two
+        if (hp.no_t && !dense && (blockDim.y & 1) == 0) {
+            const R cf = hp.coef * hp.gscale;
+            R xv[24], y[24];
+            if (active) {
+                xf.load(rbase + site, s, xv);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 24; ++k) xv[k] = R(0);
+            }
+            bidiag_shuffle16(xv, y, s, SOP_MEE, false, hp.sc, mass);
+#pragma unroll
+            for (int k = 0; k < 24; ++k) y[k] = active ? fma(cf, acc[k], y[k]) : R(0);
+            R* row = hs + (size_t)ly * site_stride(16) + s * kRowStride;
+            row_store(row, y);
+            __syncthreads();
+            const R sq = block_columns_a_adag<16>(hs, blockDim.y, hp.sc, mass, tid, nthr);
+            __syncthreads();
+            if (active) {
+                row_load(row, y);
+                fa.out2.store(rbase + site, s, y);
+            }
+            const double tot = block_sum128(sq, red);
+            if (tid == 0) fa.part[(size_t)rhs * (gridDim.x / hp.nrhs) + sblk] = tot;
+            return;
+        }
+    }
     const int sst = site_stride(Ls);
     R* mine = hs + (size_t)ly * sst + s * kRowStride;
     R res[24];

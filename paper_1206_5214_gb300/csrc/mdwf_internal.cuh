@@ -482,6 +482,41 @@ __device__ __forceinline__ void column_op(R* base, int stride, int Ls, int op, b
     }
 }
 
+// The closed-form I^-1 (Sec. 3) on a register-held column of LS complex
+// values, element s at v[REV ? LS-1-s : s]: first the last element
+// Psi_{Ls-1} from the whole column, returned in (pr, pi) ...
+template <int LS, bool REV, typename C, typename R>
+__device__ __forceinline__ void a_last(const C* v, R r, R kappa, R Mp, R& pr, R& pi) {
+    R ar = v[REV ? 0 : LS - 1].x, ai = v[REV ? 0 : LS - 1].y, pw = kappa;
+#pragma unroll
+    for (int s = 0; s < LS - 1; ++s) {
+        ar += pw * v[REV ? LS - 1 - s : s].x;
+        ai += pw * v[REV ? LS - 1 - s : s].y;
+        pw *= -r;
+    }
+    const R den = Mp * (R(1) - pw);
+    pr = ar / den;
+    pi = ai / den;
+}
+
+// ... then, with Psi_{Ls-1} in place, Psi_s = v_s / M+ - (M- / M+) Psi_{s+1}
+// from s = Ls-2 down, in place: v becomes I^-1 v.
+template <int LS, bool REV, typename C, typename R>
+__device__ __forceinline__ void a_solve(C* v, R r, R kappa, R inv, R Mp) {
+    R pr, pi;
+    a_last<LS, REV>(v, r, kappa, Mp, pr, pi);
+    v[REV ? 0 : LS - 1].x = pr;
+    v[REV ? 0 : LS - 1].y = pi;
+#pragma unroll
+    for (int s = LS - 2; s >= 0; --s) {
+        C& e = v[REV ? LS - 1 - s : s];
+        pr = e.x * inv - r * pr;
+        pi = e.y * inv - r * pi;
+        e.x = pr;
+        e.y = pi;
+    }
+}
+
 // column_op with the column held in registers (Ls known at compile time): all
 // Ls elements are loaded at once, the recursion runs on registers, and all are
 // stored back; the arithmetic is that of column_op.
@@ -493,25 +528,12 @@ __device__ __forceinline__ void column_op_reg(R* base, int stride, int op, bool 
     for (int s = 0; s < LS; ++s) v[s] = *reinterpret_cast<const C*>(base + (up ? s : LS - 1 - s) * stride);
     if (op == SOP_A || op == SOP_K) {
         const R r = sc.Mm / sc.Mp, kappa = m * r, inv = R(1) / sc.Mp;
-        R ar = v[LS - 1].x, ai = v[LS - 1].y, pw = kappa;
-#pragma unroll
-        for (int s = 0; s < LS - 1; ++s) {
-            ar += pw * v[s].x;
-            ai += pw * v[s].y;
-            pw *= -r;
-        }
-        const R den = sc.Mp * (R(1) - pw);
-        R pr = ar / den, pi = ai / den;  // Psi_{Ls-1}
-        const R lr = pr, li = pi;
         if (op == SOP_A) {
-            v[LS - 1].x = pr; v[LS - 1].y = pi;
-#pragma unroll
-            for (int s = LS - 2; s >= 0; --s) {
-                pr = v[s].x * inv - r * pr;
-                pi = v[s].y * inv - r * pi;
-                v[s].x = pr; v[s].y = pi;
-            }
+            a_solve<LS, false>(v, r, kappa, inv, sc.Mp);
         } else {
+            R pr, pi;
+            a_last<LS, false>(v, r, kappa, sc.Mp, pr, pi);  // Psi_{Ls-1}
+            const R lr = pr, li = pi;
 #pragma unroll
             for (int s = LS - 2; s >= 0; --s) {
                 const R nr = v[s].x * inv - r * pr, ni = v[s].y * inv - r * pi;  // Psi_s
@@ -611,6 +633,45 @@ __device__ __forceinline__ void block_columns(R* hs, int SB, int Ls, int op, boo
         else if (in_registers) column_op_any(hs + (size_t)ly * ss + 2 * j, kRowStride, Ls, op, up, sc, m);
         else column_op(hs + (size_t)ly * ss + 2 * j, kRowStride, Ls, op, up, sc, m);
     }
+}
+
+// The column pass of the fused t, v epilogue (closed form, Ls = LS): with y
+// staged in the rows, each column becomes t = A y, its share of |t|^2 goes
+// to the returned sum, and then v = A^dag t, which for one chirality is the
+// same recursion run from the other end of the column; v replaces y in the
+// rows. Tasks as in block_columns.
+template <int LS, typename R>
+__device__ __forceinline__ R column_a_adag_reg(R* base, int stride, bool up, const SCoef<R>& sc, R m) {
+    typedef typename CPair<R>::T C;
+    C v[LS];
+#pragma unroll
+    for (int s = 0; s < LS; ++s) v[s] = *reinterpret_cast<const C*>(base + (up ? s : LS - 1 - s) * stride);
+    const R r = sc.Mm / sc.Mp, kappa = m * r, inv = R(1) / sc.Mp;
+    a_solve<LS, false>(v, r, kappa, inv, sc.Mp);
+    R sq = 0;
+#pragma unroll
+    for (int s = 0; s < LS; ++s) {
+        sq = fma(v[s].x, v[s].x, sq);
+        sq = fma(v[s].y, v[s].y, sq);
+    }
+    a_solve<LS, true>(v, r, kappa, inv, sc.Mp);
+#pragma unroll
+    for (int s = 0; s < LS; ++s) *reinterpret_cast<C*>(base + (up ? s : LS - 1 - s) * stride) = v[s];
+    return sq;
+}
+
+template <int LS, typename R>
+__device__ __forceinline__ R block_columns_a_adag(R* hs, int SB, const SCoef<R>& sc, R m, int tid, int nthr) {
+    const int ss = site_stride(LS);
+    const int per = SB * 6, half = (per + 31) / 32 * 32;
+    R sq = 0;
+    for (int t = tid; t < 2 * half; t += nthr) {
+        const int chir = t >= half ? 1 : 0, r = t - chir * half;
+        if (r >= per) continue;
+        const int ly = r / 6, j = chir * 6 + (r - 6 * (r / 6));
+        sq += column_a_adag_reg<LS>(hs + (size_t)ly * ss + 2 * j, kRowStride, chir == 1, sc, m);
+    }
+    return sq;
 }
 
 // ------------------------------------------------------------------ tables

@@ -31,7 +31,7 @@ def oracle_residual(x_full, b_full, U, p):
 
 
 def gpu_solve(dims, Ls, b5, c5, mf, U, b, inner, nrhs=1, masses=None, host=False, graph=True, tol=1e-10,
-              staged=None):
+              staged=None, maxiter=20000):
     h = mdwf.mdwf_create(dims, Ls, 1.8, b5, c5, mf)
     try:
         if staged is not None and inner != F64:
@@ -45,7 +45,7 @@ def gpu_solve(dims, Ls, b5, c5, mf, U, b, inner, nrhs=1, masses=None, host=False
             bb = torch.from_numpy(np.ascontiguousarray(b)).cuda()
             x = torch.zeros_like(bb)
         st, info = mdwf.mdwf_cgne(h, x, bb, nrhs=nrhs, mf_per_rhs=masses, tol=tol, inner_prec=inner,
-                                  use_graph=graph)
+                                  use_graph=graph, maxiter=maxiter, raise_on_error=maxiter == 20000)
         xs = x if host else x.cpu().numpy()
         return st, info, xs
     finally:
@@ -219,6 +219,29 @@ def test_cgne_4x4x4x4_Ls16_matches_oracle(inner, b5, c5, staged):
     st, info, x = gpu_solve(dims, Ls, b5, c5, mf, U, b, inner, staged=staged)
     assert st == 0 and info[0].true_res <= 1e-10
     assert oracle_residual(x, b, U, p) <= 1.05e-10
+
+
+def test_Ls16_iteration_without_t_field_matches_t_field():
+    """The Ls = 16 iteration without a t field forms t = A (cf z' + I p) and v = A^dag t
+    in one column pass and |t|^2 from the columns; the iteration that stores t applies
+    A and A^dag in two passes. In exact arithmetic both are the CG of the plain FP64
+    solve, reliable updates included, so after 16 iterations (cut off by maxiter) the
+    three iterates agree up to FP32 rounding, while a wrong |t|^2 or v would move the
+    iterate at order one; run to 1e-10, both FP32 forms converge to the same solution."""
+    dims, Ls, mf = (4, 4, 4, 8), 16, 0.01
+    U = sy.gauge_field(dims, 0.3, 1096)
+    b = sy.gaussian_field(dims, Ls, 2096)
+    st64, info64, x64 = gpu_solve(dims, Ls, 1.5, 0.5, mf, U, b, F64, maxiter=16)
+    assert st64 == mdwf.MDWF_ENOCONV
+    for staged in (0, 1):
+        st, info, x = gpu_solve(dims, Ls, 1.5, 0.5, mf, U, b, F32, staged=staged, maxiter=16)
+        assert st == mdwf.MDWF_ENOCONV and info[0].iters == info64[0].iters
+        assert np.linalg.norm(x - x64) <= 1e-4 * np.linalg.norm(x64), staged
+    runs = [gpu_solve(dims, Ls, 1.5, 0.5, mf, U, b, F32, staged=st) for st in (0, 1)]
+    assert all(st == 0 and info[0].true_res <= 1e-10 for st, info, _ in runs)
+    # two solutions with residuals <= 1e-10 differ by at most kappa(M^dag M) * 2e-10
+    x0, x1 = runs[0][2], runs[1][2]
+    assert np.linalg.norm(x0 - x1) <= 1e-5 * np.linalg.norm(x1)
 
 
 def test_cgne_Ls16_multi_mass_without_t_field():
