@@ -439,6 +439,12 @@ def main() -> None:
                 "GBps": round(s["bytes"] / (s["ms"] * 1e-3) / 1e9, 1) if s["ms"] > 0 else None}
                for s in sorted(stats, key=lambda s: -s["ms"])]
 
+    # ---------------- end to end through the C ABI with host buffers (right after the timed
+    # solves, with the context in the same state)
+    e2e = None
+    if not args.no_extras:
+        e2e = end_to_end(args, h, b, inner, n5, flush, lambda: solve(inner))
+
     # ---------------- Dslash alone per precision (M applications on resident fields)
     dslash = {}
     precs = () if args.no_extras else (("f64", mdwf.MDWF_F64), ("f32", mdwf.MDWF_F32), ("f16n", mdwf.MDWF_F16N))
@@ -590,11 +596,6 @@ def main() -> None:
         mdwf.mdwf_destroy(hf)
         del G, phid
 
-    # ---------------- end to end through the C ABI with host buffers
-    e2e = None
-    if not args.no_extras:
-        e2e = end_to_end(args, h, b, inner, n5, flush)
-
     batched_solves = None
     if not args.no_extras and not args.no_batched and not args.quick:
         del flush
@@ -734,29 +735,39 @@ def batched_solve(name: str, cfg: dict) -> dict:
     return out
 
 
-def end_to_end(args, h, b, inner, n5, flush) -> dict:
-    """The same solve through mdwf_cgne with pinned host buffers: H2D of b and D2H of x timed."""
+def end_to_end(args, h, b, inner, n5, flush, solve_device) -> dict:
+    """The same solve through mdwf_cgne with pinned host buffers: H2D of b and D2H of x timed.
+    Each step is followed by the device-buffer solve in the same state (not counted), whose
+    wall time shows what the copies add."""
     import torch
     import paper_1206_5214_gb300 as mdwf
     bh = torch.from_numpy(b).pin_memory()
     xh = torch.zeros_like(bh).pin_memory()
     for _ in range(2):  # warm-up: the first transfers from freshly pinned pages are slower
         mdwf.mdwf_cgne(h, xh, bh, tol=1e-10, inner_prec=inner)
-    e2e_times = []
-    a0 = sum(mdwf.mdwf_counters(h)[1])
+    e2e_times, dev_times = [], []
+    applies = 0
     for _ in range(max(1, min(args.steps, 5))):
         flush.zero_()
         torch.cuda.synchronize()
+        a0 = sum(mdwf.mdwf_counters(h)[1])
         t0 = time.perf_counter()
         mdwf.mdwf_cgne(h, xh, bh, tol=1e-10, inner_prec=inner)
         e2e_times.append(time.perf_counter() - t0)
-    a1 = sum(mdwf.mdwf_counters(h)[1])
-    e2e_flops = (a1 - a0) / len(e2e_times) * FLOPS_PER_SITE * n5
+        applies += sum(mdwf.mdwf_counters(h)[1]) - a0
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        solve_device()
+        torch.cuda.synchronize()
+        dev_times.append(time.perf_counter() - t0)
+    e2e_flops = applies / len(e2e_times) * FLOPS_PER_SITE * n5
     e2e_s = sum(e2e_times) / len(e2e_times)
     bytes_field = b.nbytes
     return {"value": e2e_flops / e2e_s / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": bytes_field,
             "d2h_bytes_per_step": bytes_field, "ms_per_step": 1e3 * e2e_s,
-            "ms_each": [round(1e3 * t, 2) for t in e2e_times]}
+            "ms_each": [round(1e3 * t, 2) for t in e2e_times],
+            "device_buffers_wall_ms_each": [round(1e3 * t, 2) for t in dev_times]}
 
 
 if __name__ == "__main__":

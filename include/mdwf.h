@@ -276,6 +276,10 @@ typedef struct {
     double true_res;      /* final FP64 |M^dag b' - M^dag M x| / |M^dag b'| */
     double res_m;         /* final FP64 |b' - M x| / |b'| */
     double seconds;       /* wall time of the whole call (same for every right-hand side) */
+    int restarts;         /* mixed solves: reliable updates after which p restarted from the
+                             true residual (it exceeded the inner estimate more than twice),
+                             and roll-backs to the last update after an inner breakdown
+                             (non-positive or non-finite <p, M^dag M p>) */
 } mdwf_solve_info;
 
 /*

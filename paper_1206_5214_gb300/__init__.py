@@ -65,7 +65,8 @@ class KernelStat(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("reliable_updates", ctypes.c_int),
-                ("true_res", ctypes.c_double), ("res_m", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("true_res", ctypes.c_double), ("res_m", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("restarts", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -15,10 +15,14 @@
 // the correction x_s in FP32. When |r_s| drops below delta * max |r_s| since
 // the last update (or below the target), x += x_s and the true residual
 // r = M^dag b' - M^dag M x is recomputed with the FP64 operator; r_s = r.
+// Each update corrects the search direction for the new residual, and an
+// inner breakdown rolls back to the last update (run_mixed).
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <vector>
 
 #include "mdwf_internal.cuh"
@@ -156,13 +160,15 @@ __global__ void __launch_bounds__(128) k_pupd_w(Field<PX> x, Field<PR> r, Field<
     w.store(sr, s, wv);
 }
 
-// dst = src (precision conversion); only active right-hand sides when sc != null
+// dst = src (precision conversion); when sc != null only the right-hand sides
+// whose flag in slot `slot` is set
 template <int PD, int PS>
-__global__ void __launch_bounds__(kRedThreads) k_copy(Field<PD> d, Field<PS> src, const double* sc, Geom g) {
+__global__ void __launch_bounds__(kRedThreads) k_copy(Field<PD> d, Field<PS> src, const double* sc, int slot,
+                                                      Geom g) {
     typedef typename PrecTraits<PD>::real RD;
     typedef typename PrecTraits<PS>::real RS;
     const int rhs = blockIdx.y;
-    if (sc && SC(S_ACTIVE, rhs) == 0.0) return;
+    if (sc && SC(slot, rhs) == 0.0) return;
     SITE_LOOP(g) {
         const int s = (int)(i % g.Ls);
         const long long sr = rhs * g.Vh + i / g.Ls;
@@ -173,6 +179,80 @@ __global__ void __launch_bounds__(kRedThreads) k_copy(Field<PD> d, Field<PS> src
         for (int k = 0; k < 24; ++k) w[k] = (RD)v[k];
         d.store(sr, s, w);
     }
+}
+
+// x = 0 for the right-hand sides whose flag in slot `slot` is set
+template <int P>
+__global__ void __launch_bounds__(kRedThreads) k_zero(Field<P> x, const double* sc, int slot, Geom g) {
+    typedef typename PrecTraits<P>::real R;
+    const int rhs = blockIdx.y;
+    if (SC(slot, rhs) == 0.0) return;
+    R z[24];
+#pragma unroll
+    for (int k = 0; k < 24; ++k) z[k] = R(0);
+    SITE_LOOP(g) {
+        const int s = (int)(i % g.Ls);
+        x.store(rhs * g.Vh + i / g.Ls, s, z);
+    }
+}
+
+// d = c1 a + c2 b with c1, c2 from slots S_C1, S_C2 (the right-hand sides whose
+// flag in slot `slot` is set); d may alias a or b element by element
+template <int PD, int PA, int PB>
+__global__ void __launch_bounds__(kRedThreads) k_lincomb(Field<PD> d, Field<PA> a, Field<PB> b, const double* sc,
+                                                         int slot, Geom g) {
+    typedef typename PrecTraits<PD>::real RD;
+    typedef typename PrecTraits<PA>::real RA;
+    typedef typename PrecTraits<PB>::real RB;
+    const int rhs = blockIdx.y;
+    if (SC(slot, rhs) == 0.0) return;
+    // in the output's arithmetic precision (FP64 arithmetic on FP32 data would run on
+    // a pipe at 1/64 of the FP32 rate)
+    const RD c1 = (RD)SC(S_C1, rhs), c2 = (RD)SC(S_C2, rhs);
+    SITE_LOOP(g) {
+        const int s = (int)(i % g.Ls);
+        const long long sr = rhs * g.Vh + i / g.Ls;
+        RA av[24];
+        RB bv[24];
+        RD dv[24];
+        a.load(sr, s, av);
+        b.load(sr, s, bv);
+        if (c2 != RD(0)) {
+#pragma unroll
+            for (int k = 0; k < 24; ++k) dv[k] = fma(c1, (RD)av[k], c2 * (RD)bv[k]);
+        } else {  // b not used (it may hold non-finite values)
+#pragma unroll
+            for (int k = 0; k < 24; ++k) dv[k] = c1 * (RD)av[k];
+        }
+        d.store(sr, s, dv);
+    }
+}
+
+// Re <a, b> per right-hand side (flag in slot `slot` set; 0 otherwise) -> partials
+template <int PA, int PB>
+__global__ void __launch_bounds__(kRedThreads) k_dot2(Field<PA> a, Field<PB> b, double* part, const double* sc,
+                                                      int slot, Geom g) {
+    typedef typename PrecTraits<PA>::real RA;
+    typedef typename PrecTraits<PB>::real RB;
+    typedef decltype(RA(0) * RB(0)) RP;  // FP32 products of FP32 / FP16+norm fields
+    const int rhs = blockIdx.y;
+    double acc = 0;
+    if (SC(slot, rhs) != 0.0) {
+        SITE_LOOP(g) {
+            const int s = (int)(i % g.Ls);
+            const long long sr = rhs * g.Vh + i / g.Ls;
+            RA av[24];
+            RB bv[24];
+            a.load(sr, s, av);
+            b.load(sr, s, bv);
+            RP t = 0;  // a site's 24 products in the fields' precision, the sum over sites in FP64
+#pragma unroll
+            for (int k = 0; k < 24; ++k) t = fma((RP)av[k], (RP)bv[k], t);
+            acc += (double)t;
+        }
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[rhs * gridDim.x + blockIdx.x] = acc;
 }
 
 // y += x; x = 0 (the right-hand sides whose flag in slot `slot` is set)
@@ -273,12 +353,32 @@ struct Solver {
         return st ? st : fin(FIN_STORE, slot);
     }
     template <int PD, int PS>
-    int copy(void* d, const void* s, bool masked) {
+    int copy(void* d, const void* s, bool masked, int slot = S_ACTIVE) {
         LaunchScope scope(c, KB_BLAS * 3 + PD, n5() * (site_bytes(PS) + site_bytes(PD)), 0.0);
         k_copy<PD, PS><<<grid(), kRedThreads, 0, c->stream>>>(make_field<PD>(d, g, nrhs),
                                                                make_field<PS>(const_cast<void*>(s), g, nrhs),
-                                                               masked ? sc : nullptr, g);
+                                                               masked ? sc : nullptr, slot, g);
         return check_launch();
+    }
+    template <int PD, int PA, int PB>
+    int lincomb(void* d, const void* a, const void* b, int slot) {
+        LaunchScope scope(c, KB_BLAS * 3 + PD, n5() * (site_bytes(PA) + site_bytes(PB) + site_bytes(PD)),
+                          n5() * 72.0);
+        k_lincomb<PD, PA, PB><<<grid(), kRedThreads, 0, c->stream>>>(
+            make_field<PD>(d, g, nrhs), make_field<PA>(const_cast<void*>(a), g, nrhs),
+            make_field<PB>(const_cast<void*>(b), g, nrhs), sc, slot, g);
+        return check_launch();
+    }
+    template <int PA, int PB>
+    int dot(const void* a, const void* b, int mask_slot, int out_slot) {
+        {
+            LaunchScope scope(c, KB_BLAS * 3 + PB, n5() * (site_bytes(PA) + site_bytes(PB)), n5() * 48.0);
+            k_dot2<PA, PB><<<grid(), kRedThreads, 0, c->stream>>>(make_field<PA>(const_cast<void*>(a), g, nrhs),
+                                                                   make_field<PB>(const_cast<void*>(b), g, nrhs), part,
+                                                                   sc, mask_slot, g);
+        }
+        int st = check_launch();
+        return st ? st : fin(FIN_STORE, out_slot);
     }
     int pull() {
         int st = cuda_status(cudaMemcpyAsync(hsc, sc, sizeof(double) * S_NUM * kMaxRhs, cudaMemcpyDeviceToHost,
@@ -326,11 +426,12 @@ static int launch_pupd_w(Solver& S, void* x, void* r, void* p, void* w) {
     return check_launch();
 }
 
-// w = M_phi p (the fused iteration's first hop reads w)
+// w = M_phi p (the fused iteration's first hop reads w); with a mask, only the
+// right-hand sides whose entry is nonzero
 template <int PP>
-static int init_w(Solver& S, void* w, const void* p) {
+static int init_w(Solver& S, void* w, const void* p, const double* mask = nullptr) {
     M5Launch m{};
-    m.out = w; m.in = p; m.x = nullptr; m.coef = 1.0; m.nrhs = S.nrhs;
+    m.out = w; m.in = p; m.x = nullptr; m.coef = 1.0; m.nrhs = S.nrhs; m.mask = mask;
     set_sop(S.c, PP, SOP_MPHI, 0, m);
     return launch_m5(S.c, PP, m);
 }
@@ -420,8 +521,8 @@ static int true_residual(Solver& S, void* r, void* rs, const void* src, const vo
 // belongs to the returned x.
 template <int PP>
 static int run_mixed(Solver& S, Fields& F, const mdwf_solve_params& prm, double tol, int maxiter,
-                     std::vector<double>& maxr, std::vector<int>& rupd, std::vector<double>& last_true,
-                     cudaGraphExec_t* gexec, bool use_graph) {
+                     std::vector<double>& maxr, std::vector<int>& rupd, std::vector<int>& restarts,
+                     std::vector<double>& last_true, cudaGraphExec_t* gexec, bool use_graph) {
     mdwf_ctx* c = S.c;
     const int nrhs = S.nrhs;
     int st;
@@ -453,6 +554,22 @@ static int run_mixed(Solver& S, Fields& F, const mdwf_solve_params& prm, double 
     // FP32 carries ~7 digits, so it can reduce the residual 100x between FP64
     // updates; FP16 storage only ~3, so it updates after every 10x
     const double delta = prm.delta > 0 ? prm.delta : (PP == MDWF_F32 ? 0.005 : 0.1);
+    // At a reliable update the search direction is corrected for the new residual.
+    // With d = p - r_s = beta p_prev (formed by the last vector update), p_prev
+    // loses its component along the true r (in exact CG r is orthogonal to p_prev;
+    // after drift it is not), and beta takes the true |r|^2: p = r + gamma (d - c r)
+    // with gamma = |r|^2 / |r_s|^2 and c = <r, d> / |r|^2 (real parts: the CG runs
+    // on the real vector space of the fields). Where the true |r| exceeds the inner
+    // one more than twice (a small delta let the inner recurrence run far below
+    // what its precision carries), p restarts from r instead. An update is also
+    // forced when the inner |r| climbs 100x above the last true one. An inner
+    // breakdown (non-positive or non-finite <p, M^dag M p>) rolls back to the last
+    // update: x_s dropped, r_s = r, p = r, and the inner iterations between updates
+    // capped at half of the interval that broke down; after kMaxRollbacks of them,
+    // or from a non-finite residual, the right-hand side ends with MDWF_EBREAKDOWN.
+    constexpr double kDiverge2 = 1e4, kRestartRatio2 = 4.0;
+    constexpr int kMaxRollbacks = 8, kMinInterval = 16;
+    std::vector<int> since(nrhs, 0), cap(nrhs, maxiter), rollbacks(nrhs, 0);
     const int every = prm.check_every > 0 ? prm.check_every : 8;
     int it = 0;
     bool graph_ready = false;
@@ -485,47 +602,106 @@ static int run_mixed(Solver& S, Fields& F, const mdwf_solve_params& prm, double 
         if ((st = S.pull())) return st;
         // a right-hand side takes its FP64 reliable update when its inner residual has
         // fallen by delta since its last one (or the inner estimate says it has
-        // converged, or the iterations run out); the others go on untouched, so in a
-        // batch of masses each pays only for its own updates
-        bool any_active = false, need_update = false;
+        // converged, or the iterations run out, or a safeguard fires); the others go on
+        // untouched, so in a batch of masses each pays only for its own updates
+        bool any_active = false, need_update = false, any_rollback = false;
         for (int r = 0; r < nrhs; ++r) {
-            S.hsc[S_UPD * kMaxRhs + r] = 0.0;
-            if (S.hsc[S_ACTIVE * kMaxRhs + r] == 0.0) continue;
+            double* h = S.hsc + r;  // h[slot * kMaxRhs]
+            h[S_UPD * kMaxRhs] = 0.0;
+            h[S_RESTART * kMaxRhs] = 0.0;
+            if (h[S_ACTIVE * kMaxRhs] == 0.0) {
+                if (h[S_STATUS * kMaxRhs] == (double)MDWF_EBREAKDOWN && rollbacks[r] < kMaxRollbacks &&
+                    std::isfinite(last_true[r]) && it < maxiter) {
+                    rollbacks[r] += 1;
+                    restarts[r] += 1;
+                    cap[r] = std::max(kMinInterval, since[r] / 2);
+                    since[r] = 0;
+                    h[S_STATUS * kMaxRhs] = (double)MDWF_OK;
+                    h[S_ACTIVE * kMaxRhs] = 1.0;
+                    h[S_RR * kMaxRhs] = last_true[r];
+                    maxr[r] = sqrt(last_true[r]);
+                    h[S_RESTART * kMaxRhs] = 1.0;
+                    any_rollback = true;
+                    any_active = true;
+                }
+                continue;
+            }
             any_active = true;
-            const double rr = S.hsc[S_RR * kMaxRhs + r];
-            const double src2 = S.hsc[S_SRC2 * kMaxRhs + r];
+            since[r] += steps;
+            const double rr = h[S_RR * kMaxRhs];
+            const double src2 = h[S_SRC2 * kMaxRhs];
             const double rn = sqrt(rr);
-            if (rn < delta * maxr[r] || rr <= tol * tol * src2 || it >= maxiter) {
-                S.hsc[S_UPD * kMaxRhs + r] = 1.0;
+            if (rn < delta * maxr[r] || rr <= tol * tol * src2 || it >= maxiter || since[r] >= cap[r] ||
+                rr > kDiverge2 * last_true[r]) {
+                h[S_UPD * kMaxRhs] = 1.0;
+                h[S_C1 * kMaxRhs] = 1.0;
+                h[S_C2 * kMaxRhs] = -1.0;
                 need_update = true;
             }
             if (rn > maxr[r]) maxr[r] = rn;
         }
         if (!any_active) break;
-        if (!need_update) continue;
-        // reliable update of the flagged right-hand sides: x += x_s, x_s = 0,
-        // r = src - M^dag M x (FP64), r_s = r
-        NvtxRange nvtx_update("reliable update");
+        if (!need_update && !any_rollback) continue;
         if ((st = S.push())) return st;
-        {
-            LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, S.n5() * (2.0 * 192.0 + 2.0 * 96.0), S.n5() * 24.0);
-            k_accum_zero<MDWF_F64, MDWF_F32><<<S.grid(), kRedThreads, 0, c->stream>>>(
-                make_field<MDWF_F64>(F.xo, S.g, nrhs), make_field<MDWF_F32>(F.xs, S.g, nrhs), S.sc, S_UPD, S.g);
+        if (need_update) {
+            // reliable update of the flagged right-hand sides: d = p - r_s (into w, which
+            // is formed again below), x += x_s, x_s = 0, r = src - M^dag M x (FP64),
+            // r_s = r, then the corrected p
+            NvtxRange nvtx_update("reliable update");
+            if ((st = S.lincomb<PP, PP, MDWF_F32>(F.w, F.p, F.rs, S_UPD))) return st;
+            {
+                LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, S.n5() * (2.0 * 192.0 + 2.0 * 96.0), S.n5() * 24.0);
+                k_accum_zero<MDWF_F64, MDWF_F32><<<S.grid(), kRedThreads, 0, c->stream>>>(
+                    make_field<MDWF_F64>(F.xo, S.g, nrhs), make_field<MDWF_F32>(F.xs, S.g, nrhs), S.sc, S_UPD, S.g);
+            }
+            if ((st = check_launch())) return st;
+            if ((st = true_residual<MDWF_F32, true>(S, F.r, F.rs, F.src, F.xo, F.t64, true, true))) return st;
+            if ((st = S.dot<MDWF_F32, PP>(F.rs, F.w, S_UPD, S_C1))) return st;
+            if ((st = S.pull())) return st;
+            for (int r = 0; r < nrhs; ++r) {
+                double* h = S.hsc + r;
+                if (h[S_ACTIVE * kMaxRhs] == 0.0 || h[S_UPD * kMaxRhs] == 0.0) continue;
+                rupd[r] += 1;
+                since[r] = 0;
+                const double rr = h[S_AUX * kMaxRhs];
+                const double rr_inner = h[S_RR * kMaxRhs];
+                const double rd = h[S_C1 * kMaxRhs];
+                const double src2 = h[S_SRC2 * kMaxRhs];
+                last_true[r] = rr;
+                h[S_RR * kMaxRhs] = rr;
+                maxr[r] = sqrt(rr);
+                if (rr <= tol * tol * src2) {
+                    h[S_ACTIVE * kMaxRhs] = 0.0;
+                    h[S_C1 * kMaxRhs] = 1.0;
+                    h[S_C2 * kMaxRhs] = 0.0;
+                    continue;
+                }
+                const double gamma = rr / rr_inner, cr = rd / rr;
+                if (rr <= kRestartRatio2 * rr_inner && std::isfinite(gamma) && std::isfinite(cr)) {
+                    h[S_C1 * kMaxRhs] = 1.0 - gamma * cr;  // p = (1 - gamma c) r + gamma d
+                    h[S_C2 * kMaxRhs] = gamma;
+                } else {
+                    h[S_C1 * kMaxRhs] = 1.0;  // p = r
+                    h[S_C2 * kMaxRhs] = 0.0;
+                    restarts[r] += 1;
+                }
+            }
+            if ((st = S.push())) return st;
+            if ((st = S.lincomb<PP, MDWF_F32, PP>(F.p, F.rs, F.w, S_UPD))) return st;
+            if ((st = init_w<PP>(S, F.w, F.p, S.sc + S_UPD * kMaxRhs))) return st;
         }
-        if ((st = check_launch())) return st;
-        if ((st = true_residual<MDWF_F32, true>(S, F.r, F.rs, F.src, F.xo, F.t64, true, true))) return st;
-        if ((st = S.pull())) return st;
-        for (int r = 0; r < nrhs; ++r) {
-            if (S.hsc[S_ACTIVE * kMaxRhs + r] == 0.0 || S.hsc[S_UPD * kMaxRhs + r] == 0.0) continue;
-            rupd[r] += 1;
-            const double rr = S.hsc[S_AUX * kMaxRhs + r];
-            const double src2 = S.hsc[S_SRC2 * kMaxRhs + r];
-            last_true[r] = rr;
-            S.hsc[S_RR * kMaxRhs + r] = rr;
-            maxr[r] = sqrt(rr);
-            if (rr <= tol * tol * src2) S.hsc[S_ACTIVE * kMaxRhs + r] = 0.0;
+        if (any_rollback) {
+            // x_s = 0, r_s = r, p = r, w = M_phi p for the right-hand sides rolled back
+            {
+                LaunchScope scope(c, KB_BLAS * 3 + MDWF_F32, S.n5() * 96.0, 0.0);
+                k_zero<MDWF_F32><<<S.grid(), kRedThreads, 0, c->stream>>>(make_field<MDWF_F32>(F.xs, S.g, nrhs), S.sc,
+                                                                          S_RESTART, S.g);
+            }
+            if ((st = check_launch())) return st;
+            if ((st = S.copy<MDWF_F32, MDWF_F64>(F.rs, F.r, true, S_RESTART))) return st;
+            if ((st = S.copy<PP, MDWF_F64>(F.p, F.r, true, S_RESTART))) return st;
+            if ((st = init_w<PP>(S, F.w, F.p, S.sc + S_RESTART * kMaxRhs))) return st;
         }
-        if ((st = S.push())) return st;
     }
     return MDWF_OK;
 }
@@ -723,6 +899,11 @@ static size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 // Bytes of the solver workspace of solve_normal: FP64 r and t64, the inner
 // fields (x_s and r_s in FP32 for a mixed solve; p, t and w), CG scalars and
 // reduction partials.
+// Blocks per right-hand side of the solver's vector kernels and reductions: a
+// few per SM, more when the batch is small, so that one right-hand side fills
+// the GPU (two blocks per SM left its HBM bandwidth half used).
+static int red_blocks(int nrhs) { return 152 * std::max(2, std::min(8, 16 / nrhs)); }
+
 static size_t solver_bytes(const mdwf_ctx* c, int nrhs, int inner, int nb, int hb) {
     const size_t f64 = field_bytes(MDWF_F64, c->g, nrhs), f32 = field_bytes(MDWF_F32, c->g, nrhs);
     const size_t fpp = field_bytes(inner, c->g, nrhs);
@@ -744,6 +925,7 @@ int solve_normal(mdwf_ctx* c, int nrhs, void* xo, const void* src, const mdwf_so
     res.status.assign(nrhs, MDWF_OK);
     res.iters.assign(nrhs, 0);
     res.rupd.assign(nrhs, 0);
+    res.restarts.assign(nrhs, 0);
     res.rel.assign(nrhs, 0.0);
 
     // a captured graph needs a stream other than the legacy default one
@@ -758,7 +940,7 @@ int solve_normal(mdwf_ctx* c, int nrhs, void* xo, const void* src, const mdwf_so
     const size_t f64 = field_bytes(MDWF_F64, g, nrhs), f32 = field_bytes(MDWF_F32, g, nrhs);
     const size_t fpp = field_bytes(inner, g, nrhs);
     auto up = [](size_t v) { return (v + 255) / 256 * 256; };
-    const int nb = 2 * 152;
+    const int nb = red_blocks(nrhs);
     if (c->autotune && c->sb_tune[inner][nrhs] == 0) {
         int sb;
         if ((st = tune_hop(c, inner, nrhs, &sb))) return st;
@@ -816,9 +998,11 @@ int solve_normal(mdwf_ctx* c, int nrhs, void* xo, const void* src, const mdwf_so
         if (inner == MDWF_F64)
             st = run_plain(S, F, prm, tol, maxiter, last_true, &gexec, use_graph);
         else if (inner == MDWF_F32)
-            st = run_mixed<MDWF_F32>(S, F, prm, tol, maxiter, maxr, res.rupd, last_true, &gexec, use_graph);
+            st = run_mixed<MDWF_F32>(S, F, prm, tol, maxiter, maxr, res.rupd, res.restarts, last_true, &gexec,
+                                     use_graph);
         else
-            st = run_mixed<MDWF_F16N>(S, F, prm, tol, maxiter, maxr, res.rupd, last_true, &gexec, use_graph);
+            st = run_mixed<MDWF_F16N>(S, F, prm, tol, maxiter, maxr, res.rupd, res.restarts, last_true, &gexec,
+                                      use_graph);
         if (st) { ret = st; break; }
 
         if ((st = S.pull())) { ret = st; break; }
@@ -919,8 +1103,8 @@ extern "C" int mdwf_cgne(mdwf_ctx* c, double* x, const double* b, int nrhs, cons
         auto grow = [](size_t need_b, const Workspace& ws) { return need_b > ws.bytes ? need_b - ws.bytes : 0; };
         size_t extra = grow(keep_need, c->io) + grow(f64, c->tmp[0]) + grow(f64, c->tmp[1]);
         // the solver workspace, or the autotuner's two scratch fields before it (freed after tuning)
-        size_t later = grow(solver_bytes(c, nrhs, prm.inner_prec, 2 * 152, hop_blocks(c, prm.inner_prec, nrhs)),
-                            c->solver);
+        size_t later = grow(
+            solver_bytes(c, nrhs, prm.inner_prec, red_blocks(nrhs), hop_blocks(c, prm.inner_prec, nrhs)), c->solver);
         if (c->autotune) {
             const size_t tune_f = 2 * up(field_bytes(MDWF_F64, g, nrhs));
             if (tune_f > later) later = tune_f;
@@ -1015,6 +1199,7 @@ extern "C" int mdwf_cgne(mdwf_ctx* c, double* x, const double* b, int nrhs, cons
             info[r].status = res.status[r];
             info[r].iters = res.iters[r];
             info[r].reliable_updates = res.rupd[r];
+            info[r].restarts = res.restarts[r];
             info[r].true_res = res.rel[r];
             info[r].res_m = bb[r] > 0 ? sqrt(rr[r] / bb[r]) : 0.0;
             info[r].seconds = secs;

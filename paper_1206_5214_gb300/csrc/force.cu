@@ -203,6 +203,7 @@ extern "C" int mdwf_force(mdwf_ctx* c, double* dSdU, double* dSdb5, double* dSdc
         info->status = res.status[0];
         info->iters = res.iters[0];
         info->reliable_updates = res.rupd[0];
+        info->restarts = res.restarts[0];
         info->true_res = res.rel[0];
         info->res_m = 0.0;
         info->seconds = 0.0;

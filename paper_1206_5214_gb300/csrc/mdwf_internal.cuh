@@ -52,9 +52,12 @@ constexpr int kMaxRhs = 64;  // right-hand sides per call
 
 // CG scalars per right-hand side, stored [slot][kMaxRhs] in device memory:
 // |r|^2, <p, M^dag M p>, alpha, beta, |src|^2, active flag, status, scratch,
-// iteration count, and the flag of a right-hand side whose FP64 reliable
-// update runs now.
-enum CgSlot { S_RR = 0, S_PAP, S_ALPHA, S_BETA, S_SRC2, S_ACTIVE, S_STATUS, S_AUX, S_ITERS, S_UPD, S_NUM };
+// iteration count, the flag of a right-hand side whose FP64 reliable update
+// runs now, the flag of one that rolls back to its last update, and two
+// coefficients of the search-direction correction of a reliable update.
+enum CgSlot {
+    S_RR = 0, S_PAP, S_ALPHA, S_BETA, S_SRC2, S_ACTIVE, S_STATUS, S_AUX, S_ITERS, S_UPD, S_RESTART, S_C1, S_C2, S_NUM
+};
 // What a finished reduction v does: store it in a slot, or form alpha from
 // v = <p, M^dag M p>, or beta from v = |r_new|^2 (and count the iteration).
 enum FinMode { FIN_STORE = 0, FIN_ALPHA = 1, FIN_BETA = 2 };
@@ -913,7 +916,7 @@ int tune_hop(mdwf_ctx* c, int prec, int nrhs, int* chosen);
 
 // solver (cg.cu)
 struct NormalResult {
-    std::vector<int> status, iters, rupd;
+    std::vector<int> status, iters, rupd, restarts;
     std::vector<double> rel;  // |src - M^dag M x| / |src| in FP64
 };
 int solve_normal(mdwf_ctx* c, int nrhs, void* xo, const void* src, const mdwf_solve_params& prm, NormalResult& res);

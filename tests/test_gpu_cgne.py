@@ -244,6 +244,47 @@ def test_Ls16_iteration_without_t_field_matches_t_field():
     assert np.linalg.norm(x0 - x1) <= 1e-5 * np.linalg.norm(x1)
 
 
+@pytest.mark.parametrize("inner,dims,Ls,seed,delta", [
+    (F16N, (8, 8, 8, 8), 16, 1097, 0.0),
+    (F16N, (4, 4, 4, 4), 8, 1001, 0.01),
+    (F32, (4, 4, 4, 4), 8, 1001, 1e-4),
+    (F32, (4, 4, 4, 8), 16, 1096, 1e-6),
+    (F32, (8, 8, 8, 8), 16, 1097, 1e-4),
+], ids=["f16n-8x8x8x8-default", "f16n-4x4x4x4-Ls8-1e-2", "f32-4x4x4x4-Ls8-1e-4", "f32-4x4x4x8-1e-6",
+        "f32-8x8x8x8-1e-4"])
+def test_mixed_solve_safeguards(inner, dims, Ls, seed, delta):
+    """Cases in which the inner iteration, with p kept unchanged across reliable updates,
+    drifted from the true residual and broke down (a small delta) or diverged (FP16
+    storage on a rough 8^4 field). With the search direction corrected at each update
+    (its component along the new residual removed, beta from the true |r|^2), a forced
+    update when the inner |r| climbs and a roll-back after a breakdown, every one reaches
+    1e-10, confirmed by the oracle's residual."""
+    U = sy.gauge_field(dims, 0.3, seed)
+    b = sy.gaussian_field(dims, Ls, seed + 1000)
+    p = oracle.Params(dims, Ls, 1.8, 1.5, 0.5, 0.01)
+    h = mdwf.mdwf_create(dims, Ls, 1.8, 1.5, 0.5, 0.01)
+    try:
+        mdwf.mdwf_load_gauge(h, torch.from_numpy(U).cuda())
+        bb = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+        x = torch.zeros_like(bb)
+        st, info = mdwf.mdwf_cgne(h, x, bb, tol=1e-10, inner_prec=inner, delta=delta, raise_on_error=False)
+        xs = x.cpu().numpy()
+    finally:
+        mdwf.mdwf_destroy(h)
+    assert st == 0 and info[0].true_res <= 1e-10, info[0].as_dict()
+    assert oracle_residual(xs, b, U, p) <= 1.05e-10
+
+
+def test_default_delta_takes_no_restart():
+    """At the default threshold a well-behaved FP32 solve neither restarts p nor breaks
+    down: every reliable update finds the true residual within twice the inner one."""
+    dims, Ls, mf = (4, 4, 4, 8), 16, 0.01
+    U = sy.gauge_field(dims, 0.3, 1096)
+    b = sy.gaussian_field(dims, Ls, 2096)
+    st, info, _ = gpu_solve(dims, Ls, 1.5, 0.5, mf, U, b, F32)
+    assert st == 0 and info[0].restarts == 0 and info[0].reliable_updates >= 2
+
+
 def test_cgne_Ls16_multi_mass_without_t_field():
     """Three masses in one Ls = 16 mixed FP32 solve with the t field dropped: each
     right-hand side's I^dag takes its own mass in the wrap-around term."""
