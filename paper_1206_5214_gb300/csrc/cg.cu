@@ -79,6 +79,8 @@ __global__ void __launch_bounds__(kRedThreads) k_norm(Field<PA> a, double* part,
 constexpr int kFinThreads = 1024;
 
 __global__ void __launch_bounds__(kFinThreads) k_finalize(const double* part, int nb, double* sc, int mode, int slot) {
+    pdl_wait();  // the partials come from the kernel before
+    pdl_release();
     const int rhs = blockIdx.x;
     const double* pp = part + (size_t)rhs * nb;
     const int bd = blockDim.x;
@@ -113,6 +115,8 @@ __global__ void __launch_bounds__(128) k_pupd_w(Field<PX> x, Field<PR> r, Field<
     typedef typename PrecTraits<PP>::real RP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     RP* hs = reinterpret_cast<RP*>(smem_raw);
+    pdl_wait();  // r and the CG scalars come from the kernels before
+    pdl_release();
     const int rhs = blockIdx.y;
     if (SC(S_ACTIVE, rhs) == 0.0) return;  // uniform over the block
     const int Ls = g.Ls, s = threadIdx.x, ly = threadIdx.y;
@@ -334,12 +338,16 @@ struct Solver {
     double n5() const { return (double)g.Vh * g.Ls * nrhs; }
     int fin(int mode, int slot = 0) {
         LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, 8.0 * nrhs * nb, 0.0);
-        k_finalize<<<nrhs, kFinThreads, 0, c->stream>>>(part, nb, sc, mode, slot);
+        if (cudaError_t e = launch_pdl(k_finalize, dim3(nrhs), dim3(kFinThreads), 0, c->stream, part, nb, sc, mode,
+                                       slot))
+            return cuda_status(e);
         return check_launch();
     }
     int fin_hop(int mode) {
         LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, 8.0 * nrhs * hb, 0.0);
-        k_finalize<<<nrhs, kFinThreads, 0, c->stream>>>(hpart, hb, sc, mode, 0);
+        if (cudaError_t e = launch_pdl(k_finalize, dim3(nrhs), dim3(kFinThreads), 0, c->stream, hpart, hb, sc, mode,
+                                       0))
+            return cuda_status(e);
         return check_launch();
     }
     template <int P>
@@ -418,11 +426,10 @@ static int launch_pupd_w(Solver& S, void* x, void* r, void* p, void* w) {
     const RP* gs = !c->sdep ? nullptr
                             : reinterpret_cast<const RP*>(PP == MDWF_F64 ? (const void*)c->gs64 : (const void*)c->gs32);
     LaunchScope scope(c, KB_BLAS * 3 + PP, S.n5() * (3.0 * site_bytes(PR) + 3.0 * site_bytes(PP)), S.n5() * 144.0);
-    k_pupd_w<PR, PR, PP><<<grid, block, smem, c->stream>>>(make_field<PR>(x, S.g, S.nrhs),
-                                                            make_field<PR>(r, S.g, S.nrhs),
-                                                            make_field<PP>(p, S.g, S.nrhs),
-                                                            make_field<PP>(w, S.g, S.nrhs), S.sc, mass, gs, S.g,
-                                                            c->b5, c->c5);
+    if (cudaError_t e = launch_pdl(k_pupd_w<PR, PR, PP>, grid, block, smem, c->stream, make_field<PR>(x, S.g, S.nrhs),
+                                   make_field<PR>(r, S.g, S.nrhs), make_field<PP>(p, S.g, S.nrhs),
+                                   make_field<PP>(w, S.g, S.nrhs), (const double*)S.sc, mass, gs, S.g, c->b5, c->c5))
+        return cuda_status(e);
     return check_launch();
 }
 

@@ -784,8 +784,6 @@ __global__ void __launch_bounds__(128, STAGE == 1   ? MDWF_MINB_STAGE
     R* hs = mat2 + (dense && FUSE == FUSE_T ? 2 * Ls * Ls : 0);   // [SB][site_stride], rows of kRowStride
     const int s = threadIdx.x, ly = threadIdx.y;
     const int rhs = blockIdx.x % hp.nrhs;
-    // a right-hand side left out of this launch (block-uniform: before any barrier)
-    if (hp.mask && hp.mask[rhs] == 0.0) return;
     const long long sblk = blockIdx.x / hp.nrhs;
     const int tid = ly * blockDim.x + s, nthr = blockDim.x * blockDim.y;
     if (dense) {
@@ -806,6 +804,26 @@ __global__ void __launch_bounds__(128, STAGE == 1   ? MDWF_MINB_STAGE
         gfac = hp.gs[64 + s];
         gpre = hp.gs[128 + s];
     }
+    // the site's eight links into L1 before the terms need them (the links come from
+    // L2, and a link load that waits for L2 inside a term stalls its chain): thread s
+    // of the column asks for the lines of link s / 2 (forward links at the site,
+    // backward ones at the neighbour), two lines per 80-byte FP32 link. The links and
+    // the neighbour table do not change during a solve, so this runs before the wait
+    // for the previous kernel.
+    if constexpr (P != MDWF_F64 && STAGE != 2) {
+        if (active && s < 16) {
+            const int* nbi = reinterpret_cast<const int*>(hp.nbr + ((long long)hp.out_parity * hp.g.Vh + site) * 2);
+            const int t = s >> 1, mu = t & 3;
+            const bool fwd = t < 4;
+            const long long j = fwd ? site : (long long)__ldg(nbi + 4 + mu);
+            const long long li = ((long long)(fwd ? hp.out_parity : 1 - hp.out_parity) * 4 + mu) * hp.g.Vh + j;
+            if (j >= 0) prefetch_l1(reinterpret_cast<const char*>(U.u + li * 5) + (s & 1) * 64);  // halo: none
+        }
+    }
+    pdl_wait();
+    pdl_release();
+    // a right-hand side left out of this launch (block-uniform: before any barrier)
+    if (hp.mask && hp.mask[rhs] == 0.0) return;
     R acc[24];
 #pragma unroll
     for (int k = 0; k < 24; ++k) acc[k] = 0;
@@ -823,19 +841,6 @@ __global__ void __launch_bounds__(128, STAGE == 1   ? MDWF_MINB_STAGE
         hop_bulk<P, DAG>(acc, in, U, hp, bk, bars, active, site, s, ly, tid, rbase);
     } else if (active) {
         const int4* nb = hp.nbr + ((long long)hp.out_parity * hp.g.Vh + site) * 2;
-        // the site's eight links into L1 before the terms need them (the links come from
-        // L2, and a link load that waits for L2 inside a term stalls its chain): thread s
-        // of the column asks for the lines of link s / 2 (forward links at the site,
-        // backward ones at the neighbour), two lines per 80-byte FP32 link
-        if constexpr (P != MDWF_F64) {
-            if (s < 16) {
-                const int t = s >> 1, mu = t & 3;
-                const bool fwd = t < 4;
-                const long long j = fwd ? site : (long long)__ldg(reinterpret_cast<const int*>(nb) + 4 + mu);
-                const long long li = ((long long)(fwd ? hp.out_parity : 1 - hp.out_parity) * 4 + mu) * hp.g.Vh + j;
-                if (j >= 0) prefetch_l1(reinterpret_cast<const char*>(U.u + li * 5) + (s & 1) * 64);  // halo: none
-            }
-        }
         if constexpr (STAGE == 3) {
             hop_prefetch<P, DAG>(acc, in, U, hp, reinterpret_cast<const int*>(nb), site, s, rbase);
         } else if constexpr (STAGE == 1) {
@@ -1057,7 +1062,7 @@ static int launch_hop_variant(mdwf_ctx* c, const HopLaunch& h, const HopParams<t
     const double bytes = n5 * fields + 8.0 * g.Vh * link_bytes(P);
     const double flops = n5 * (1320.0 + (G ? 72.0 : 0.0) + 144.0 + (X ? 48.0 : 0.0) + (FU ? 144.0 : 0.0));
     LaunchScope scope(c, base * 3 + P, bytes, flops);
-    kern<<<grid, block, smem, c->stream>>>(out, in, xf, U, hp, fa);
+    if (cudaError_t e = launch_pdl(kern, grid, block, smem, c->stream, out, in, xf, U, hp, fa)) return cuda_status(e);
     return check_launch();
 }
 

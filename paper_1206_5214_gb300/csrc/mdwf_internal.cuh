@@ -137,6 +137,32 @@ __device__ __forceinline__ void prefetch_l1(const void* p) {
     asm volatile("prefetch.global.L1 [%0];\n" ::"l"(p));
 }
 
+// Programmatic dependent launch. A kernel launched by launch_pdl may be
+// scheduled while the kernel before it on the stream is still running (its
+// blocks then wait on SMs that the earlier kernel has left). Such a kernel
+// calls pdl_wait() before it reads anything an earlier kernel wrote, and every
+// one of its blocks reaches pdl_wait() before it exits, so that it completes
+// after its predecessor. pdl_release() lets the next kernel be scheduled.
+// Without a programmatic predecessor both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                              Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Bounds-checked debug build (-DMDWF_BOUNDS_CHECK=1, a separate library): every
 // field access checks 0 <= sr < (sites x right-hand sides of the view) and
 // 0 <= s < Ls, and every link access 0 <= index < 8 Vh; an access out of range
