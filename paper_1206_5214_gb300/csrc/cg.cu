@@ -1161,16 +1161,6 @@ extern "C" int mdwf_cgne(mdwf_ctx* c, double* x, const double* b, int nrhs, cons
         void* xo_r = (char*)xo + (size_t)r * f1;
         point_at(r);
         if (!keep && (st = prepare_rhs(c, sw, b, where, r))) return st;  // b_e, b'_o again
-        if ((st = apply_op(c, sw.t, xo_r, MDWF_F64, 1, 0, r))) return st;
-        {
-            M5Launch d{};  // t = b' - M x
-            d.nrhs = 1; d.out = sw.t; d.in = sw.t; d.x = sw.bp; d.coef = -1.0;
-            set_sop(c, MDWF_F64, SOP_ID, 0, d);
-            offset_rhs(c, MDWF_F64, r, d);
-            if ((st = launch_m5(c, MDWF_F64, d))) return st;
-        }
-        if ((st = field_dot64(c, sw.t, sw.t, 1, &rr[r]))) return st;
-        if ((st = field_dot64(c, sw.bp, sw.bp, 1, &bb[r]))) return st;
         {
             M5Launch f{};  // xe (scratch until it is formed below) = M_phi x_o
             f.nrhs = 1; f.out = sw.xe; f.in = xo_r; f.x = nullptr; f.coef = 1.0;
@@ -1178,12 +1168,38 @@ extern "C" int mdwf_cgne(mdwf_ctx* c, double* x, const double* b, int nrhs, cons
             offset_rhs(c, MDWF_F64, r, f);
             if ((st = launch_m5(c, MDWF_F64, f))) return st;
         }
-        HopLaunch h{};
+        HopLaunch h{};  // t = 1/2 A H_eo M_phi x_o
         h.nrhs = 1; h.b5 = c->b5; h.c5 = c->c5; h.mass = c->mass64;
         h.out = sw.t; h.in = sw.xe; h.x = nullptr; h.coef = 0.5; h.out_parity = 0; h.gather = 0; h.dagger = 0;
         set_sop(c, MDWF_F64, SOP_A, 0, h);
         offset_rhs(c, MDWF_F64, r, h);
         if ((st = launch_hop(c, MDWF_F64, h))) return st;
+        // M x_o = x_o - 1/4 A H_oe z with z = K H_eo M_phi x_o = M_phi (A H_eo M_phi x_o) = 2 M_phi t:
+        // the hop of the reconstruction is the first hop of M, so only the second runs here
+        void* z = c->tmp[0].p;
+        void* mx = c->tmp[1].p;
+        {
+            M5Launch f{};
+            f.nrhs = 1; f.out = z; f.in = sw.t; f.x = nullptr; f.coef = 2.0;
+            set_sop(c, MDWF_F64, SOP_MPHI, 0, f);
+            offset_rhs(c, MDWF_F64, r, f);
+            if ((st = launch_m5(c, MDWF_F64, f))) return st;
+        }
+        note_apply(c, MDWF_F64);
+        h.out = mx; h.in = z; h.x = xo_r; h.coef = -0.25; h.out_parity = 1; h.gather = 0; h.dagger = 0;
+        h.mass = c->mass64;
+        set_sop(c, MDWF_F64, SOP_A, 0, h);
+        offset_rhs(c, MDWF_F64, r, h);
+        if ((st = launch_hop(c, MDWF_F64, h))) return st;
+        {
+            M5Launch d{};  // mx = b' - M x
+            d.nrhs = 1; d.out = mx; d.in = mx; d.x = sw.bp; d.coef = -1.0;
+            set_sop(c, MDWF_F64, SOP_ID, 0, d);
+            offset_rhs(c, MDWF_F64, r, d);
+            if ((st = launch_m5(c, MDWF_F64, d))) return st;
+        }
+        if ((st = field_dot64(c, mx, mx, 1, &rr[r]))) return st;
+        if ((st = field_dot64(c, sw.bp, sw.bp, 1, &bb[r]))) return st;
         M5Launch m{};
         m.nrhs = 1; m.out = sw.xe; m.in = sw.be; m.x = sw.t; m.coef = 1.0;
         set_sop(c, MDWF_F64, SOP_A, 0, m);
