@@ -76,10 +76,14 @@ __global__ void __launch_bounds__(kRedThreads) k_norm(Field<PA> a, double* part,
 // One block of kFinThreads per right-hand side sums the nb partials in a
 // fixed order (four independent running sums per thread, so that the loads
 // of a thread are in flight together), then updates the CG scalars.
+// late = 1: the partials come from the kernel before the previous one, which
+// the previous kernel waited for before it let this one start; the block then
+// runs beside the previous kernel's end and waits for it only before it exits.
 constexpr int kFinThreads = 1024;
 
-__global__ void __launch_bounds__(kFinThreads) k_finalize(const double* part, int nb, double* sc, int mode, int slot) {
-    pdl_wait();  // the partials come from the kernel before
+__global__ void __launch_bounds__(kFinThreads) k_finalize(const double* part, int nb, double* sc, int mode, int slot,
+                                                          int late) {
+    if (!late) pdl_wait();  // the partials come from the kernel before
     pdl_release();
     const int rhs = blockIdx.x;
     const double* pp = part + (size_t)rhs * nb;
@@ -95,6 +99,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(const double* part, in
     for (; i < nb; i += bd) v0 += pp[i];
     double v = block_sum((v0 + v1) + (v2 + v3));
     if (threadIdx.x == 0) cg_scalar_update(sc, rhs, mode, slot, v);
+    if (late) pdl_wait();  // complete after the previous kernel
 }
 
 // Column-blocked update for the fused iteration: block = (Ls, SB) threads
@@ -339,14 +344,15 @@ struct Solver {
     int fin(int mode, int slot = 0) {
         LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, 8.0 * nrhs * nb, 0.0);
         if (cudaError_t e = launch_pdl(k_finalize, dim3(nrhs), dim3(kFinThreads), 0, c->stream, part, nb, sc, mode,
-                                       slot))
+                                       slot, 0))
             return cuda_status(e);
         return check_launch();
     }
-    int fin_hop(int mode) {
+    // late: the partials come from the hop before the previous one (see k_finalize)
+    int fin_hop(int mode, int late = 0) {
         LaunchScope scope(c, KB_BLAS * 3 + MDWF_F64, 8.0 * nrhs * hb, 0.0);
         if (cudaError_t e = launch_pdl(k_finalize, dim3(nrhs), dim3(kFinThreads), 0, c->stream, hpart, hb, sc, mode,
-                                       0))
+                                       0, late))
             return cuda_status(e);
         return check_launch();
     }
@@ -479,11 +485,12 @@ static int cg_iteration_fused(Solver& S, void* x, void* r, void* p, void* t, voi
     if ((st = launch_hop(c, PP, h))) return st;
     h.mat2 = nullptr;
     h.no_t = 0;
-    if ((st = S.fin_hop(FIN_ALPHA))) return st;
+    // K1' does not need alpha, so alpha is formed after it is launched, beside its end
     h.out = c->tmp[0].p; h.in = c->tmp[1].p; h.x = nullptr; h.coef = 1.0; h.out_parity = 0; h.dagger = 1;
     set_sop(c, PP, SOP_K, 1, h);
     h.fuse = 0;
     if ((st = launch_hop(c, PP, h))) return st;
+    if ((st = S.fin_hop(FIN_ALPHA, 1))) return st;
     h.out = c->tmp[1].p; h.in = c->tmp[0].p; h.x = no_t ? c->tmp[1].p : t; h.coef = -0.25; h.out_parity = 1;
     h.dagger = 1;
     set_sop(c, PP, SOP_MPHI, 1, h);
