@@ -278,6 +278,53 @@ def test_mixed_solve_safeguards(inner, dims, Ls, seed, delta):
     assert oracle_residual(xs, b, U, p) <= 1.05e-10
 
 
+@pytest.mark.parametrize("inner", [F32, F16N], ids=["mixed-f32", "mixed-f16n"])
+def test_near_fp64_limit_with_no_threshold(inner):
+    """delta = 1e-30 never triggers an update on its own: the inner iteration runs until
+    its estimate says 1e-14 or it breaks down. The corrected directions, restarts and
+    roll-backs still take the solve to a true residual of 1e-14, near the FP64 limit,
+    confirmed by the oracle."""
+    dims, Ls = (4, 4, 4, 4), 8
+    U = sy.gauge_field(dims, 0.3, 1001)
+    b = sy.gaussian_field(dims, Ls, 2001)
+    p = oracle.Params(dims, Ls, 1.8, 1.5, 0.5, 0.01)
+    h = mdwf.mdwf_create(dims, Ls, 1.8, 1.5, 0.5, 0.01)
+    try:
+        mdwf.mdwf_load_gauge(h, torch.from_numpy(U).cuda())
+        bb = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+        x = torch.zeros_like(bb)
+        st, info = mdwf.mdwf_cgne(h, x, bb, tol=1e-14, inner_prec=inner, delta=1e-30, maxiter=4000,
+                                  raise_on_error=False)
+        xs = x.cpu().numpy()
+    finally:
+        mdwf.mdwf_destroy(h)
+    assert st == 0 and info[0].true_res <= 1e-14 and info[0].restarts >= 1, info[0].as_dict()
+    assert oracle_residual(xs, b, U, p) <= 2e-14
+
+
+def test_roll_back_after_inner_breakdown():
+    """With an unreachable target (1e-30) and threshold the inner FP32 iteration runs on
+    until it breaks down; each breakdown rolls back to the last reliable update (more
+    restarts than updates: an update restarts p at most once). The solve ends at maxiter
+    with MDWF_ENOCONV, a finite x and the FP64 residual at its floor."""
+    dims, Ls = (4, 4, 2, 4), 6
+    U = sy.gauge_field(dims, 0.3, 1093)
+    b = sy.gaussian_field(dims, Ls, 2093)
+    h = mdwf.mdwf_create(dims, Ls, 1.8, 1.5, 0.5, 0.01)
+    try:
+        mdwf.mdwf_load_gauge(h, torch.from_numpy(U).cuda())
+        bb = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+        x = torch.zeros_like(bb)
+        st, info = mdwf.mdwf_cgne(h, x, bb, tol=1e-30, inner_prec=F32, delta=1e-30, maxiter=3000,
+                                  raise_on_error=False)
+        finite = bool(torch.isfinite(x).all())
+    finally:
+        mdwf.mdwf_destroy(h)
+    assert st == mdwf.MDWF_ENOCONV and finite
+    assert info[0].restarts > info[0].reliable_updates, info[0].as_dict()
+    assert info[0].true_res <= 1e-14
+
+
 def test_default_delta_takes_no_restart():
     """At the default threshold a well-behaved FP32 solve neither restarts p nor breaks
     down: every reliable update finds the true residual within twice the inner one."""
