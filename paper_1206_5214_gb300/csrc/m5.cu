@@ -24,6 +24,48 @@ __global__ void __launch_bounds__(256) m5_kernel(Field<P> out, Field<P> in, Fiel
     if (mask && mask[rhs] == 0.0) return;  // block-uniform, before any barrier
     const long long sblk = blockIdx.x / nrhs;
     const int tid = ly * blockDim.x + s, nthr = blockDim.x * blockDim.y;
+    // The bidiagonal operators (M_phi, C, I = M+ + M- C) and the identity need only
+    // the s +- 1 neighbours of a column, which share the thread's cache lines: each
+    // thread reads its spinor and the two half spinors straight from memory, with no
+    // staging and no barrier (the identity also in place; the others out of place,
+    // since a neighbour's element may be overwritten). Chirality 0 (reals 0..11)
+    // couples to s - 1 and chirality 1 to s + 1; the adjoint (swap) exchanges them;
+    // the wrap-around term carries -m. Block-uniform.
+    const bool bidiag = sop == SOP_MPHI || sop == SOP_C || sop == SOP_MEE;
+    if (!dense && (sop == SOP_ID || (bidiag && (const void*)out.v != (const void*)in.v))) {
+        const long long site = sblk * blockDim.y + ly;
+        if (site >= g.Vh) return;
+        const long long sr = (long long)rhs * g.Vh + site;
+        R v[24];
+        in.load(sr, s, v);
+        if (bidiag) {
+            const R w0 = sop == SOP_MPHI ? sc.b5 : sop == SOP_MEE ? sc.Mp : R(0);
+            const R w1 = sop == SOP_MPHI ? sc.c5 : sop == SOP_MEE ? sc.Mm : R(1);
+            const R m = mass[rhs];
+            const bool sw = swap != 0;
+            const int up = s + 1 < Ls ? s + 1 : 0, dn = s > 0 ? s - 1 : Ls - 1;
+            const R f0 = w1 * ((sw ? s < Ls - 1 : s > 0) ? R(1) : -m);
+            const R f1 = w1 * ((sw ? s > 0 : s < Ls - 1) ? R(1) : -m);
+            R h0[12], h1[12];
+            in.load_half(sr, sw ? up : dn, 0, h0);
+            in.load_half(sr, sw ? dn : up, 1, h1);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                v[k] = w0 * v[k] + f0 * h0[k];
+                v[12 + k] = w0 * v[12 + k] + f1 * h1[k];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 24; ++k) v[k] *= coef;
+        if (XPAY) {
+            R xv[24];
+            xf.load(sr, s, xv);
+#pragma unroll
+            for (int k = 0; k < 24; ++k) v[k] += xv[k];
+        }
+        out.store(sr, s, v);
+        return;
+    }
     if (dense) {
         const R* gm = tab + (size_t)rhs * 2 * Ls * Ls;
         for (int i = tid; i < 2 * Ls * Ls; i += nthr) mat[i] = gm[i];
