@@ -289,6 +289,14 @@ typedef struct {
  * x_e = I_rr^-1 (b_e - D_rb x_o). x has b's format and location.
  * mf_per_rhs: NULL or nrhs masses (host). params may be NULL (defaults).
  * info: NULL or an array of nrhs entries. Synchronises the stream.
+ * Mixed precision: each right-hand side takes its own FP64 reliable update
+ * when its inner |r| has fallen by delta (or the inner estimate reaches tol,
+ * or maxiter is reached, or the inner |r| climbs 100x above the last true
+ * one); the update corrects the search direction for the true residual, or
+ * restarts it when the true |r| exceeds the inner one more than twice; an
+ * inner breakdown rolls back to the last update (at most 8 times, then
+ * MDWF_EBREAKDOWN). The reported true_res and the tol test are always the
+ * FP64 residual of the returned x.
  * Returns the worst per-rhs status.
  */
 int mdwf_cgne(mdwf_ctx *ctx, double *x, const double *b, int nrhs, const double *mf_per_rhs,
