@@ -928,10 +928,26 @@ static size_t solver_bytes(const mdwf_ctx* c, int nrhs, int inner, int nb, int h
            up256(sizeof(double) * nrhs * hb);
 }
 
+// M x of the returned x, formed by the solve's last FP64 true residual: an FP64
+// field of nrhs slots in the solver's workspace (valid until the next solve) and
+// the right-hand sides for which it holds (mdwf_cgne reuses it for |b' - M x|)
+struct SolvedMx {
+    const void* mx = nullptr;
+    std::vector<char> ok;
+};
+
+static int solve_normal_mx(mdwf_ctx* c, int nrhs, void* xo, const void* src, const mdwf_solve_params& prm,
+                           NormalResult& res, SolvedMx* smx);
+
 // Solves M^dag M x = src for nrhs FP64 internal odd fields (x starts at zero).
 // Plain FP64 CG or mixed precision with FP64 reliable updates (prm.inner_prec).
 int solve_normal(mdwf_ctx* c, int nrhs, void* xo, const void* src, const mdwf_solve_params& prm,
                  NormalResult& res) {
+    return solve_normal_mx(c, nrhs, xo, src, prm, res, nullptr);
+}
+
+static int solve_normal_mx(mdwf_ctx* c, int nrhs, void* xo, const void* src, const mdwf_solve_params& prm,
+                           NormalResult& res, SolvedMx* smx) {
     const double tol = prm.tol > 0 ? prm.tol : 1e-10;
     const int maxiter = prm.maxiter > 0 ? prm.maxiter : 20000;
     const int inner = prm.inner_prec;
@@ -1020,6 +1036,14 @@ int solve_normal(mdwf_ctx* c, int nrhs, void* xo, const void* src, const mdwf_so
         if (st) { ret = st; break; }
 
         if ((st = S.pull())) { ret = st; break; }
+        // x changes only at the FP64 true residuals, which form M x on the way: the plain
+        // CG ends on one for every right-hand side, the mixed solve on each one's last
+        // update (or the residual of the guess)
+        if (smx) {
+            smx->mx = F.t64;
+            smx->ok.assign(nrhs, 0);
+            for (int r = 0; r < nrhs; ++r) smx->ok[r] = inner == MDWF_F64 || prm.guess || res.rupd[r] > 0;
+        }
         // the last FP64 true residual |src - M^dag M x| / |src| of every right-hand side
         for (int r = 0; r < nrhs; ++r) {
             res.status[r] = (int)S.hsc[S_STATUS * kMaxRhs + r];
@@ -1160,7 +1184,8 @@ extern "C" int mdwf_cgne(mdwf_ctx* c, double* x, const double* b, int nrhs, cons
         }
 
     NormalResult res;
-    if ((st = solve_normal(c, nrhs, xo, src, prm, res))) return st;
+    SolvedMx smx;
+    if ((st = solve_normal_mx(c, nrhs, xo, src, prm, res, &smx))) return st;
 
     // per right-hand side: |b' - M x| / |b'| and x_e = A b_e + 1/2 A H_eo M_phi x_o
     std::vector<double> bb(nrhs), rr(nrhs);
@@ -1181,26 +1206,30 @@ extern "C" int mdwf_cgne(mdwf_ctx* c, double* x, const double* b, int nrhs, cons
         set_sop(c, MDWF_F64, SOP_A, 0, h);
         offset_rhs(c, MDWF_F64, r, h);
         if ((st = launch_hop(c, MDWF_F64, h))) return st;
-        // M x_o = x_o - 1/4 A H_oe z with z = K H_eo M_phi x_o = M_phi (A H_eo M_phi x_o) = 2 M_phi t:
-        // the hop of the reconstruction is the first hop of M, so only the second runs here
-        void* z = c->tmp[0].p;
         void* mx = c->tmp[1].p;
-        {
+        const void* mx_in = mx;
+        if (smx.mx && smx.ok[r]) {
+            mx_in = (const char*)smx.mx + (size_t)r * f1;  // M x_o from the solve's last true residual
+        } else {
+            // M x_o = x_o - 1/4 A H_oe z with z = K H_eo M_phi x_o = M_phi (A H_eo M_phi x_o) =
+            // 2 M_phi t: the hop of the reconstruction is the first hop of M, so only the second
+            // runs here
+            void* z = c->tmp[0].p;
             M5Launch f{};
             f.nrhs = 1; f.out = z; f.in = sw.t; f.x = nullptr; f.coef = 2.0;
             set_sop(c, MDWF_F64, SOP_MPHI, 0, f);
             offset_rhs(c, MDWF_F64, r, f);
             if ((st = launch_m5(c, MDWF_F64, f))) return st;
+            note_apply(c, MDWF_F64);
+            h.out = mx; h.in = z; h.x = xo_r; h.coef = -0.25; h.out_parity = 1; h.gather = 0; h.dagger = 0;
+            h.mass = c->mass64;
+            set_sop(c, MDWF_F64, SOP_A, 0, h);
+            offset_rhs(c, MDWF_F64, r, h);
+            if ((st = launch_hop(c, MDWF_F64, h))) return st;
         }
-        note_apply(c, MDWF_F64);
-        h.out = mx; h.in = z; h.x = xo_r; h.coef = -0.25; h.out_parity = 1; h.gather = 0; h.dagger = 0;
-        h.mass = c->mass64;
-        set_sop(c, MDWF_F64, SOP_A, 0, h);
-        offset_rhs(c, MDWF_F64, r, h);
-        if ((st = launch_hop(c, MDWF_F64, h))) return st;
         {
             M5Launch d{};  // mx = b' - M x
-            d.nrhs = 1; d.out = mx; d.in = mx; d.x = sw.bp; d.coef = -1.0;
+            d.nrhs = 1; d.out = mx; d.in = mx_in; d.x = sw.bp; d.coef = -1.0;
             set_sop(c, MDWF_F64, SOP_ID, 0, d);
             offset_rhs(c, MDWF_F64, r, d);
             if ((st = launch_m5(c, MDWF_F64, d))) return st;
