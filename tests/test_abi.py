@@ -153,3 +153,34 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(m._build, "LIB", str(tmp_path / "libmdwf.so"))
     with pytest.raises(OSError, match="not found"):
         m.load(build_if_missing=False)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes structures of the binding have the C layout of the header's structs:
+    a C program built against include/mdwf.h prints each struct's size and each field's
+    offset, and they equal the ctypes figures (field names in the header's order)."""
+    import shutil
+    import subprocess
+    import paper_1206_5214_gb300 as m
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"mdwf_opts": m._Opts, "mdwf_solve_params": m.SolveParams, "mdwf_solve_info": m.SolveInfo,
+               "mdwf_kernel_stat": m.KernelStat}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "mdwf.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, cls in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert got[(cname, fname)] == getattr(cls, fname).offset, (cname, fname)
