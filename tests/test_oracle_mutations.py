@@ -122,6 +122,19 @@ MUTATIONS = {
         "            rr = rr_new;\n        }\n    }", ["solve"]),
     "adjoint_solve_wrong_rhs": (
         "or_ddw(rhs, b, U, p, 0);", "or_ddw(rhs, b, U, p, 1);", ["adjoint_solve"]),
+    "m_plus_sign": (
+        "c.v[s] = b5_of(p, s) * (4.0 - p->M5) + 1.0;", "c.v[s] = b5_of(p, s) * (4.0 - p->M5) - 1.0;",
+        ["blocks"]),
+    "schur_complement_sign": (
+        "for (long k = 0; k < n; ++k) out[k] = in[k] - b[k];", "for (long k = 0; k < n; ++k) out[k] = in[k] + b[k];",
+        ["blocks"]),
+    "m_dagger_inner_inverse_not_adjoint": (
+        "or_mee_inv(a, b, Vh, p, 1);        /* I_rr^-dag (even) */",
+        "or_mee_inv(a, b, Vh, p, 0);        /* I_rr^-dag (even) */", ["blocks"]),
+    "cg_step_halved": (
+        "            double alpha = rr / pap;\n            for (long i = 0; i < n; ++i) { x[i] += alpha * pp[i];",
+        "            double alpha = 0.5 * rr / pap;\n            for (long i = 0; i < n; ++i) { x[i] += alpha * pp[i];",
+        ["solve"]),
 }
 
 
